@@ -1,0 +1,214 @@
+/*
+ * tps.h -- C ABI of the GB300 tensor-product three-body eigensolver.
+ *
+ * Implements the hot path of "Tensor Product Scheme for Computing Bound States
+ * of the Quantum Mechanical Three-Body Problem" (arXiv 2111.02534):
+ * the pseudospectral Jacobi-coordinate Hamiltonian applied to blocks of wave
+ * functions as dense mode products plus a pointwise potential (Sec. 3.2-3.3),
+ * the shifted kinetic preconditioner (Sec. 4.2) and the block Jacobi-Davidson
+ * eigensolver around them (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Units: hbar and the masses are given explicitly (tps_set_masses), or the
+ *    paper's heavy-light units are selected with tps_set_alpha.  The kinetic
+ *    coefficient of coordinate k is a_k = -hbar^2 / (2 mu_k); x is the
+ *    heavy-heavy separation (mu_x = M/2), y the light particle relative to the
+ *    heavy pair's centre of mass (mu_y = 2Mm/(2M+m)).
+ *  - Grid: each coordinate is a periodic Fourier grid x_j = -L + j*2L/n on
+ *    [-L, L), n even and >= 4; D2 is the dense spectral second derivative.
+ *  - Vectors: FP64, one wave function after another.  1D layout [nvec][n_x][n_y],
+ *    2D layout [nvec][n_x1][n_x2][n_y1][n_y2], the last index fastest (the
+ *    ordering of Sec. 3.1).  N = product of the n's.
+ *  - Pointers named *_dev are device pointers on the context's device; *_host are
+ *    host pointers.  The caller owns every buffer it passes; the context owns
+ *    every device array it allocates (operators, potential, workspaces) and
+ *    frees them in tps_destroy.  Apply calls never allocate.
+ *  - Calls taking a stream are asynchronous on it unless stated otherwise;
+ *    stream 0 is the legacy default stream.
+ *  - Every call returns a tps_status; on failure tps_last_error(ctx) describes it.
+ *    No exception crosses the ABI.  A context is not thread-safe.
+ */
+#ifndef TPS_H
+#define TPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *cudaStream_t; /* identical to the CUDA runtime's typedef */
+
+typedef struct tps_ctx tps_ctx;
+
+typedef enum tps_status {
+  TPS_OK = 0,
+  TPS_ERR_INVALID_ARG = -1,   /* a size, pointer, enum or value is out of range */
+  TPS_ERR_NOT_CONFIGURED = -2,/* masses, grid or potential not set yet */
+  TPS_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the CUDA error) */
+  TPS_ERR_NOMEM = -4,         /* a device allocation failed */
+  TPS_ERR_SINGULAR = -5,      /* the preconditioner's shift hits the kinetic spectrum */
+  TPS_ERR_NOT_CONVERGED = -6, /* solver hit its iteration cap; results valid for stats->n_converged pairs */
+  TPS_ERR_TIMEOUT = -7        /* reserved: a bounded device wait expired */
+} tps_status;
+
+enum { TPS_GAUSS = 0, TPS_LORENTZ3 = 1 };          /* f_G = exp(-xi^2), f_L = (1+xi^2)^-3 */
+enum { TPS_ANY = 0, TPS_X_EVEN = 1, TPS_X_ODD = 2 }; /* heavy-exchange sector (Sec. 5.1) */
+enum { TPS_F64 = 0 };                                /* arithmetic of apply calls */
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context for a 1D (dim = 1) or 2D (dim = 2) three-body problem on CUDA
+ * device `device`.  Sec. 2: the three-body problem in d dimensions is a
+ * 2d-dimensional eigenvalue problem after removing the centre of mass. */
+int tps_create(tps_ctx **out, int dim, int device);
+int tps_destroy(tps_ctx *ctx);
+const char *tps_last_error(const tps_ctx *ctx);
+const char *tps_status_string(int status);
+
+/* ---- problem definition ------------------------------------------------- */
+
+/* Sec. 2 (Eq. Schroedinger_equation_three_body): kinetic coefficients from the
+ * heavy mass M, light mass m and hbar (all > 0).  a_x = -hbar^2/M,
+ * a_y = -hbar^2 (2M+m) / (4Mm). */
+int tps_set_masses(tps_ctx *ctx, double M, double m, double hbar);
+
+/* Sec. 2: the paper's dimensionless form, heavy-light reduced mass 1:
+ * a_x = -alpha_x/2 = -1/(1+alpha), a_y = -alpha_y/2 = -(1+2alpha)/(4+4alpha). */
+int tps_set_alpha(tps_ctx *ctx, double alpha);
+
+/* Sec. 3.1: grid sizes n[0..2*dim-1] (each even, >= 4) and half box lengths
+ * L[0..2*dim-1] (> 0), order (x, y) or (x1, x2, y1, y2), host arrays.  Builds the
+ * dense operators a_k*D2_k and their eigendecompositions on the device.  In 2D
+ * n_x1 = n_x2 and n_y1 = n_y2 (with equal L) are required. */
+int tps_set_grid(tps_ctx *ctx, const int *n, const double *L);
+
+/* Sec. 3.3 (Eq. tensor_form): an arbitrary diagonal potential V[N] in the vector
+ * layout (no structure assumed), copied in.  on_device != 0: V is a device
+ * pointer, else a host pointer.  Requires tps_set_grid first. */
+int tps_set_potential(tps_ctx *ctx, const double *V, int on_device);
+
+/* Eq. definition_potential: V = -v0 [f(|y - x/2|/sigma) + f(|y + x/2|/sigma)]
+ * (2D: vector distances), evaluated pointwise on the grid.  shape TPS_GAUSS or
+ * TPS_LORENTZ3, sigma > 0. */
+int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma);
+
+/* Sec. 2 and Sec. 5.1: the smallest well depth v0 for which the two-body problem
+ * [-hbar^2/(2 mu_hl) Laplacian - v0 f(|xi|/sigma)] psi = -E0 psi has a solution,
+ * from the generalized eigenvalue problem (T + E0) psi = v0 F psi on the periodic
+ * grid with n points per dimension on [-L, L) (dim 1 or 2).  E0 > 0.  Host-side
+ * setup computation; writes *v0_out. */
+int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, double sigma,
+                    int n, double L, double *v0_out);
+
+/* Number of unknowns N and the norm estimate ||H||_est = sum_k |a_k| (pi/h_k)^2 + max|V|. */
+int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est);
+
+/* ---- hot path: operator applications ----------------------------------- */
+
+/* Eq. tensor_op1D (1D) and Eq. tensor_op2D (2D): out = (H - theta) psi for nvec
+ * vectors, H = sum_k a_k (I x .. x D2_k x .. x I) + diag(V).  psi_dev, out_dev:
+ * device, [nvec][N] FP64, must not overlap.  dtype: TPS_F64. */
+int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, double theta,
+                int dtype, cudaStream_t stream);
+
+/* Sec. 4.2 (Eq. sylvester_equation): out = (T - theta)^-1 r, T the kinetic part of
+ * H (V neglected), by fast diagonalisation S ((S^T r S) ./ (Lambda (+) .. - theta)) S^T
+ * over all 2*dim modes.  Returns TPS_ERR_SINGULAR when
+ * min |lambda_sum - theta| < 1e-14 * max |lambda_sum|.  r_dev, out_dev: device
+ * [nvec][N], must not overlap. */
+int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, double theta,
+                   int dtype, cudaStream_t stream);
+
+/* ---- hot path: solver ---------------------------------------------------- */
+
+typedef struct tps_solver_opts {
+  int m_min;          /* search-space size kept at restart (0: max(2k, 8) rounded up to the block) */
+  int m_max;          /* search-space size that triggers a restart (0: m_min + 2*block; at most 64) */
+  int inner_steps;    /* GMRES steps per correction equation (0: 10; Sec. 4.1) */
+  int max_outer;      /* outer-iteration cap (0: 500) */
+  int use_prec;       /* 1: prec-JDQR (Sec. 4.2 preconditioner), 0: no-prec-JDQR */
+  double prec_shift;  /* fixed preconditioner shift; NaN: lowest active Ritz value each iteration */
+  unsigned long long seed; /* start block when x0 is NULL (counter-based normal deviates) */
+  double inner_tol;   /* GMRES stops a system when its preconditioned residual drops by this
+                         factor (0: 1e-3) */
+} tps_solver_opts;
+
+typedef struct tps_stats {
+  int outer_iters;    /* Newton (outer) iterations */
+  int h_applies;      /* single-vector H applications (MVMs, Table 2) */
+  int prec_applies;   /* single-vector preconditioner applications */
+  int inner_steps;    /* GMRES steps summed over systems */
+  int restarts;
+  int n_converged;    /* pairs returned */
+  double hnorm_est;
+  double time_ms;     /* wall time of tps_solve */
+  double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
+} tps_stats;
+
+/* Defaults for tps_solve's options. */
+void tps_default_opts(tps_solver_opts *opts);
+
+/* Sec. 4.1: the k lowest eigenpairs of H in a heavy-exchange sector (TPS_ANY,
+ * TPS_X_EVEN, TPS_X_ODD; 2D supports TPS_ANY only) by block Jacobi-Davidson with
+ * block size `block` (1..32; 1 is the paper's single-vector JDQR), converged when
+ * ||H x - theta x|| <= tol * ||H||_est.  x0_dev: nullable device [n_x0][N] warm
+ * start (Sec. 5.2 homotopy).  evals_host: host [k] ascending.  evecs_dev: device
+ * [k][N] unit-norm, sign such that the entry of largest magnitude is positive.
+ * opts may be NULL (defaults).  Synchronous: returns when results are ready.
+ * The first call allocates the solver's device workspace inside the context
+ * (kept for later calls of the same or smaller size).  k <= 64. */
+int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
+              int n_x0, const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
+              tps_stats *stats, cudaStream_t stream);
+
+/* ---- hot path: Jacobi-Davidson building blocks (device FP64) -------------
+ * Column blocks are column-major: column c of an nrows x p block A starts at
+ * A + c*lda (lda >= nrows).  Small matrices are column-major with leading
+ * dimension as given. */
+
+/* Gram matrix G = A^T B (p, q <= 64) -- block orthogonalisation and Rayleigh-Ritz
+ * projections of Sec. 4.1.  G_dev: device p x q, leading dimension ldg. */
+int tps_gram(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *B_dev,
+             long long ldb, int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream);
+
+/* Block update C = beta*C + A Y (p, q <= 64); Y_dev: device p x q, leading
+ * dimension ldy.  C must not overlap A. */
+int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *Y_dev,
+                     int ldy, int q, double beta, double *C_dev, long long ldc, long long nrows,
+                     cudaStream_t stream);
+
+/* Orthonormalise the block T (b <= 32 columns) against the orthonormal block Q
+ * (nq columns, may be 0) and within itself: two passes of block classical
+ * Gram-Schmidt followed by Cholesky QR twice (Sec. 4.1, search-space expansion).
+ * Columns that are numerically in span(Q, earlier columns) are set to zero and
+ * counted out: *rank_host receives the number of columns kept (the kept columns
+ * are moved to the front).  Synchronous. */
+int tps_orthonormalize(tps_ctx *ctx, const double *Q_dev, long long ldq, int nq, double *T_dev,
+                       long long ldt, int b, long long nrows, int *rank_host, cudaStream_t stream);
+
+/* Eigen-decomposition of a symmetric m x m matrix (m <= 64) on the device by cyclic
+ * Jacobi (Rayleigh-Ritz of Sec. 4.1).  theta_dev: m eigenvalues ascending; Y_dev:
+ * eigenvectors, column-major m x m with leading dimension ldy. */
+int tps_small_eigh(tps_ctx *ctx, const double *G_dev, int m, int ldg, double *theta_dev,
+                   double *Y_dev, int ldy, cudaStream_t stream);
+
+/* Eq. jdcor with the Sec. 4.2 preconditioner: approximate solutions t_i _|_ Qt of
+ * (I - Qt Qt^T)(H - theta_i)(I - Qt Qt^T) t_i = -r_i for nsys systems, by
+ * `steps` steps of left-preconditioned GMRES with the projected preconditioner
+ * Kt^-1 = K^-1 - K^-1 Qt (Qt^T K^-1 Qt)^-1 Qt^T K^-1, K = T - shift (use_prec = 1),
+ * or with the projector alone (use_prec = 0).  Full-grid vectors of this context:
+ * Qt_dev [nq][N] orthonormal, R_dev and T_dev [nsys][N], theta_dev [nsys] on the
+ * device.  Runs all `steps` steps (a system stops early only on breakdown).
+ * nsys <= 32, nq <= 96.  The first call allocates the correction workspace inside
+ * the context.  Synchronous. */
+int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_dev,
+                   const double *theta_dev, int nsys, int steps, int use_prec, double shift,
+                   double *T_dev, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPS_H */

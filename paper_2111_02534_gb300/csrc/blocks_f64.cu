@@ -1,0 +1,592 @@
+// FP64 block kernels for the Jacobi-Davidson steps of Sec. 4.1: tall-skinny Gram
+// matrices and block updates (orthogonalisation, Rayleigh-Ritz projection, Ritz
+// vectors, restarts, Arnoldi), the small dense eigen/Cholesky/Givens work on one
+// CTA, and elementwise helpers.  Everything stays on the device; the host only
+// reads a few scalars per outer iteration to steer the loop.
+#include <cstring>
+
+#include "tps_internal.h"
+
+namespace tps {
+namespace {
+
+constexpr int GT = 256;  // threads of the Gram / update kernels
+
+// -------------------------------- Gram ---------------------------------------
+// partial[s][pb][c][16]: the 4x4 block pb of A_s^T B_s summed over the rows of chunk c.
+__global__ void __launch_bounds__(GT)
+k_gram_partial(const double *__restrict__ A, long long lda, long long bsa, int p,
+               const double *__restrict__ B, long long ldb, long long bsb, int q,
+               long long nrows, int nchunk, double *__restrict__ partial) {
+  const int c = blockIdx.x, s = blockIdx.y, pb = blockIdx.z;
+  const int qb = (q + 3) / 4;
+  const int i0 = (pb / qb) * 4, j0 = (pb % qb) * 4;
+  const double *As = A + s * bsa;
+  const double *Bs = B + s * bsb;
+  const long long rows_per = (nrows + nchunk - 1) / nchunk;
+  const long long r0 = (long long)c * rows_per;
+  const long long r1 = r0 + rows_per < nrows ? r0 + rows_per : nrows;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += GT) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (i0 + i < p) ? As[(long long)(i0 + i) * lda + r] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = (j0 + j < q) ? Bs[(long long)(j0 + j) * ldb + r] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+  __shared__ double red[GT / 32][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double v = acc[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i * 4 + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double v = 0.0;
+    for (int w = 0; w < GT / 32; ++w) v += red[w][threadIdx.x];
+    const int npb = ((p + 3) / 4) * qb;
+    partial[(((long long)s * npb + pb) * nchunk + c) * 16 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_gram_reduce(const double *__restrict__ partial, int p, int q, int nchunk,
+                              int batch, double *__restrict__ G, int ldg, long long bsg) {
+  const int qb = (q + 3) / 4;
+  const int npb = ((p + 3) / 4) * qb;
+  const long long total = (long long)batch * p * q;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ((long long)p * q));
+    const int ij = (int)(e % ((long long)p * q));
+    const int i = ij % p, j = ij / p;
+    const int pb = (i / 4) * qb + j / 4;
+    const int w = (i % 4) * 4 + (j % 4);
+    const double *src = partial + ((long long)s * npb + pb) * nchunk * 16 + w;
+    double v = 0.0;
+    for (int c = 0; c < nchunk; ++c) v += src[(long long)c * 16];
+    G[s * bsg + (long long)j * ldg + i] = v;
+  }
+}
+
+int gram_chunks(long long nrows, int batch, int npb) {
+  const long long want = (2LL * 152 + (long long)batch * npb - 1) / ((long long)batch * npb);
+  const long long maxc = (nrows + 1023) / 1024;
+  long long c = want < maxc ? want : maxc;
+  if (c < 1) c = 1;
+  if (c > 1024) c = 1024;
+  return (int)c;
+}
+
+// ------------------------------- update --------------------------------------
+// C_s[:, j0:j0+8] = beta*C_s + alpha * A_s Y_s[:, j0:j0+8]
+__global__ void __launch_bounds__(GT)
+k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
+         const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha, double beta,
+         double *__restrict__ C, long long ldc, long long bsc, long long nrows) {
+  const int s = blockIdx.y;
+  const int j0 = blockIdx.z * 8;
+  __shared__ double Ys[64][8];
+  for (int e = threadIdx.x; e < p * 8; e += GT) {
+    const int i = e / 8, j = e % 8;
+    Ys[i][j] = (j0 + j < q) ? alpha * Y[s * bsy + (long long)(j0 + j) * ldy + i] : 0.0;
+  }
+  __syncthreads();
+  const long long r = blockIdx.x * (long long)GT + threadIdx.x;
+  if (r >= nrows) return;
+  const double *As = A + s * bsa;
+  double acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+  for (int i = 0; i < p; ++i) {
+    const double a = As[(long long)i * lda + r];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);
+  }
+  double *Cs = C + s * bsc;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j0 + j >= q) break;
+    double *dst = Cs + (long long)(j0 + j) * ldc + r;
+    *dst = (beta == 0.0) ? acc[j] : fma(beta, *dst, acc[j]);
+  }
+}
+
+// ------------------------------ Jacobi eigh ----------------------------------
+// Cyclic Jacobi with round-robin (tournament) ordering: each round rotates m/2
+// disjoint pairs at once (Golub & Van Loan, symmetric Schur decomposition and the
+// parallel ordering of the cyclic Jacobi method).  A' = J^T A J is formed element by
+// element from the two pairs an element's row and column belong to.
+constexpr int JMAX = 64;
+__global__ void __launch_bounds__(512)
+k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ theta,
+         double *__restrict__ Yout, int ldy) {
+  extern __shared__ double jsm[];
+  typedef double Mat[JMAX][JMAX + 1];
+  Mat *A = reinterpret_cast<Mat *>(jsm);                       // A[2]
+  Mat *Vv = reinterpret_cast<Mat *>(jsm + 2 * JMAX * (JMAX + 1));  // Vv[2]
+  __shared__ double rc[JMAX], rs[JMAX];
+  __shared__ double normA;  // per index: coefficient on itself and on its partner
+  __shared__ int partner[JMAX];
+  __shared__ int rotated;
+  __shared__ double offsum;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int mm = (m + 1) & ~1;  // even number of players (m odd: one dummy)
+  for (int e = tid; e < mm * mm; e += nt) {
+    const int i = e / mm, j = e % mm;
+    double v = 0.0;
+    if (i < m && j < m) v = 0.5 * (G[(long long)j * ldg + i] + G[(long long)i * ldg + j]);
+    A[0][i][j] = v;
+    Vv[0][i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) f += A[0][i][j] * A[0][i][j];
+    normA = sqrt(f);
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < mm - 1; ++r) {
+      // pairs of this round (circle method): (mm-1, r), ((r+k) mod (mm-1), (r-k) mod (mm-1))
+      if (tid < mm / 2) {
+        const int k = tid;
+        int pi, qi;
+        if (k == 0) {
+          pi = mm - 1;
+          qi = r;
+        } else {
+          pi = (r + k) % (mm - 1);
+          qi = (r - k + (mm - 1)) % (mm - 1);
+        }
+        const int p = pi < qi ? pi : qi, q = pi < qi ? qi : pi;
+        double c = 1.0, s = 0.0;
+        const double apq = A[cur][p][q];
+        if (q < m && apq != 0.0) {
+          const double app = A[cur][p][p], aqq = A[cur][q][q];
+          // rotate unless a_pq is negligible both relative to its diagonal pair and
+          // in absolute terms (rounding-level entries are not chased)
+          const double thr = 1e-18 * sqrt(fabs(app * aqq));
+          if (fabs(apq) > thr && fabs(apq) > 1e-17 * normA && fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            double t;
+            if (fabs(tau) > 1e150)
+              t = 0.5 / tau;
+            else
+              t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            rotated = 1;
+          }
+        }
+        // column p of J = c e_p - s e_q ; column q of J = s e_p + c e_q
+        partner[p] = q;
+        partner[q] = p;
+        rc[p] = c;
+        rs[p] = -s;
+        rc[q] = c;
+        rs[q] = s;
+      }
+      __syncthreads();
+      const int nxt = cur ^ 1;
+      for (int e = tid; e < mm * mm; e += nt) {
+        const int i = e / mm, j = e % mm;
+        const int pi = partner[i], pj = partner[j];
+        const double ci = rc[i], si = rs[i], cj = rc[j], sj = rs[j];
+        // A'[i][j] = sum_{a in {i,pi}, b in {j,pj}} J[a][i] J[b][j] A[a][b]
+        const double v = ci * (cj * A[cur][i][j] + sj * A[cur][i][pj]) +
+                         si * (cj * A[cur][pi][j] + sj * A[cur][pi][pj]);
+        A[nxt][i][j] = v;
+        Vv[nxt][i][j] = cj * Vv[cur][i][j] + sj * Vv[cur][i][pj];
+      }
+      __syncthreads();
+      cur = nxt;
+    }
+    if (tid == 0) {
+      double off = 0.0;
+      for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) off += A[cur][i][j] * A[cur][i][j];
+      offsum = off;
+    }
+    __syncthreads();
+    if (!rotated || offsum == 0.0) break;
+    __syncthreads();
+  }
+  // sort ascending (selection by one thread; m <= 64)
+  __shared__ int perm[JMAX];
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    for (int i = 0; i < m; ++i) {
+      int best = i;
+      for (int j = i + 1; j < m; ++j)
+        if (A[cur][perm[j]][perm[j]] < A[cur][perm[best]][perm[best]]) best = j;
+      const int t = perm[i];
+      perm[i] = perm[best];
+      perm[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    Yout[(long long)j * ldy + i] = Vv[cur][i][perm[j]];
+  }
+  for (int j = tid; j < m; j += nt) theta[j] = A[cur][perm[j]][perm[j]];
+}
+
+// ------------------------------ Cholesky QR ----------------------------------
+__global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__restrict__ ref,
+                           double tol_rel, double *__restrict__ Rinv, int *__restrict__ keep) {
+  __shared__ double R[32][33];
+  __shared__ int kp[32];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    R[i][j] = G[(long long)j * b + i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // right-looking Cholesky G = R^T R (R upper), dropping dependent columns
+    for (int j = 0; j < b; ++j) {
+      double d = R[j][j];
+      for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
+      const double rj = ref ? ref[j] : G[(long long)j * b + j];
+      if (!(d > tol_rel * tol_rel * rj) || !(d > 0.0)) {
+        kp[j] = 0;
+        for (int i = j; i < b; ++i) R[j][i] = 0.0;
+        continue;
+      }
+      kp[j] = 1;
+      const double rjj = sqrt(d);
+      R[j][j] = rjj;
+      for (int i = j + 1; i < b; ++i) {
+        double v = R[j][i];
+        for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
+        R[j][i] = v / rjj;
+      }
+    }
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < i; ++j) R[i][j] = 0.0;
+  }
+  __syncthreads();
+  // Rinv column c by back substitution (dropped rows/columns are zero)
+  if (tid < b) {
+    const int c = tid;
+    double x[32];
+    for (int i = 0; i < b; ++i) x[i] = 0.0;
+    if (kp[c]) {
+      for (int i = c; i >= 0; --i) {
+        if (!kp[i]) {
+          x[i] = 0.0;
+          continue;
+        }
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= c; ++k) v -= R[i][k] * x[k];
+        x[i] = v / R[i][i];
+      }
+    }
+    for (int i = 0; i < b; ++i) Rinv[(long long)c * b + i] = x[i];
+    keep[c] = kp[c];
+  }
+}
+
+// --------------------------- SPD inverse (small) ------------------------------
+// Minv = M^-1 by Cholesky M = L L^T in place in Minv (lower), then L^-1, then L^-T L^-1.
+__global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__restrict__ W) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ double sm[];
+  double *Lm = sm;           // q x q, column-major
+  double *Li = sm + q * q;   // q x q
+  for (int e = tid; e < q * q; e += nt) {
+    const int i = e % q, j = e / q;
+    Lm[e] = 0.5 * (M[(long long)j * q + i] + M[(long long)i * q + j]);
+    Li[e] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    if (tid == 0) {
+      double d = Lm[j * q + j];
+      for (int k = 0; k < j; ++k) d -= Lm[k * q + j] * Lm[k * q + j];
+      Lm[j * q + j] = sqrt(d > 0.0 ? d : 1e-300);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < q; i += nt) {
+      double v = Lm[j * q + i];
+      for (int k = 0; k < j; ++k) v -= Lm[k * q + i] * Lm[k * q + j];
+      Lm[j * q + i] = v / Lm[j * q + j];
+    }
+    __syncthreads();
+  }
+  // Li = L^-1 column by column (forward substitution), one thread per column
+  for (int c = tid; c < q; c += nt) {
+    for (int i = c; i < q; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= Lm[k * q + i] * Li[c * q + k];
+      Li[c * q + i] = v / Lm[i * q + i];
+    }
+  }
+  __syncthreads();
+  // W = Li^T Li
+  for (int e = tid; e < q * q; e += nt) {
+    const int i = e % q, j = e / q;
+    double v = 0.0;
+    const int k0 = i > j ? i : j;
+    for (int k = k0; k < q; ++k) v += Li[i * q + k] * Li[j * q + k];
+    W[(long long)j * q + i] = v;
+  }
+}
+
+// ------------------------------ elementwise ----------------------------------
+__global__ void k_axpby_cols(int ncols, long long nrows, double alpha, const double *X,
+                             long long ldx, double beta, double *Y, long long ldy) {
+  const long long total = (long long)ncols * nrows;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / nrows, r = e % nrows;
+    double *y = Y + c * ldy + r;
+    const double xv = alpha * X[c * ldx + r];
+    *y = (beta == 0.0) ? xv : fma(beta, *y, xv);
+  }
+}
+
+__global__ void k_scale_cols(int ncols, long long nrows, const double *X, long long ldx,
+                             const double *scale, int invert, double *Y, long long ldy) {
+  const long long total = (long long)ncols * nrows;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / nrows, r = e % nrows;
+    double f = scale[c];
+    if (invert) f = (f > 1e-300 || f < -1e-300) ? 1.0 / f : 0.0;
+    Y[c * ldy + r] = X[c * ldx + r] * f;
+  }
+}
+
+__global__ void k_residual(int ncols, long long nrows, const double *HX, const double *X,
+                           const double *theta, double *R) {
+  const long long total = (long long)ncols * nrows;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / nrows;
+    R[e] = fma(-theta[c], X[e], HX[e]);
+  }
+}
+
+// Parity-reduced coordinates of the 1D grid (mode 0 = x folded by x -> -x):
+//  even: u_i = sqrt(w_i) * (P_i + P_{n-i}) / 2, i = 0..n/2, w = (1, 2, .., 2, 1)
+//  odd:  u_i = sqrt(2) * (P_i - P_{n-i}) / 2,   i = 1..n/2-1
+__global__ void k_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
+                                  double *red) {
+  const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
+  const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
+  const long long total = (long long)ncols * Nr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / Nr, rem = e % Nr;
+    const int ir = (int)(rem / ny), j = (int)(rem % ny);
+    const double *P = full + c * Nf;
+    double v;
+    if (parity == TPS_X_EVEN) {
+      const int i = ir;
+      if (i == 0 || i == nx / 2)
+        v = P[(long long)i * ny + j];
+      else
+        v = sqrt(2.0) * 0.5 * (P[(long long)i * ny + j] + P[(long long)(nx - i) * ny + j]);
+    } else {
+      const int i = ir + 1;
+      v = sqrt(2.0) * 0.5 * (P[(long long)i * ny + j] - P[(long long)(nx - i) * ny + j]);
+    }
+    red[c * Nr + rem] = v;
+  }
+}
+
+__global__ void k_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
+                                double *full) {
+  const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
+  const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
+  const long long total = (long long)ncols * Nf;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / Nf, rem = e % Nf;
+    const int i = (int)(rem / ny), j = (int)(rem % ny);
+    const double *u = red + c * Nr;
+    double v;
+    if (parity == TPS_X_EVEN) {
+      const int ir = i <= nx / 2 ? i : nx - i;
+      const double w = (ir == 0 || ir == nx / 2) ? 1.0 : sqrt(0.5);
+      v = w * u[(long long)ir * ny + j];
+    } else {
+      if (i == 0 || i == nx / 2) {
+        v = 0.0;
+      } else {
+        const int ir = i < nx / 2 ? i : nx - i;
+        const double sg = i < nx / 2 ? 1.0 : -1.0;
+        v = sg * sqrt(0.5) * u[(long long)(ir - 1) * ny + j];
+      }
+    }
+    full[c * Nf + rem] = v;
+  }
+}
+
+// sign fix: one CTA per column, argmax |x| (lowest index on ties), flip if negative
+__global__ void k_fix_sign(long long nrows, double *X) {
+  const long long c = blockIdx.x;
+  double *x = X + c * nrows;
+  double best = -1.0;
+  long long bi = 0;
+  for (long long r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const double a = fabs(x[r]);
+    if (a > best) {
+      best = a;
+      bi = r;
+    }
+  }
+  __shared__ double sb[256];
+  __shared__ long long si[256];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = sb[threadIdx.x + o];
+      const long long ai = si[threadIdx.x + o];
+      if (a > sb[threadIdx.x] || (a == sb[threadIdx.x] && ai < si[threadIdx.x])) {
+        sb[threadIdx.x] = a;
+        si[threadIdx.x] = ai;
+      }
+    }
+    __syncthreads();
+  }
+  const double sgn = x[si[0]] < 0.0 ? -1.0 : 1.0;
+  __syncthreads();
+  if (sgn < 0.0)
+    for (long long r = threadIdx.x; r < nrows; r += blockDim.x) x[r] = -x[r];
+}
+
+unsigned grid_for(long long total, int threads = 256) {
+  long long b = (total + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+long long gram_scratch_doubles(int p, int q, int batch) {
+  const int npb = ((p + 3) / 4) * ((q + 3) / 4);
+  return (long long)batch * npb * 1024 * 16;
+}
+
+void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
+                 long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
+                 long long bsg, int batch, GramScratch &scr, cudaStream_t s) {
+  if (p <= 0 || q <= 0 || batch <= 0) return;
+  const int npb = ((p + 3) / 4) * ((q + 3) / 4);
+  int nchunk = gram_chunks(nrows, batch, npb);
+  const long long cap = scr.capacity / ((long long)batch * npb * 16);
+  if (nchunk > cap) nchunk = (int)(cap > 0 ? cap : 1);
+  dim3 grid(nchunk, batch, npb);
+  k_gram_partial<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial);
+  const long long total = (long long)batch * p * q;
+  k_gram_reduce<<<grid_for(total), 256, 0, s>>>(scr.partial, p, q, nchunk, batch, G, ldg, bsg);
+}
+
+void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
+                   long long bsy, int q, double alpha, double beta, double *C, long long ldc,
+                   long long bsc, long long nrows, int batch, cudaStream_t s) {
+  if (q <= 0 || batch <= 0 || nrows <= 0) return;
+  if (p <= 0) {  // C = beta * C
+    for (int b = 0; b < batch; ++b)
+      k_axpby_cols<<<grid_for((long long)q * nrows), 256, 0, s>>>(q, nrows, 0.0, C + b * bsc, ldc,
+                                                                beta, C + b * bsc, ldc);
+    return;
+  }
+  // p is processed in slabs of 64 rows of Y; the first slab applies beta
+  for (int i0 = 0; i0 < p; i0 += 64) {
+    const int pp = p - i0 < 64 ? p - i0 : 64;
+    dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + 7) / 8);
+    k_update<<<grid, GT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha,
+                                 i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows);
+  }
+}
+
+void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
+                        cudaStream_t s) {
+  const size_t smem = 4 * (size_t)JMAX * (JMAX + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_jacobi<<<1, 512, smem, s>>>(G, m, ldg, theta, Y, ldy);
+}
+
+void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,
+                     int *keep, cudaStream_t s) {
+  k_chol_inv<<<1, 32, 0, s>>>(G, b, ref, tol_rel, Rinv, keep);
+}
+
+void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)q * q * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_spd_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * 96 * 96 * (int)sizeof(double));
+    attr = true;
+  }
+  k_spd_inverse<<<1, 128, smem, s>>>(M, q, Minv);
+}
+
+void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X, long long ldx,
+                       double beta, double *Y, long long ldy, cudaStream_t s) {
+  if (ncols <= 0 || nrows <= 0) return;
+  k_axpby_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, alpha, X, ldx,
+                                                                   beta, Y, ldy);
+}
+
+void launch_scale_cols(int ncols, long long nrows, const double *X, long long ldx,
+                       const double *scale, int invert, double *Y, long long ldy, cudaStream_t s) {
+  if (ncols <= 0 || nrows <= 0) return;
+  k_scale_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, X, ldx, scale,
+                                                                   invert, Y, ldy);
+}
+
+void launch_residual(int ncols, long long nrows, const double *HX, const double *X,
+                     const double *theta, double *R, cudaStream_t s) {
+  if (ncols <= 0) return;
+  k_residual<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, HX, X, theta, R);
+}
+
+void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
+                            double *red, cudaStream_t s) {
+  const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
+  k_sector_restrict<<<grid_for((long long)ncols * nr * ny), 256, 0, s>>>(parity, nx, ny, ncols,
+                                                                         full, red);
+}
+
+void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
+                          double *full, cudaStream_t s) {
+  k_sector_expand<<<grid_for((long long)ncols * nx * ny), 256, 0, s>>>(parity, nx, ny, ncols, red,
+                                                                       full);
+}
+
+void launch_fix_sign(int ncols, long long nrows, double *X, cudaStream_t s) {
+  if (ncols <= 0) return;
+  k_fix_sign<<<ncols, 256, 0, s>>>(nrows, X);
+}
+
+}  // namespace tps

@@ -1,0 +1,596 @@
+// Block Jacobi-Davidson eigensolver (Sec. 4.1) with the fast-diagonalisation
+// preconditioner of Sec. 4.2, for the lowest eigenpairs of the symmetric Kronecker-sum
+// Hamiltonian.  For symmetric H the Newton system of Eq. jdqr reduces to Ritz pairs of
+// V^T H V and the correction equation Eq. jdcor; the paper's single-vector JDQR is
+// block size 1.
+//
+// All vector work runs in device kernels on one stream.  The host keeps the loop
+// state (basis size, number of locked pairs) and reads a handful of scalars per
+// outer iteration (Ritz values, residual norms, rank flags) to steer it.
+//
+// 1D problems in a heavy-exchange sector run on the parity-folded operator (Sec. 5.1,
+// parity selection rule): half the x grid, roughly 2.6x fewer flops per H-apply.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "jd_kernels.h"
+#include "tps_internal.h"
+
+namespace tps {
+
+struct SolverWorkspace {
+  long long N = 0;
+  int mmax = 0, b = 0, kmax = 0, steps = 0;
+  double *arena = nullptr;
+  size_t arena_bytes = 0;
+  // big vectors
+  double *V = nullptr, *HV = nullptr, *V2 = nullptr, *HV2 = nullptr;  // [mmax][N]
+  double *QX = nullptr, *KQX = nullptr;                                // [kmax + b][N]
+  double *HX = nullptr, *R = nullptr, *P = nullptr, *W = nullptr;      // [b][N]
+  double *Z = nullptr;                                                 // [(steps+1) b][N]
+  double *T2 = nullptr;                                                // [b][N] scratch
+  // small
+  double *G = nullptr, *Y = nullptr;            // [mmax * mmax]
+  double *theta = nullptr, *theta2 = nullptr;   // [mmax]
+  double *nrm2 = nullptr, *ref = nullptr;       // [max(b, kmax + b)]
+  double *C = nullptr;                          // [(kmax + mmax + b) * b] projection coefficients
+  double *Mq = nullptr, *Minv = nullptr;        // [(kmax+b)^2]
+  double *Rinv = nullptr;                       // [b * b]
+  int *keep = nullptr;                          // [b]
+  GmresState gm;
+  double *h_pinned = nullptr;                   // host readback buffer
+  int *hi_pinned = nullptr;
+};
+
+namespace {
+
+// counter-based normal deviates (splitmix64 + Box-Muller) for random start blocks
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+double uniform01(uint64_t seed, uint64_t i) {
+  return ((splitmix64(seed * 0x2545F4914F6CDD1DULL + i) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
+  const double two_pi = 6.283185307179586;
+  for (size_t e = 0; e < v.size(); e += 2) {
+    const double u1 = uniform01(seed, offset + e), u2 = uniform01(seed, offset + e + 1);
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    v[e] = r * std::cos(two_pi * u2);
+    if (e + 1 < v.size()) v[e + 1] = r * std::sin(two_pi * u2);
+  }
+}
+
+struct Ctx {
+  tps_ctx *ctx;
+  const DevOperator &op;
+  SolverWorkspace &w;
+  cudaStream_t s;
+  long long N;
+};
+
+int fill_random(Ctx &c, double *dst, int ncols, uint64_t seed, uint64_t &counter) {
+  std::vector<double> h((size_t)ncols * c.N);
+  random_normal(h, seed, counter);
+  counter += h.size() + 1;
+  TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double),
+                                      cudaMemcpyHostToDevice, c.s));
+  TPS_CUDA_TRY(c.ctx, cudaStreamSynchronize(c.s));
+  return TPS_OK;
+}
+
+// diag(A^T A) for ncols columns -> out[ncols] (device)
+void col_norms2(Ctx &c, const double *A, int ncols, double *out) {
+  launch_gram(A, c.N, c.N, 1, A, c.N, c.N, 1, c.N, out, 1, 1, ncols, c.ctx->gscr, c.s);
+}
+
+// T (b cols) <- orthonormal basis of span(T) minus span(B1, B2); B1, B2 orthonormal blocks
+// (nb1, nb2 columns, ld N).  Returns the number of kept columns (moved to the front).
+int orthonormalize(Ctx &c, const double *B1, int nb1, const double *B2, int nb2, double *T, int b,
+                   int *rank) {
+  SolverWorkspace &w = c.w;
+  col_norms2(c, T, b, w.ref);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (nb1 > 0) {
+      launch_gram(B1, c.N, 0, nb1, T, c.N, 0, b, c.N, w.C, nb1, 0, 1, c.ctx->gscr, c.s);
+      launch_update(B1, c.N, 0, nb1, w.C, nb1, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+    }
+    if (nb2 > 0) {
+      launch_gram(B2, c.N, 0, nb2, T, c.N, 0, b, c.N, w.C, nb2, 0, 1, c.ctx->gscr, c.s);
+      launch_update(B2, c.N, 0, nb2, w.C, nb2, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+    }
+  }
+  // Cholesky QR twice; the first pass drops numerically dependent columns
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_gram(T, c.N, 0, b, T, c.N, 0, b, c.N, w.C, b, 0, 1, c.ctx->gscr, c.s);
+    launch_chol_inv(w.C, b, pass == 0 ? w.ref : nullptr, pass == 0 ? 1e-7 : 1e-12, w.Rinv,
+                    w.keep, c.s);
+    launch_update(T, c.N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, c.N, 0, c.N, 1, c.s);
+    TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(T, w.T2, (size_t)b * c.N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c.s));
+    if (pass == 0) {
+      TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(w.hi_pinned, w.keep, b * sizeof(int),
+                                          cudaMemcpyDeviceToHost, c.s));
+    }
+  }
+  TPS_CUDA_TRY(c.ctx, cudaStreamSynchronize(c.s));
+  TPS_CUDA_TRY(c.ctx, cudaGetLastError());
+  int r = 0;
+  for (int j = 0; j < b; ++j) {
+    if (w.hi_pinned[j]) {
+      if (r != j)
+        TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(T + (long long)r * c.N, T + (long long)j * c.N,
+                                            c.N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+      ++r;
+    }
+  }
+  *rank = r;
+  return TPS_OK;
+}
+
+// Out = Kt^-1 Y for nsys columns: projected preconditioner (use_prec) or projector.
+void kt_inverse(Ctx &c, const double *Qt, int nq, const double *KQt, int use_prec, double shift,
+                const double *Yin, int nsys, double *Out) {
+  SolverWorkspace &w = c.w;
+  if (use_prec) {
+    launch_apply_prec(c.op, Yin, Out, nsys, shift, c.ctx->ws, c.s);
+    if (nq > 0) {
+      launch_gram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
+      // C2 = Minv * C, stored after C
+      double *C2 = w.C + (long long)nq * nsys;
+      launch_small_gemm(nq, nsys, nq, 1.0, w.Minv, nq, w.C, nq, 0.0, C2, nq, c.s);
+      launch_update(KQt, c.N, 0, nq, C2, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+    }
+  } else {
+    if (Out != Yin) launch_axpby_cols(nsys, c.N, 1.0, Yin, c.N, 0.0, Out, c.N, c.s);
+    for (int pass = 0; pass < 2 && nq > 0; ++pass) {
+      launch_gram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
+      launch_update(Qt, c.N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+    }
+  }
+}
+
+int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int steps) {
+  SolverWorkspace *w = ctx->sw;
+  if (w && w->N == N && w->mmax >= mmax && w->b >= b && w->kmax >= kmax && w->steps >= steps)
+    return TPS_OK;
+  if (w) {
+    mmax = std::max(mmax, w->mmax);
+    b = std::max(b, w->b);
+    kmax = std::max(kmax, w->kmax);
+    steps = std::max(steps, w->steps);
+    free_solver_workspace(ctx);
+  }
+  w = new SolverWorkspace;
+  ctx->sw = w;
+  w->N = N;
+  w->mmax = mmax;
+  w->b = b;
+  w->kmax = kmax;
+  w->steps = steps;
+  const int mk2 = std::max(mmax, kmax);  // V2/HV2 also hold the final H Q and residuals
+  const long long nbig = 2LL * mmax + 2LL * mk2 + 2LL * (kmax + b) + 4LL * b +
+                         (long long)(steps + 1) * b + b;
+  const int q = kmax + b;
+  const long long nsmall = 2LL * mmax * mmax + 2LL * mmax + 2LL * std::max(q, mmax) +
+                           2LL * (q + mmax + b) * std::max(b, q) + 2LL * q * q + (long long)b * b +
+                           /* gmres */ (long long)b * ((steps + 1) * steps + 2 * steps + (steps + 1) +
+                                                      3 + steps + (steps + 1)) + 64;
+  const size_t bytes = ((size_t)nbig * N + (size_t)nsmall) * sizeof(double) + 4096 * 4;
+  TPS_CUDA_TRY(ctx, cudaMalloc((void **)&w->arena, bytes));
+  w->arena_bytes = bytes;
+  double *p = w->arena;
+  auto take = [&](long long n) {
+    double *r = p;
+    p += (n + 31) / 32 * 32;
+    return r;
+  };
+  w->V = take((long long)mmax * N);
+  w->HV = take((long long)mmax * N);
+  w->V2 = take((long long)mk2 * N);
+  w->HV2 = take((long long)mk2 * N);
+  w->QX = take((long long)q * N);
+  w->KQX = take((long long)q * N);
+  w->HX = take((long long)b * N);
+  w->R = take((long long)b * N);
+  w->P = take((long long)b * N);
+  w->W = take((long long)b * N);
+  w->Z = take((long long)(steps + 1) * b * N);
+  w->T2 = take((long long)b * N);
+  w->G = take((long long)mmax * mmax);
+  w->Y = take((long long)mmax * mmax);
+  w->theta = take(mmax);
+  w->theta2 = take(mmax);
+  w->nrm2 = take(std::max(q, mmax));
+  w->ref = take(std::max(q, mmax));
+  w->C = take(2LL * (q + mmax + b) * std::max(b, q));
+  w->Mq = take((long long)q * q);
+  w->Minv = take((long long)q * q);
+  w->Rinv = take((long long)b * b);
+  w->gm.Hb = take((long long)b * (steps + 1) * steps);
+  w->gm.cs = take((long long)b * steps);
+  w->gm.sn = take((long long)b * steps);
+  w->gm.g = take((long long)b * (steps + 1));
+  w->gm.beta = take(b);
+  w->gm.scale = take(b);
+  w->gm.y = take((long long)b * steps);
+  w->gm.h = take((long long)b * (steps + 1));
+  w->gm.nrm2 = take(b);
+  w->keep = reinterpret_cast<int *>(take(b));
+  w->gm.done = reinterpret_cast<int *>(take(b));
+  w->gm.mvalid = reinterpret_cast<int *>(take(b));
+  if ((char *)p > (char *)w->arena + bytes) return set_error(ctx, TPS_ERR_CUDA, "arena overflow");
+  TPS_CUDA_TRY(ctx, cudaMemset(w->arena, 0, bytes));
+  TPS_CUDA_TRY(ctx, cudaMallocHost((void **)&w->h_pinned, 4096 * sizeof(double)));
+  TPS_CUDA_TRY(ctx, cudaMallocHost((void **)&w->hi_pinned, 4096 * sizeof(int)));
+  // the Gram scratch must hold the largest skinny product of the loop
+  int st = ensure_gram_scratch(ctx, gram_scratch_doubles(std::max(q, mmax), std::max(q, mmax), 1));
+  if (st) return st;
+  // preconditioner intermediates for a block of b vectors
+  return ensure_apply_workspace(ctx, (long long)std::max(b, q) * N);
+}
+
+}  // namespace
+
+void free_solver_workspace(tps_ctx *ctx) {
+  if (!ctx->sw) return;
+  cudaFree(ctx->sw->arena);
+  cudaFreeHost(ctx->sw->h_pinned);
+  cudaFreeHost(ctx->sw->hi_pinned);
+  delete ctx->sw;
+  ctx->sw = nullptr;
+}
+
+// GMRES on the projected, preconditioned correction equation for nsys systems in
+// lockstep (Eq. jdcor; Sec. 4.1: GMRES with the preconditioner of Sec. 4.2).  Qt: nq
+// orthonormal columns; KQt: K^-1 Qt if already computed (nq_cached of the columns; the
+// rest are computed here), theta: device [nsys].  Writes T [nsys][N].
+int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int nq,
+                    const double *KQt_cached, int nq_cached, const double *R,
+                    const double *theta, int nsys, int steps, int use_prec, double shift,
+                    double inner_tol, double *T, int *h_applies, int *prec_applies,
+                    cudaStream_t s) {
+  SolverWorkspace &w = *ctx->sw;
+  Ctx c{ctx, op, w, s, op.N};
+  const long long N = op.N;
+  double *KQt = w.KQX;
+  if (use_prec && nq > 0) {
+    if (KQt_cached != KQt && nq_cached > 0)
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(KQt, KQt_cached, (size_t)nq_cached * N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+    if (nq > nq_cached) {
+      launch_apply_prec(op, Qt + (long long)nq_cached * N, KQt + (long long)nq_cached * N,
+                        nq - nq_cached, shift, ctx->ws, s);
+      *prec_applies += nq - nq_cached;
+    }
+    launch_gram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s);
+    launch_spd_inverse(w.Mq, nq, w.Minv, s);
+  }
+  const int sst = steps;
+  // z_0 = -Kt^-1 r / beta
+  double *Z = w.Z;
+  kt_inverse(c, Qt, nq, KQt, use_prec, shift, R, nsys, Z);
+  if (use_prec) *prec_applies += nsys;
+  col_norms2(c, Z, nsys, w.gm.nrm2);
+  launch_gmres_init(nsys, sst, w.gm.nrm2, w.gm, s);
+  launch_scale_cols(nsys, N, Z, N, w.gm.scale, 0, Z, N, s);
+  for (int j = 0; j < sst; ++j) {
+    double *zj = Z + (long long)j * nsys * N;
+    launch_apply_h(op, zj, w.W, nsys, theta, 0.0, s);
+    *h_applies += nsys;
+    kt_inverse(c, Qt, nq, KQt, use_prec, shift, w.W, nsys, w.P);
+    if (use_prec) *prec_applies += nsys;
+    // Arnoldi, classical Gram-Schmidt twice, per system: h = Z_i^T p_i ; p_i -= Z_i h
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_gram(Z, (long long)nsys * N, N, j + 1, w.P, N, N, 1, N, w.gm.h, sst + 1, sst + 1, nsys,
+                  ctx->gscr, s);
+      launch_update(Z, (long long)nsys * N, N, j + 1, w.gm.h, sst + 1, sst + 1, 1, -1.0, 1.0, w.P, N,
+                    N, N, nsys, s);
+      launch_hess_add(nsys, sst, j, w.gm.h, sst + 1, w.gm, s);
+    }
+    col_norms2(c, w.P, nsys, w.gm.nrm2);
+    launch_gmres_givens(nsys, sst, j, w.gm.nrm2, w.gm, inner_tol, s);
+    launch_scale_cols(nsys, N, w.P, N, w.gm.scale, 0, Z + (long long)(j + 1) * nsys * N, N, s);
+  }
+  launch_gmres_solve(nsys, sst, w.gm, s);
+  launch_update(Z, (long long)nsys * N, N, sst, w.gm.y, sst, sst, 1, 1.0, 0.0, T, N, N, N, nsys, s);
+  TPS_CUDA_TRY(ctx, cudaGetLastError());
+  return TPS_OK;
+}
+
+int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0,
+               int n_x0, const tps_solver_opts *opts_in, double *evals_host, double *evecs_dev,
+               tps_stats *stats, cudaStream_t s) {
+  const auto t_start = std::chrono::steady_clock::now();
+  tps_solver_opts opts;
+  tps_default_opts(&opts);
+  if (opts_in) opts = *opts_in;
+  const int b = std::min(block, k);
+  int mmin = opts.m_min > 0 ? opts.m_min : std::max(2 * k, 8);
+  mmin = ((mmin + b - 1) / b) * b;
+  int mmax = opts.m_max > 0 ? opts.m_max : mmin + 2 * b;
+  mmax = std::min(mmax, 64);
+  if (mmin > mmax - b) mmin = std::max(b, mmax - b);
+  if (mmin < k) mmin = std::min(k, mmax - b);
+  const int steps = opts.inner_steps > 0 ? opts.inner_steps : 10;
+  const int max_outer = opts.max_outer > 0 ? opts.max_outer : 500;
+  const double inner_tol = opts.inner_tol > 0 ? opts.inner_tol : 1e-3;
+  if (mmax < 2 * b || steps > 40)
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "search space too small for the block");
+
+  const DevOperator *opp = &ctx->full;
+  if (parity != TPS_ANY) {
+    int st = build_sector_operator(ctx, parity);
+    if (st) return st;
+    opp = &ctx->sect[parity];
+  }
+  const DevOperator &op = *opp;
+  const long long N = op.N;
+  if (k > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
+  int st = alloc_workspace(ctx, N, mmax, b, k, steps);
+  if (st) return st;
+  SolverWorkspace &w = *ctx->sw;
+  Ctx c{ctx, op, w, s, N};
+  double hnorm = 0.0;
+  tps_get_info(ctx, nullptr, &hnorm);
+
+  tps_stats stt;
+  std::memset(&stt, 0, sizeof(stt));
+  stt.hnorm_est = hnorm;
+  uint64_t rng_counter = 0;
+  std::vector<double> lam(k, 0.0), resid(k, 0.0);
+
+  // start block: warm start restricted to the sector, completed with random columns
+  int bn = b;
+  {
+    const int nw = std::min(n_x0, b);
+    if (nw > 0 && x0) {
+      if (parity != TPS_ANY)
+        launch_sector_restrict(parity, ctx->n[0], ctx->n[1], nw, x0, w.V, s);
+      else
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.V, x0, (size_t)nw * N * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+    }
+    if (nw < b) {
+      st = fill_random(c, w.V + (long long)nw * N, b - nw, opts.seed, rng_counter);
+      if (st) return st;
+    }
+  }
+  int m = 0, nlock = 0;
+  double cached_shift = NAN;
+  int kq_valid = 0;  // locked columns of KQX valid for cached_shift
+  int outer = 0;
+  bool converged = false;
+  for (outer = 0; outer < max_outer; ++outer) {
+    // (1) orthonormalise the new block against the locked vectors and the basis
+    double *T = w.V + (long long)m * N;
+    int rank = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      st = orthonormalize(c, w.QX, nlock, w.V, m, T, bn, &rank);
+      if (st) return st;
+      if (rank > 0) break;
+      st = fill_random(c, T, bn, opts.seed, rng_counter);
+      if (st) return st;
+    }
+    if (rank == 0) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "search space cannot be expanded");
+    bn = rank;
+    // (2) H applied to the new block
+    double *HT = w.HV + (long long)m * N;
+    launch_apply_h(op, T, HT, bn, nullptr, 0.0, s);
+    stt.h_applies += bn;
+    // (3) projected matrix G = V^T H V, new columns and their mirror
+    if (m > 0) launch_gram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * mmax, mmax, 0, 1,
+                           ctx->gscr, s);
+    launch_gram(T, N, 0, bn, HT, N, 0, bn, N, w.G + (long long)m * mmax + m, mmax, 0, 1, ctx->gscr,
+                s);
+    launch_mirror_block(w.G, mmax, m, bn, s);
+    m += bn;
+    // (4) Rayleigh-Ritz
+    launch_jacobi_eigh(w.G, m, mmax, w.theta, w.Y, mmax, s);
+    const int nact = std::min(b, std::min(k - nlock, m));
+    double *X = w.QX + (long long)nlock * N;
+    launch_update(w.V, N, 0, m, w.Y, mmax, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
+    launch_update(w.HV, N, 0, m, w.Y, mmax, 0, nact, 1.0, 0.0, w.HX, N, 0, N, 1, s);
+    launch_residual(nact, N, w.HX, X, w.theta, w.R, s);
+    col_norms2(c, w.R, nact, w.nrm2);
+    // (5) read back Ritz values and residual norms
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta, nact * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 64, w.nrm2, nact * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    TPS_CUDA_TRY(ctx, cudaGetLastError());
+    int nconv = 0;
+    while (nconv < nact && std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) <= tol * hnorm) {
+      lam[nlock + nconv] = w.h_pinned[nconv];
+      resid[nlock + nconv] = std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) / hnorm;
+      ++nconv;
+    }
+    if (!std::isfinite(w.h_pinned[0]))
+      return set_error(ctx, TPS_ERR_NOT_CONVERGED, "non-finite Ritz value");
+    nlock += nconv;
+    if (nlock >= k) {
+      converged = true;
+      ++outer;
+      break;
+    }
+    // (6) lock and/or restart: keep Ritz vectors nconv .. nconv+mk-1
+    int nact2 = nact;
+    if (nconv > 0 || m + b > mmax) {
+      const int avail = m - nconv;
+      const int mk = (m + b > mmax) ? std::min(avail, mmin) : avail;
+      launch_update(w.V, N, 0, m, w.Y + (long long)nconv * mmax, mmax, 0, mk, 1.0, 0.0, w.V2, N, 0,
+                    N, 1, s);
+      launch_update(w.HV, N, 0, m, w.Y + (long long)nconv * mmax, mmax, 0, mk, 1.0, 0.0, w.HV2, N,
+                    0, N, 1, s);
+      std::swap(w.V, w.V2);
+      std::swap(w.HV, w.HV2);
+      launch_copy_small(w.theta + nconv, w.theta2, mk, s);
+      std::swap(w.theta, w.theta2);
+      launch_set_diag(w.G, mmax, w.theta, mk, s);
+      m = mk;
+      ++stt.restarts;
+      nact2 = std::min(b, std::min(k - nlock, m));
+      X = w.QX + (long long)nlock * N;
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(X, w.V, (size_t)nact2 * N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.HX, w.HV, (size_t)nact2 * N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+      launch_residual(nact2, N, w.HX, X, w.theta, w.R, s);
+    }
+    // (7) correction equations for the active Ritz pairs
+    double shift = opts.prec_shift;
+    if (!std::isfinite(shift)) {
+      const double th0 = w.h_pinned[nconv < nact ? nconv : 0];
+      shift = th0;
+    }
+    if (opts.use_prec) {
+      if (!(shift == cached_shift)) {
+        kq_valid = 0;
+        cached_shift = shift;
+      }
+      // singular shift: move it just below the kinetic spectrum's bottom
+      if (shift > op.lam_min_sum - 1e-12 * std::max(1.0, op.lam_max_sum)) {
+        if (std::fabs(shift - op.lam_min_sum) < 1e-10 * std::max(1.0, op.lam_max_sum))
+          shift = op.lam_min_sum - 1e-6 * std::max(1.0, op.lam_max_sum);
+      }
+    }
+    const int nq = nlock + nact2;
+    // K^-1 of newly locked columns is recomputed each time (kq_valid tracks the cache)
+    st = correction_impl(ctx, op, w.QX, nq, w.KQX, opts.use_prec ? std::min(kq_valid, nlock) : 0,
+                         w.R, w.theta, nact2, steps, opts.use_prec, shift, inner_tol,
+                         w.V + (long long)m * N, &stt.h_applies, &stt.prec_applies, s);
+    if (st) return st;
+    kq_valid = nlock;
+    stt.inner_steps += steps * nact2;
+    bn = nact2;
+  }
+  stt.outer_iters = outer;
+  // final Rayleigh quotients and residuals with a fresh H-apply of the locked vectors
+  const int nret = std::min(nlock, k);
+  if (nret > 0) {
+    double *HQ = w.V2;  // at least mmax >= nret columns
+    launch_apply_h(op, w.QX, HQ, nret, nullptr, 0.0, s);
+    stt.h_applies += nret;
+    launch_gram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nret, ctx->gscr, s);
+    col_norms2(c, w.QX, nret, w.ref);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta2, nret * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 64, w.ref, nret * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (int i = 0; i < nret; ++i) lam[i] = w.h_pinned[i] / w.h_pinned[64 + i];
+    // final residual norms ||H x - lambda x|| / ||H||_est
+    for (int i = 0; i < nret; ++i) w.h_pinned[128 + i] = lam[i];
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.theta2, w.h_pinned + 128, nret * sizeof(double),
+                                      cudaMemcpyHostToDevice, s));
+    launch_residual(nret, N, HQ, w.QX, w.theta2, w.HV2, s);
+    col_norms2(c, w.HV2, nret, w.ref);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 256, w.ref, nret * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (int i = 0; i < nret; ++i) resid[i] = std::sqrt(std::max(w.h_pinned[256 + i], 0.0)) / hnorm;
+    // sort ascending (locking order is ascending up to rounding within clusters)
+    std::vector<int> order(nret);
+    for (int i = 0; i < nret; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int bb) { return lam[a] < lam[bb]; });
+    // expand to the full grid in sorted order
+    for (int i = 0; i < nret; ++i) {
+      const double *src = w.QX + (long long)order[i] * N;
+      double *dst = evecs_dev + (long long)i * ctx->full.N;
+      if (parity != TPS_ANY)
+        launch_sector_expand(parity, ctx->n[0], ctx->n[1], 1, src, dst, s);
+      else
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      evals_host[i] = lam[order[i]];
+      if (i < 64) stt.resid[i] = resid[order[i]];
+    }
+    launch_fix_sign(nret, ctx->full.N, evecs_dev, s);
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    TPS_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  stt.n_converged = nret;
+  stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = stt;
+  if (!converged) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "outer-iteration cap reached");
+  return TPS_OK;
+}
+
+}  // namespace tps
+
+using namespace tps;
+
+extern "C" {
+
+void tps_default_opts(tps_solver_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->use_prec = 1;
+  o->prec_shift = NAN;
+  o->seed = 12345;
+}
+
+int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
+              int n_x0, const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
+              tps_stats *stats, cudaStream_t stream) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  if (!ctx->have_masses || !ctx->have_grid)
+    return set_error(ctx, TPS_ERR_NOT_CONFIGURED, "masses and grid must be set first");
+  if (k < 1 || k > 64 || block < 1 || block > 32 || !(tol > 0) || !evals_host || !evecs_dev ||
+      (parity != TPS_ANY && parity != TPS_X_EVEN && parity != TPS_X_ODD) || n_x0 < 0 ||
+      (n_x0 > 0 && !x0_dev))
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "bad solve arguments");
+  if (ctx->dim == 2 && parity != TPS_ANY)
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "2D supports TPS_ANY only");
+  cudaSetDevice(ctx->device);
+  return solve_impl(ctx, k, parity, tol, block, x0_dev, n_x0, opts, evals_host, evecs_dev, stats,
+                    stream);
+}
+
+int tps_orthonormalize(tps_ctx *ctx, const double *Q_dev, long long ldq, int nq, double *T_dev,
+                       long long ldt, int b, long long nrows, int *rank_host, cudaStream_t stream) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  if (b < 1 || b > 32 || nq < 0 || nq > 64 || nrows < 1 || ldq != nrows || ldt != nrows ||
+      !T_dev || !rank_host || (nq > 0 && !Q_dev))
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "bad orthonormalize arguments (ld must equal nrows)");
+  int st = alloc_workspace(ctx, nrows, std::max(nq, 2 * b), b, std::max(nq, 1), 1);
+  if (st) return st;
+  DevOperator dummy;
+  dummy.N = nrows;
+  Ctx c{ctx, dummy, *ctx->sw, stream, nrows};
+  return orthonormalize(c, Q_dev, nq, nullptr, 0, T_dev, b, rank_host);
+}
+
+int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_dev,
+                   const double *theta_dev, int nsys, int steps, int use_prec, double shift,
+                   double *T_dev, cudaStream_t stream) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  if (!ctx->have_masses || !ctx->have_grid)
+    return set_error(ctx, TPS_ERR_NOT_CONFIGURED, "masses and grid must be set first");
+  if (nsys < 1 || nsys > 32 || nq < 0 || nq > 96 || steps < 1 || steps > 40 || !R_dev ||
+      !theta_dev || !T_dev || (nq > 0 && !Qt_dev) || (use_prec && !std::isfinite(shift)))
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "bad correction arguments");
+  int st = alloc_workspace(ctx, ctx->full.N, 2 * nsys, nsys, std::max(nq - nsys, 1), steps);
+  if (st) return st;
+  if (ctx->sw->kmax + ctx->sw->b < nq) {
+    st = alloc_workspace(ctx, ctx->full.N, 2 * nsys, nsys, nq, steps);
+    if (st) return st;
+  }
+  int ha = 0, pa = 0;
+  st = correction_impl(ctx, ctx->full, Qt_dev, nq, nullptr, 0, R_dev, theta_dev, nsys, steps,
+                       use_prec, shift, 0.0, T_dev, &ha, &pa, stream);
+  if (st) return st;
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+  return TPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal declarations of the tps library: device operator description,
+// kernel launchers and the context.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tps.h"
+
+namespace tps {
+
+// ---------------------------------------------------------------------------
+// A discretised Kronecker-sum operator resident on the device:
+//   H = sum_k (I x .. x K_k x .. x I) + diag(V),  K_k = a_k D2_k (dense n_k x n_k),
+// with the orthonormal eigendecomposition K_k = S_k diag(lam_k) S_k^T used by the
+// preconditioner.  nmodes = 2 (1D) or 4 (2D); the vector layout is C order over
+// (n_0, .., n_{nmodes-1}).  The same struct describes the full grid and the
+// parity-reduced operators of the solver (mode 0 folded, Sec. 5.1).
+// ---------------------------------------------------------------------------
+struct DevOperator {
+  int nmodes = 0;
+  int n[4] = {0, 0, 0, 0};
+  long long N = 0;
+  double *K[4] = {nullptr, nullptr, nullptr, nullptr};   // row-major n x n
+  double *KT[4] = {nullptr, nullptr, nullptr, nullptr};  // K^T (equal to K for symmetric D2)
+  double *S[4] = {nullptr, nullptr, nullptr, nullptr};   // row-major, columns = eigenvectors
+  double *ST[4] = {nullptr, nullptr, nullptr, nullptr};  // S^T
+  double *lam[4] = {nullptr, nullptr, nullptr, nullptr}; // eigenvalues of K_k
+  double *V = nullptr;                                   // [N]
+  std::vector<double> lam_h[4];                          // host copies (singularity test)
+  double lam_min_sum = 0.0, lam_max_sum = 0.0;
+  bool owns = true;
+};
+
+// Workspace for one operator application (preconditioner intermediates).
+struct ApplyWorkspace {
+  double *t0 = nullptr, *t1 = nullptr;
+  long long capacity = 0;  // doubles per buffer
+};
+
+// ------------------------------- launchers ----------------------------------
+// out[v] = (H - theta_v) psi[v], theta_v = theta_dev ? theta_dev[v] : theta.
+void launch_apply_h(const DevOperator &op, const double *psi, double *out, int nvec,
+                    const double *theta_dev, double theta, cudaStream_t s);
+// out[v] = (T - sigma)^-1 r[v] by fast diagonalisation (needs 2 * nvec * N workspace).
+void launch_apply_prec(const DevOperator &op, const double *r, double *out, int nvec,
+                       double sigma, ApplyWorkspace &ws, cudaStream_t s);
+
+// Skinny block kernels.  Column c of block X is X + c*ldx; batch s adds s*bsx.
+struct GramScratch {
+  double *partial = nullptr;
+  long long capacity = 0;  // doubles
+};
+// G_s = A_s^T B_s (p x q, column-major ldg) for s < batch.
+void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
+                 long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
+                 long long bsg, int batch, GramScratch &scr, cudaStream_t s);
+// C_s = beta*C_s + alpha * A_s Y_s (Y column-major p x q, ldy, batch stride bsy).
+void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
+                   long long bsy, int q, double alpha, double beta, double *C, long long ldc,
+                   long long bsc, long long nrows, int batch, cudaStream_t s);
+
+// Small dense kernels (one CTA each).
+void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
+                        cudaStream_t s);
+// Cholesky G = R^T R of the b x b Gram matrix (ld b); writes Rinv (upper, ld b) and
+// keep[c] = 1 if column c has a pivot >= tol_rel * ref[c] (ref = squared column norms
+// before projection, device, may be null), else 0 (column dropped, Rinv column zero).
+void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,
+                     int *keep, cudaStream_t s);
+// Minv = M^-1 for an SPD q x q matrix (column-major, ld q).
+void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s);
+
+// Elementwise helpers.
+void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X, long long ldx,
+                       double beta, double *Y, long long ldy, cudaStream_t s);
+// Y[:, c] = X[:, c] * scale[c] (scale device); safe in place.
+void launch_scale_cols(int ncols, long long nrows, const double *X, long long ldx,
+                       const double *scale, int invert, double *Y, long long ldy, cudaStream_t s);
+// R[:, c] = HX[:, c] - theta[c] * X[:, c]
+void launch_residual(int ncols, long long nrows, const double *HX, const double *X,
+                     const double *theta, double *R, cudaStream_t s);
+// expand/restrict between the full 1D grid and a parity-reduced one.
+void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
+                            double *red, cudaStream_t s);
+void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
+                          double *full, cudaStream_t s);
+// flip the sign of each column so that its entry of largest magnitude is positive.
+void launch_fix_sign(int ncols, long long nrows, double *X, cudaStream_t s);
+
+// ------------------------------- context ------------------------------------
+struct SolverWorkspace;
+
+}  // namespace tps
+
+struct tps_ctx {
+  int device = 0;
+  int dim = 1;
+  bool have_masses = false, have_grid = false, have_V = false;
+  double a[2] = {0, 0};  // kinetic coefficient of x and y
+  int n[4] = {0, 0, 0, 0};
+  double L[4] = {0, 0, 0, 0};
+  std::vector<double> V_host;          // potential on the full grid
+  tps::DevOperator full;               // full grid operator
+  tps::DevOperator sect[3];            // [TPS_X_EVEN], [TPS_X_ODD] parity-reduced 1D operators
+  bool sect_ready[3] = {false, false, false};
+  tps::ApplyWorkspace ws;
+  tps::GramScratch gscr;
+  tps::SolverWorkspace *sw = nullptr;
+  std::string err;
+};
+
+namespace tps {
+// Error helpers used by the API layer.
+int set_error(tps_ctx *ctx, int code, const std::string &msg);
+int cuda_error(tps_ctx *ctx, cudaError_t e, const char *where);
+int ensure_apply_workspace(tps_ctx *ctx, long long doubles);
+int ensure_gram_scratch(tps_ctx *ctx, long long doubles);
+void free_operator(DevOperator &op);
+// Build the parity-reduced 1D operator for TPS_X_EVEN / TPS_X_ODD.
+int build_sector_operator(tps_ctx *ctx, int parity);
+int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0,
+               int n_x0, const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
+               tps_stats *stats, cudaStream_t stream);
+void free_solver_workspace(tps_ctx *ctx);
+long long gram_scratch_doubles(int p, int q, int batch);
+int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int nq,
+                    const double *KQt_cached, int nq_cached, const double *R,
+                    const double *theta, int nsys, int steps, int use_prec, double shift,
+                    double inner_tol, double *T, int *h_applies, int *prec_applies,
+                    cudaStream_t s);
+}  // namespace tps
+
+#define TPS_CUDA_TRY(ctx, expr)                                   \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return tps::cuda_error(ctx, _e, #expr); \
+  } while (0)

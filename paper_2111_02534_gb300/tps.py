@@ -1,0 +1,226 @@
+"""ctypes binding of the tps C ABI (include/tps.h): argument marshalling only.
+
+Every computation runs inside libtps.so (hand-written CUDA for sm_103a).  PyTorch
+supplies device memory (tensors' ``data_ptr()``) and streams; nothing else.
+Importing this module raises if the compiled library is missing: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtps.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"tps CUDA library not found at {LIB_PATH}; build it with "
+        "`python -m paper_2111_02534_gb300.build` (nvcc, sm_103a)")
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_NOT_CONFIGURED = -2
+ERR_CUDA = -3
+ERR_NOMEM = -4
+ERR_SINGULAR = -5
+ERR_NOT_CONVERGED = -6
+ERR_TIMEOUT = -7
+GAUSS, LORENTZ3 = 0, 1
+ANY, X_EVEN, X_ODD = 0, 1, 2
+F64 = 0
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("m_min", C.c_int), ("m_max", C.c_int), ("inner_steps", C.c_int),
+                ("max_outer", C.c_int), ("use_prec", C.c_int), ("prec_shift", C.c_double),
+                ("seed", C.c_ulonglong), ("inner_tol", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("h_applies", C.c_int), ("prec_applies", C.c_int),
+                ("inner_steps", C.c_int), ("restarts", C.c_int), ("n_converged", C.c_int),
+                ("hnorm_est", C.c_double), ("time_ms", C.c_double), ("resid", C.c_double * 64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "resid"}
+        d["resid"] = list(self.resid[: self.n_converged])
+        return d
+
+
+_vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+_ll = C.c_longlong
+_sig = {
+    "tps_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
+    "tps_destroy": (C.c_int, [_vp]),
+    "tps_last_error": (C.c_char_p, [_vp]),
+    "tps_status_string": (C.c_char_p, [C.c_int]),
+    "tps_set_masses": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "tps_set_alpha": (C.c_int, [_vp, C.c_double]),
+    "tps_set_grid": (C.c_int, [_vp, _ip, _dp]),
+    "tps_set_potential": (C.c_int, [_vp, _vp, C.c_int]),
+    "tps_set_pair_potential": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
+    "tps_two_body_v0": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                  C.c_double, C.c_int, C.c_double, _dp]),
+    "tps_get_info": (C.c_int, [_vp, C.POINTER(_ll), _dp]),
+    "tps_apply_h": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
+    "tps_apply_prec": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
+    "tps_default_opts": (None, [C.POINTER(SolverOpts)]),
+    "tps_solve": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_int, _vp, C.c_int,
+                            C.POINTER(SolverOpts), _dp, _vp, C.POINTER(Stats), _vp]),
+    "tps_gram": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
+    "tps_block_update": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, C.c_int, C.c_int, C.c_double,
+                                   _vp, _ll, _ll, _vp]),
+    "tps_orthonormalize": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _ip, _vp]),
+    "tps_small_eigh": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp]),
+    "tps_correction": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int,
+                                 C.c_double, _vp, _vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class TpsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.tps_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def default_opts() -> SolverOpts:
+    o = SolverOpts()
+    _lib.tps_default_opts(C.byref(o))
+    return o
+
+
+def two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L) -> float:
+    out = C.c_double()
+    st = _lib.tps_two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L, C.byref(out))
+    if st != OK:
+        raise TpsError(st, "tps_two_body_v0")
+    return out.value
+
+
+class Context:
+    """Owns one tps_ctx.  Tensors passed in must be contiguous float64 CUDA tensors."""
+
+    def __init__(self, dim: int, device: int = 0):
+        h = C.c_void_p()
+        st = _lib.tps_create(C.byref(h), dim, device)
+        if st != OK:
+            raise TpsError(st, "tps_create")
+        self._h = h
+        self.dim = dim
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tps_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st, what):
+        if st != OK:
+            raise TpsError(st, f"{what}: {_lib.tps_last_error(self._h).decode()}")
+
+    # ---- problem definition -------------------------------------------------
+    def set_masses(self, M, m, hbar=1.0):
+        self._check(_lib.tps_set_masses(self._h, M, m, hbar), "set_masses")
+
+    def set_alpha(self, alpha):
+        self._check(_lib.tps_set_alpha(self._h, alpha), "set_alpha")
+
+    def set_grid(self, n, L):
+        na = (C.c_int * len(n))(*n)
+        La = (C.c_double * len(L))(*L)
+        self._check(_lib.tps_set_grid(self._h, na, La), "set_grid")
+
+    def set_potential(self, V):
+        """V: float64 tensor of N entries (host or device) or a numpy array (host)."""
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            self._check(_lib.tps_set_potential(self._h, V.ctypes.data_as(C.c_void_p), 0),
+                        "set_potential")
+        else:
+            self._check(_lib.tps_set_potential(self._h, _ptr(V), 1 if V.is_cuda else 0),
+                        "set_potential")
+
+    def set_pair_potential(self, shape, v0, sigma):
+        self._check(_lib.tps_set_pair_potential(self._h, shape, v0, sigma), "set_pair_potential")
+
+    def info(self):
+        N = C.c_longlong()
+        h = C.c_double()
+        self._check(_lib.tps_get_info(self._h, C.byref(N), C.byref(h)), "get_info")
+        return N.value, h.value
+
+    # ---- operator applications -------------------------------------------------
+    def apply_h(self, psi, out, theta=0.0, stream=None):
+        nvec = psi.numel() // self.info()[0]
+        self._check(_lib.tps_apply_h(self._h, _ptr(psi), _ptr(out), nvec, theta, F64,
+                                     _stream(stream)), "apply_h")
+
+    def apply_prec(self, r, out, theta, stream=None):
+        nvec = r.numel() // self.info()[0]
+        self._check(_lib.tps_apply_prec(self._h, _ptr(r), _ptr(out), nvec, theta, F64,
+                                        _stream(stream)), "apply_prec")
+
+    # ---- solver -----------------------------------------------------------------
+    def solve(self, k, parity, tol, block, evecs, x0=None, opts=None, stream=None,
+              allow_not_converged=False):
+        """Returns (evals numpy [k], Stats); eigenvectors written into ``evecs`` [k, N]."""
+        ev = (C.c_double * k)()
+        stats = Stats()
+        n_x0 = 0 if x0 is None else x0.numel() // self.info()[0]
+        st = _lib.tps_solve(self._h, k, parity, tol, block, _ptr(x0), n_x0,
+                            C.byref(opts) if opts is not None else None, ev, _ptr(evecs),
+                            C.byref(stats), _stream(stream))
+        if st != OK and not (allow_not_converged and st == ERR_NOT_CONVERGED):
+            self._check(st, "solve")
+        return np.array(ev[: stats.n_converged]), stats
+
+    # ---- building blocks ----------------------------------------------------------
+    def gram(self, A, p, B, q, nrows, G, ldg=None, lda=None, ldb=None, stream=None):
+        self._check(_lib.tps_gram(self._h, _ptr(A), lda or nrows, p, _ptr(B), ldb or nrows, q,
+                                  nrows, _ptr(G), ldg or p, _stream(stream)), "gram")
+
+    def block_update(self, A, p, Y, q, beta, Cm, nrows, ldy=None, stream=None):
+        self._check(_lib.tps_block_update(self._h, _ptr(A), nrows, p, _ptr(Y), ldy or p, q, beta,
+                                          _ptr(Cm), nrows, nrows, _stream(stream)), "block_update")
+
+    def orthonormalize(self, Q, nq, T, b, nrows, stream=None):
+        rank = C.c_int()
+        self._check(_lib.tps_orthonormalize(self._h, _ptr(Q), nrows, nq, _ptr(T), nrows, b, nrows,
+                                            C.byref(rank), _stream(stream)), "orthonormalize")
+        return rank.value
+
+    def small_eigh(self, G, m, theta, Y, stream=None):
+        self._check(_lib.tps_small_eigh(self._h, _ptr(G), m, m, _ptr(theta), _ptr(Y), m,
+                                        _stream(stream)), "small_eigh")
+
+    def correction(self, Qt, nq, R, theta, nsys, steps, use_prec, shift, T, stream=None):
+        self._check(_lib.tps_correction(self._h, _ptr(Qt), nq, _ptr(R), _ptr(theta), nsys, steps,
+                                        use_prec, shift if use_prec else math.nan, _ptr(T),
+                                        _stream(stream)), "correction")

@@ -1,0 +1,178 @@
+"""GPU parity of the H-apply (Eq. tensor_op1D / tensor_op2D) and the preconditioner
+(Sec. 4.2) against the oracle, element by element, through the C ABI.
+
+Tolerances (derived from FP64 rounding of a length-n dot product with entries of size
+up to |a|(pi/h)^2): H psi to 1e-12 of ||H||_est ||psi|| norm-wise (and 1e-13 of
+||H||_est max|psi| per element); preconditioner outputs to 1e-11 relative norm-wise.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import torch, require_gpu, make_ctx_1d, make_ctx_2d, dev, host
+from oracle.hamiltonian import problem_1d, problem_2d
+from oracle.precond import apply_dense, apply_sylvester, kinetic_residual
+from paper_2111_02534_gb300.inputs import random_block, WORKLOADS
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_h(P, ctx, nvec, theta, seed, rows=None):
+    psi = random_block(nvec, P.N, seed)
+    out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_h(dev(psi), out, theta)
+    got = host(out)
+    hn = P.norm_estimate()
+    if rows is None:
+        ref = P.apply_kron(psi, theta)
+        err = np.linalg.norm(got - ref, axis=1) / (hn * np.linalg.norm(psi, axis=1))
+        assert err.max() <= 1e-12, err.max()
+        assert np.max(np.abs(got - ref)) <= 1e-13 * hn * np.abs(psi).max() * 10
+    else:
+        for v in range(nvec):
+            ref = P.apply_rows(psi[v], rows, theta)
+            assert np.max(np.abs(got[v][rows] - ref)) <= 1e-13 * hn * np.abs(psi[v]).max() * 10
+    return got, psi
+
+
+@pytest.mark.parametrize("n,nvec,theta", [((64, 64), 4, 0.0), ((100, 70), 3, -0.37),
+                                          ((12, 8), 5, 0.5), ((130, 200), 2, 1.25),
+                                          ((4, 4), 1, 0.0)])
+def test_apply_h_1d(n, nvec, theta):
+    require_gpu()
+    P = problem_1d(20.0, 1.0, 1.0, n, (20.0, 15.0), 1.0, 1.0)
+    ctx = make_ctx_1d(20.0, 1.0, n, (20.0, 15.0), 1.0, 1.0)
+    assert ctx.info()[0] == P.N
+    assert ctx.info()[1] == pytest.approx(P.norm_estimate(), rel=1e-13)
+    _check_h(P, ctx, nvec, theta, seed=hash(n) % 1000)
+
+
+def test_apply_h_1d_dense_assembly():
+    require_gpu()
+    n = (10, 6)
+    P = problem_1d(40.0, 1.0, 1.0, n, (3.0, 4.0), 0.7, 1.3, shape=1)
+    ctx = make_ctx_1d(40.0, 1.0, n, (3.0, 4.0), 0.7, 1.3, shape=1)
+    psi = random_block(2, P.N, 7)
+    out = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_h(dev(psi), out, 0.25)
+    ref = psi @ (P.assemble_dense() - 0.25 * np.eye(P.N)).T
+    assert np.max(np.abs(host(out) - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_apply_h_1d_full_size_sampled_rows():
+    # the 1d_n512 workload size, in the launch configuration the bench times (8 vectors)
+    require_gpu()
+    w = WORKLOADS["1d_n512"]
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, 0.05, w.sigma)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, 0.05, w.sigma)
+    rows = np.random.default_rng(0).choice(P.N, 96, replace=False)
+    rows = np.concatenate([rows, [0, P.N - 1, 511, 512 * 511]])
+    got, psi = _check_h(P, ctx, 8, 0.0, seed=11, rows=rows)
+    # whole vectors against the Kronecker apply as well
+    ref = P.apply_kron(psi[:2])
+    err = np.linalg.norm(got[:2] - ref, axis=1) / (P.norm_estimate() * np.linalg.norm(psi[:2], axis=1))
+    assert err.max() <= 1e-12
+
+
+def test_apply_h_user_potential_and_alpha_units():
+    require_gpu()
+    n = (32, 24)
+    V = np.random.default_rng(3).uniform(-2, 1, size=n)
+    P = problem_1d(None, None, None, n, (6.0, 5.0), 0, 1, V=V, alpha=20.0)
+    ctx = make_ctx_1d(None, None, n, (6.0, 5.0), 0, 1, alpha=20.0, V=V)
+    _check_h(P, ctx, 3, -0.1, seed=5)
+
+
+@pytest.mark.parametrize("n,nvec", [((8, 8, 6, 6), 2), ((6, 6, 10, 10), 3), ((12, 12, 8, 8), 1)])
+def test_apply_h_2d(n, nvec):
+    require_gpu()
+    L = (5.0, 5.0, 4.0, 4.0)
+    P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+    ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    _check_h(P, ctx, nvec, -0.2, seed=sum(n))
+    if P.N <= 4096:
+        psi = random_block(1, P.N, 1)
+        out = torch.empty(1, P.N, dtype=torch.float64, device="cuda")
+        ctx.apply_h(dev(psi), out, 0.0)
+        ref = psi @ P.assemble_dense().T
+        assert np.max(np.abs(host(out) - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_apply_h_2d_full_size():
+    # the 2d_n48 workload (5.3 M unknowns) on 2 vectors; whole-vector comparison
+    require_gpu()
+    w = WORKLOADS["2d_n48"]
+    P = problem_2d(w.M, w.m, w.hbar, w.n, w.L, w.v0, w.sigma)
+    ctx = make_ctx_2d(w.M, w.m, w.n, w.L, w.v0, w.sigma)
+    rows = np.random.default_rng(1).choice(P.N, 64, replace=False)
+    _check_h(P, ctx, 2, 0.0, seed=21, rows=rows)
+
+
+def test_apply_h_empty_and_errors():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    ctx = make_ctx_1d(20.0, 1.0, (8, 8), (3.0, 3.0), 1.0, 1.0)
+    x = torch.zeros(0, dtype=torch.float64, device="cuda")
+    ctx.apply_h(x, x, 0.0)        # nvec = 0 is a no-op
+    a = torch.zeros(2, 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(tps.TpsError):
+        ctx.apply_h(a, a, 0.0)    # aliasing rejected
+    with pytest.raises(tps.TpsError) as e:
+        ctx.apply_prec(a, torch.empty_like(a), 0.0)   # shift 0 hits the k = 0 kinetic mode
+    assert e.value.status == tps.ERR_SINGULAR
+
+
+@pytest.mark.parametrize("n,nvec,theta", [((64, 64), 3, -0.5), ((100, 70), 2, -1.3),
+                                          ((12, 8), 4, -0.05), ((130, 200), 1, -2.0)])
+def test_apply_prec_1d(n, nvec, theta):
+    require_gpu()
+    L = (20.0, 15.0)
+    P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+    ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    r = random_block(nvec, P.N, seed=nvec)
+    out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, theta)
+    got = host(out)
+    ref = apply_sylvester(P, r, theta)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-11, err.max()
+    if P.N <= 2000:
+        assert np.max(np.abs(got - apply_dense(P, r, theta))) <= 1e-11 * np.abs(ref).max()
+
+
+def test_apply_prec_1d_full_size():
+    require_gpu()
+    w = WORKLOADS["1d_n512"]
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, 0.05, w.sigma)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, 0.05, w.sigma)
+    r = random_block(8, P.N, seed=3)
+    out = torch.empty(8, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, -1e-3)
+    got = host(out)
+    ref = apply_sylvester(P, r[:1], -1e-3)
+    assert np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0]) <= 1e-11
+    assert kinetic_residual(P, got, r, -1e-3) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [(6, 6, 4, 4), (8, 8, 6, 6)])
+def test_apply_prec_2d_dense(n):
+    require_gpu()
+    L = (4.0, 4.0, 3.0, 3.0)
+    P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+    ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    r = random_block(2, P.N, seed=2)
+    out = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, -0.4)
+    ref = apply_dense(P, r, -0.4)
+    got = host(out)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+def test_apply_prec_2d_full_size_property():
+    require_gpu()
+    w = WORKLOADS["2d_n48"]
+    P = problem_2d(w.M, w.m, w.hbar, w.n, w.L, w.v0, w.sigma)
+    ctx = make_ctx_2d(w.M, w.m, w.n, w.L, w.v0, w.sigma)
+    r = random_block(2, P.N, seed=4)
+    out = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, -0.3)
+    assert kinetic_residual(P, host(out), r, -0.3) <= 1e-11

@@ -1,0 +1,145 @@
+"""GPU parity of the Jacobi-Davidson building blocks (Sec. 4.1) through the C ABI:
+Gram matrices, block updates, the device Jacobi eigensolver, block orthonormalisation
+and the preconditioned GMRES correction solve, against oracle.blocks definitions."""
+import numpy as np
+import pytest
+
+from gpu_common import torch, require_gpu, make_ctx_1d, dev, host
+from oracle import blocks
+from oracle.hamiltonian import problem_1d, Problem
+from oracle.precond import apply_dense
+from paper_2111_02534_gb300.inputs import random_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    return make_ctx_1d(20.0, 1.0, (8, 8), (3.0, 3.0), 1.0, 1.0)
+
+
+@pytest.mark.parametrize("nrows,p,q", [(131584, 24, 8), (1000003, 5, 1), (4097, 64, 64),
+                                       (257, 1, 1), (0, 3, 2)])
+def test_gram(ctx, nrows, p, q):
+    A = random_block(p, nrows, 1)
+    B = random_block(q, nrows, 2)
+    G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")   # column-major p x q
+    ctx.gram(dev(A), p, dev(B), q, nrows, G)
+    got = host(G).T
+    ref = A @ B.T
+    scale = max(1.0, np.sqrt(nrows))
+    assert np.max(np.abs(got - ref)) <= 1e-14 * scale * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nrows,p,q,beta", [(131584, 24, 8, 0.0), (100003, 70, 3, 1.0),
+                                            (513, 1, 17, -0.5), (1000, 0, 4, 2.0)])
+def test_block_update(ctx, nrows, p, q, beta):
+    A = random_block(max(p, 1), nrows, 3)[:p]
+    Y = np.random.default_rng(4).standard_normal((p, q))
+    C0 = random_block(q, nrows, 5)
+    Cd = dev(C0)
+    if p > 64:
+        from paper_2111_02534_gb300 import tps
+        with pytest.raises(tps.TpsError):
+            ctx.block_update(dev(A), p, dev(Y.T.copy()), q, beta, Cd, nrows)
+        return
+    ctx.block_update(dev(A) if p else None, p, dev(Y.T.copy()) if p else None, q, beta, Cd, nrows,
+                     ldy=max(p, 1))
+    ref = beta * C0 + (Y.T @ A if p else 0.0)
+    assert np.max(np.abs(host(Cd) - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("m,kind", [(1, "rand"), (7, "rand"), (32, "rand"), (64, "rand"),
+                                    (40, "cluster"), (33, "graded")])
+def test_small_eigh(ctx, m, kind):
+    rng = np.random.default_rng(m)
+    if kind == "rand":
+        A = rng.standard_normal((m, m))
+        A = A + A.T
+    else:
+        Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        if kind == "cluster":
+            d = np.repeat(np.array([-3.0, -1e-3, 0.0, 1e-12, 2.0]), m // 5 + 1)[:m] + 1e-14 * rng.standard_normal(m)
+        else:
+            d = np.logspace(-12, 3, m) * np.where(np.arange(m) % 2, -1, 1)
+        A = (Q * d) @ Q.T
+        A = 0.5 * (A + A.T)
+    th = torch.empty(m, dtype=torch.float64, device="cuda")
+    Y = torch.empty(m, m, dtype=torch.float64, device="cuda")
+    ctx.small_eigh(dev(A.T.copy()), m, th, Y)
+    w, Yh = host(th), host(Y).T          # Y is column-major
+    ref = np.linalg.eigvalsh(A)
+    nrm = np.linalg.norm(A, 2)
+    assert np.all(np.diff(w) >= 0)
+    assert np.max(np.abs(w - ref)) <= 1e-14 * nrm * m
+    assert np.max(np.abs(Yh.T @ Yh - np.eye(m))) <= 1e-13 * m
+    assert np.max(np.abs(A @ Yh - Yh * w)) <= 1e-14 * nrm * m
+
+
+def test_orthonormalize(ctx):
+    nrows = 50000
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.standard_normal((nrows, 6)))
+    T = rng.standard_normal((nrows, 5))
+    T[:, 3] = 2 * T[:, 0] - T[:, 1] + 1e-12 * rng.standard_normal(nrows)  # dependent column
+    T[:, 4] = Q[:, 2] * 3.0                                                # inside span(Q)
+    Td = dev(T.T.copy())
+    rank = ctx.orthonormalize(dev(Q.T.copy()), 6, Td, 5, nrows)
+    assert rank == 3
+    Z = host(Td)[:rank].T
+    assert np.max(np.abs(Z.T @ Z - np.eye(rank))) <= 1e-13
+    assert np.max(np.abs(Q.T @ Z)) <= 1e-13
+    ref = blocks.orthonormal_complement_step(Q, T[:, :3])
+    # same subspace as the Householder definition
+    assert np.linalg.norm(ref @ (ref.T @ Z) - Z) <= 1e-10
+
+
+@pytest.mark.parametrize("use_prec", [1, 0])
+def test_correction_full_krylov_is_exact(use_prec):
+    # steps >= dimension of the complement: GMRES solves Eq. jdcor exactly
+    require_gpu()
+    n = (6, 6)
+    P = problem_1d(20.0, 1.0, 1.0, n, (3.0, 3.0), 1.0, 1.0)
+    c = make_ctx_1d(20.0, 1.0, n, (3.0, 3.0), 1.0, 1.0)
+    H = P.assemble_dense()
+    w, U = np.linalg.eigh(H)
+    rng = np.random.default_rng(1)
+    X = U[:, :2] + 1e-2 * rng.standard_normal((P.N, 2))
+    Qt, _ = np.linalg.qr(X)
+    th = np.array([Qt[:, i] @ H @ Qt[:, i] for i in range(2)])
+    R = H @ Qt - Qt * th
+    R = R - Qt @ (Qt.T @ R)
+    T = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
+    c.correction(dev(Qt.T.copy()), 2, dev(R.T.copy()), dev(th), 2, P.N - 2, use_prec, -0.7, T)
+    got = host(T)
+    for i in range(2):
+        ref = blocks.correction_exact(H, Qt, th[i], R[:, i])
+        assert np.linalg.norm(got[i] - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_correction_matches_textbook_gmres():
+    # a few steps: same Krylov space and minimisation as the oracle's textbook GMRES
+    require_gpu()
+    n = (10, 8)
+    L = (4.0, 4.0)
+    P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+    c = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    H = P.assemble_dense()
+    w, U = np.linalg.eigh(H)
+    rng = np.random.default_rng(2)
+    Qt, _ = np.linalg.qr(U[:, :3] + 1e-2 * rng.standard_normal((P.N, 3)))
+    th = np.array([Qt[:, i] @ H @ Qt[:, i] for i in range(3)])
+    R = H @ Qt - Qt * th
+    shift, steps = -0.9, 6
+    T = torch.empty(3, P.N, dtype=torch.float64, device="cuda")
+    c.correction(dev(Qt.T.copy()), 3, dev(R.T.copy()), dev(th), 3, steps, 1, shift, T)
+    got = host(T)
+    Kinv = lambda Y: apply_dense(P, np.asarray(Y).T, shift).T
+    Pm = np.eye(P.N) - Qt @ Qt.T
+    for i in range(3):
+        A = lambda v: blocks.projected_preconditioner(Kinv, Qt, Pm @ ((H - th[i] * np.eye(P.N)) @ (Pm @ v)))
+        b = -blocks.projected_preconditioner(Kinv, Qt, R[:, i])
+        x, _ = blocks.gmres(A, b, steps)
+        assert np.linalg.norm(got[i] - x) <= 1e-9 * np.linalg.norm(x)
+        assert abs(Qt.T @ got[i]).max() <= 1e-10 * np.linalg.norm(got[i])

@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 three-body eigensolver (arXiv 2111.02534 hot path).
+
+One step = one tps_solve of the 1D workload with n = 512 points per Jacobi coordinate
+(M/m = 40, v0 tuned to a heavy-light binding of 1e-3, 8 lowest heavy-exchange-even
+eigenpairs, block size 8, FP64): every row of the hot path runs inside it (H-apply,
+preconditioner, projectors, GMRES, block orthogonalisation, Rayleigh-Ritz, restarts).
+
+metric  eigenpairs/sec counting only pairs whose eigenvalue is within 1e-10 relative of
+        the oracle's (tests/golden/evals_1d_n512.json, written by oracle-only code);
+        the H-apply / mode-product throughput is reported in ``roofline``.
+Multi-GPU: replicas only (one independent solve per rank, no collective on the data
+path); value = pairs of all ranks / max-over-ranks time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/sec at rel. eigenvalue err ≤1e-10; H-apply TFLOP/s vs peak"
+UNIT = "eigenpairs/s"
+WORKLOAD = "1d_n512"
+REL_TOL = 1e-10
+# FP64 FMA peak: 2 FP64 FMA units' worth of work per SM per clock (4 flop/clk/SM, the
+# nominal 1.25 TFLOP/s of GB300 at 152 SMs x 2070 MHz; a throughput probe reached 95 %)
+FP64_FLOP_PER_CLK_PER_SM = 4
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# DRAM bytes per k_gemm_f64 launch from the ncu capture summarised in
+# profiles/k_gemm_f64_1d_n512.md (None until a capture of the current kernel exists)
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def aggregate(local_seconds, local_pairs, world, device=None):
+    """Max time over ranks and total passing pairs (all-reduce when world > 1)."""
+    if world == 1:
+        return local_seconds, local_pairs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    p = torch.tensor([float(local_pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(p.item()))
+
+
+def golden():
+    with open(os.path.join(ROOT, "tests", "golden", f"evals_{WORKLOAD}.json")) as f:
+        return json.load(f)
+
+
+def passing_pairs(lam, ref):
+    lam = np.asarray(lam)
+    n = min(len(lam), len(ref))
+    rel = np.abs(lam[:n] - ref[:n]) / np.abs(ref[:n])
+    return int(np.sum(rel <= REL_TOL)), float(rel.max()) if n else float("inf")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(w, v0):
+    """The oracle as it stands on this host: LOBPCG for the lowest eigenpair of the same
+    workload (a bounded sample of the 8-pair solve).  Returns (pairs/s, seconds, cores)."""
+    from oracle.hamiltonian import problem_1d
+    from oracle.eig import lowest_iterative
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, v0, w.sigma)
+    t0 = time.perf_counter()
+    lam, _ = lowest_iterative(P, 1, 1, tol=1e-12, extra=2)
+    dt = time.perf_counter() - t0
+    ref = golden()["evals"][0]
+    ok = abs(lam[0] - ref) / abs(ref) <= REL_TOL
+    return (1.0 if ok else 0.0) / dt, dt, os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2111_02534_gb300.inputs import WORKLOADS
+    w = WORKLOADS[WORKLOAD]
+    v0 = golden()["v0"]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, v0)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt, cores = cpu_oracle_sample(w, v0)
+        vals.append(v)
+        secs.append(dt)
+    total = sum(secs)
+    value = args.steps / total if all(x > 0 for x in vals) else 0.0
+    sample = ("oracle (NumPy/SciPy FP64, LOBPCG on the explicit Kronecker sum) computing the "
+              "lowest x-even eigenpair of the n=512 workload per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: M/m=40, n=512x512 on [-20,20)^2, E0=1e-3, sigma=1, "
+                               "x-even, 1 lowest pair per step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for --impl ours")
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    from paper_2111_02534_gb300 import tps
+    from paper_2111_02534_gb300.inputs import WORKLOADS, random_normal_block
+
+    w = WORKLOADS[WORKLOAD]
+    gold = golden()
+    ref = np.array(gold["evals"])
+    mu_hl = w.M * w.m / (w.M + w.m)
+    v0 = tps.two_body_v0(1, mu_hl, w.hbar, w.E0, tps.GAUSS, w.sigma, w.n[1], w.L[1])
+    ctx = tps.Context(1, local)
+    ctx.set_masses(w.M, w.m, w.hbar)
+    ctx.set_grid(list(w.n), list(w.L))
+    ctx.set_pair_potential(tps.GAUSS, v0, w.sigma)
+    N, hnorm = ctx.info()
+    stream = torch.cuda.current_stream()
+    x0 = torch.from_numpy(random_normal_block(w.block, N, seed=1000 + rank)).cuda()
+    evecs = torch.empty(w.k, N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    opts = tps.default_opts()
+    opts.timing = 1
+
+    def step():
+        lam, st = ctx.solve(w.k, tps.X_EVEN, 1e-12, w.block, evecs, x0=x0, opts=opts,
+                            stream=stream)
+        return lam, st
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times, stats, pairs, rel_max = [], [], 0, 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # L2 flushed between timed steps
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            lam, st = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1000.0)
+            stats.append(st)
+            p, r = passing_pairs(lam, ref)
+            pairs += p
+            rel_max = max(rel_max, r)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    local_t = sum(times)
+    T, total_pairs = aggregate(local_t, pairs, world, device="cuda")
+    value = total_pairs / T
+
+    # end to end through the public API with host buffers: every step sets the potential
+    # (the library evaluates it and uploads N doubles), copies the start block from pinned
+    # host memory, solves, and reads eigenvectors and eigenvalues back to the host
+    x0_host = x0.cpu().pin_memory()
+    x0_dev = torch.empty_like(x0)
+    evecs_host = torch.empty(w.k, N, dtype=torch.float64).pin_memory()
+    e2e_t, e2e_pairs = 0.0, 0
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    for _ in range(n_e2e):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_pair_potential(tps.GAUSS, v0, w.sigma)
+        x0_dev.copy_(x0_host, non_blocking=True)
+        lam, st = ctx.solve(w.k, tps.X_EVEN, 1e-12, w.block, evecs, x0=x0_dev, opts=opts,
+                            stream=stream)
+        evecs_host.copy_(evecs, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t += time.perf_counter() - t0
+        e2e_pairs += passing_pairs(lam, ref)[0]
+    E_T, E_pairs = aggregate(e2e_t, e2e_pairs, world, device="cuda")
+    h2d = 8 * N + 8 * w.block * N
+    d2h = 8 * w.k * N + 8 * w.k
+
+    # roofline of the dominant kernel (k_gemm_f64: every mode product of the H and
+    # preconditioner applications), from the solver's own CUDA-event timers
+    fl = sum(st.h_flops + st.prec_flops for st in stats)
+    ms = sum(st.h_ms + st.prec_ms for st in stats)
+    achieved = fl / (ms / 1000.0) / 1e12
+    clocks = clk.summary()
+    peak = N_SM * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    h_tf = sum(st.h_flops for st in stats) / (sum(st.h_ms for st in stats) / 1000.0) / 1e12
+    gemm_launches = sum(st.h_launches + 4 * st.prec_launches for st in stats)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = cpu_oracle_sample(w, gold["v0"])
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle LOBPCG (NumPy/SciPy FP64) for the lowest x-even eigenpair of "
+                         f"the same n=512 workload, {dt:.1f} s on the host"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1000.0 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 1D heavy-heavy-light, M/m=40, n=512 per Jacobi "
+                                   "coordinate on [-20,20), v0 tuned to E0=1e-3, sigma=1, 8 lowest "
+                                   "x-even eigenpairs, block 8, tol 1e-12*||H||",
+                       "parallelism": f"replicas x{world}", "l2": "flushed between timed steps",
+                       "unknowns": N, "sector_unknowns": (w.n[0] // 2 + 1) * w.n[1]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "traffic": GEMM_TRAFFIC_BYTES_PER_LAUNCH,
+                         "kernel": "k_gemm_f64 (H-apply and preconditioner mode products)",
+                         "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz",
+                         "h_apply_tflops": h_tf, "launches": gemm_launches},
+            "e2e": {"value": E_pairs / E_T, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": n_e2e},
+            "clocks": clocks,
+            "gpu_launches": int(sum(st.kernel_launches for st in stats)),
+            "eigen_rel_err_max": rel_max, "pairs_passing": total_pairs,
+            "solver": {"outer_iters": stats[-1].outer_iters, "h_applies": stats[-1].h_applies,
+                       "prec_applies": stats[-1].prec_applies, "restarts": stats[-1].restarts},
+            "wall_s": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -130,10 +130,17 @@ typedef struct tps_solver_opts {
   int inner_steps;    /* GMRES steps per correction equation (0: 10; Sec. 4.1) */
   int max_outer;      /* outer-iteration cap (0: 500) */
   int use_prec;       /* 1: prec-JDQR (Sec. 4.2 preconditioner), 0: no-prec-JDQR */
-  double prec_shift;  /* fixed preconditioner shift; NaN: lowest active Ritz value each iteration */
+  double prec_shift;  /* fixed preconditioner shift (the paper's -E0); NaN: adaptive, -|theta| of
+                         the lowest active Ritz value (kept below the kinetic spectrum) */
   unsigned long long seed; /* start block when x0 is NULL (counter-based normal deviates) */
   double inner_tol;   /* GMRES stops a system when its preconditioned residual drops by this
                          factor (0: 1e-3) */
+  int timing;         /* 1: time every H and preconditioner application with CUDA events on
+                         the solve's stream (tps_stats h_ms / prec_ms) */
+  int guard;          /* extra eigenpairs converged beyond k and discarded, so that a state
+                         absent from the early search space is not skipped (default 2) */
+  int smooth_start;   /* applications of the kinetic preconditioner (shift -1e-3 ||H||_est) to
+                         the random part of the start block, a low-pass filter (default 2) */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -145,6 +152,13 @@ typedef struct tps_stats {
   int n_converged;    /* pairs returned */
   double hnorm_est;
   double time_ms;     /* wall time of tps_solve */
+  double h_ms;        /* with opts.timing: device time of the H applications */
+  double prec_ms;     /* with opts.timing: device time of the preconditioner applications */
+  double h_flops;     /* algorithmic FP64 flops of the H applications (2N(sum n_k) + 3N each) */
+  double prec_flops;  /* algorithmic flops of the preconditioner applications (4N(sum n_k) + N) */
+  long long h_launches;      /* H-application launches (each over a block of vectors) */
+  long long prec_launches;   /* preconditioner-application launches */
+  long long kernel_launches; /* all CUDA kernels launched by this call */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

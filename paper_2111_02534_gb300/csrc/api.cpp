@@ -16,6 +16,8 @@
 
 namespace tps {
 
+std::atomic<long long> g_kernel_launches{0};
+
 int set_error(tps_ctx *ctx, int code, const std::string &msg) {
   if (ctx) ctx->err = msg;
   return code;
@@ -619,7 +621,7 @@ int tps_gram(tps_ctx *ctx, const double *A_dev, long long lda, int p, const doub
              long long ldb, int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream) {
   if (!ctx) return TPS_ERR_INVALID_ARG;
   if (p < 1 || q < 1 || p > 64 || q > 64 || nrows < 0 || lda < nrows || ldb < nrows || ldg < p ||
-      !A_dev || !B_dev || !G_dev)
+      !G_dev || (nrows > 0 && (!A_dev || !B_dev)))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad gram arguments");
   launch_gram(A_dev, lda, 0, p, B_dev, ldb, 0, q, nrows, G_dev, ldg, 0, 1, ctx->gscr, stream);
   TPS_CUDA_TRY(ctx, cudaGetLastError());

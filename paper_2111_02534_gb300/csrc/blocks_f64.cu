@@ -500,8 +500,10 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
   const long long cap = scr.capacity / ((long long)batch * npb * 16);
   if (nchunk > cap) nchunk = (int)(cap > 0 ? cap : 1);
   dim3 grid(nchunk, batch, npb);
+  count_launch();
   k_gram_partial<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial);
   const long long total = (long long)batch * p * q;
+  count_launch();
   k_gram_reduce<<<grid_for(total), 256, 0, s>>>(scr.partial, p, q, nchunk, batch, G, ldg, bsg);
 }
 
@@ -510,15 +512,18 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
                    long long bsc, long long nrows, int batch, cudaStream_t s) {
   if (q <= 0 || batch <= 0 || nrows <= 0) return;
   if (p <= 0) {  // C = beta * C
-    for (int b = 0; b < batch; ++b)
+    for (int b = 0; b < batch; ++b) {
+      count_launch();
       k_axpby_cols<<<grid_for((long long)q * nrows), 256, 0, s>>>(q, nrows, 0.0, C + b * bsc, ldc,
                                                                 beta, C + b * bsc, ldc);
+    }
     return;
   }
   // p is processed in slabs of 64 rows of Y; the first slab applies beta
   for (int i0 = 0; i0 < p; i0 += 64) {
     const int pp = p - i0 < 64 ? p - i0 : 64;
     dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + 7) / 8);
+    count_launch();
     k_update<<<grid, GT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha,
                                  i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows);
   }
@@ -532,11 +537,13 @@ void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *
     cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  count_launch();
   k_jacobi<<<1, 512, smem, s>>>(G, m, ldg, theta, Y, ldy);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,
                      int *keep, cudaStream_t s) {
+  count_launch();
   k_chol_inv<<<1, 32, 0, s>>>(G, b, ref, tol_rel, Rinv, keep);
 }
 
@@ -548,12 +555,14 @@ void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s) {
                          2 * 96 * 96 * (int)sizeof(double));
     attr = true;
   }
+  count_launch();
   k_spd_inverse<<<1, 128, smem, s>>>(M, q, Minv);
 }
 
 void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X, long long ldx,
                        double beta, double *Y, long long ldy, cudaStream_t s) {
   if (ncols <= 0 || nrows <= 0) return;
+  count_launch();
   k_axpby_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, alpha, X, ldx,
                                                                    beta, Y, ldy);
 }
@@ -561,6 +570,7 @@ void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X
 void launch_scale_cols(int ncols, long long nrows, const double *X, long long ldx,
                        const double *scale, int invert, double *Y, long long ldy, cudaStream_t s) {
   if (ncols <= 0 || nrows <= 0) return;
+  count_launch();
   k_scale_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, X, ldx, scale,
                                                                    invert, Y, ldy);
 }
@@ -568,24 +578,28 @@ void launch_scale_cols(int ncols, long long nrows, const double *X, long long ld
 void launch_residual(int ncols, long long nrows, const double *HX, const double *X,
                      const double *theta, double *R, cudaStream_t s) {
   if (ncols <= 0) return;
+  count_launch();
   k_residual<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, HX, X, theta, R);
 }
 
 void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
                             double *red, cudaStream_t s) {
   const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
+  count_launch();
   k_sector_restrict<<<grid_for((long long)ncols * nr * ny), 256, 0, s>>>(parity, nx, ny, ncols,
                                                                          full, red);
 }
 
 void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
                           double *full, cudaStream_t s) {
+  count_launch();
   k_sector_expand<<<grid_for((long long)ncols * nx * ny), 256, 0, s>>>(parity, nx, ny, ncols, red,
                                                                        full);
 }
 
 void launch_fix_sign(int ncols, long long nrows, double *X, cudaStream_t s) {
   if (ncols <= 0) return;
+  count_launch();
   k_fix_sign<<<ncols, 256, 0, s>>>(nrows, X);
 }
 

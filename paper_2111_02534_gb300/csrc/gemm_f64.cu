@@ -191,6 +191,7 @@ void run(GemmArgs g, cudaStream_t s) {
   g.tiles_n = (g.Nc + TN - 1) / TN;
   const long long blocks = (long long)g.batch * g.tiles_m * g.tiles_n;
   if (blocks <= 0) return;
+  count_launch();
   k_gemm_f64<TM, TN><<<(unsigned)blocks, (TM / 4) * (TN / 4), 0, s>>>(g);
 }
 

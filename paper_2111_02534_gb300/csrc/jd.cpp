@@ -24,7 +24,52 @@
 
 namespace tps {
 
+// Optional device timing of the operator applications: CUDA events bracket every H and
+// preconditioner launch group on the solve's stream; completed pairs are drained at the
+// host synchronisation points of the outer loop.
+struct PhaseTiming {
+  bool on = false;
+  std::vector<cudaEvent_t> all, free_ev;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[2];
+  double ms[2] = {0, 0}, flops[2] = {0, 0};
+  long long launches[2] = {0, 0};
+  void reset(bool enable) {
+    on = enable;
+    ms[0] = ms[1] = flops[0] = flops[1] = 0.0;
+    launches[0] = launches[1] = 0;
+  }
+  cudaEvent_t get() {
+    if (free_ev.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      all.push_back(e);
+      return e;
+    }
+    cudaEvent_t e = free_ev.back();
+    free_ev.pop_back();
+    return e;
+  }
+  void drain() {
+    for (int k = 0; k < 2; ++k) {
+      for (auto &pr : pend[k]) {
+        cudaEventSynchronize(pr.second);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) ms[k] += t;
+        free_ev.push_back(pr.first);
+        free_ev.push_back(pr.second);
+      }
+      pend[k].clear();
+    }
+  }
+  void destroy() {
+    for (auto e : all) cudaEventDestroy(e);
+    all.clear();
+    free_ev.clear();
+  }
+};
+
 struct SolverWorkspace {
+  PhaseTiming tm;
   long long N = 0;
   int mmax = 0, b = 0, kmax = 0, steps = 0;
   double *arena = nullptr;
@@ -88,6 +133,54 @@ int fill_random(Ctx &c, double *dst, int ncols, uint64_t seed, uint64_t &counter
   return TPS_OK;
 }
 
+// algorithmic FP64 flops of one H application (sum over modes of 2 N n_k, plus 3 N for
+// the pointwise (V - theta) psi term) and of one preconditioner application (forward and
+// backward mode products, 4 N n_k, plus N divisions)
+double h_flops_per_vec(const DevOperator &op) {
+  double s = 0.0;
+  for (int k = 0; k < op.nmodes; ++k) s += op.n[k];
+  return 2.0 * op.N * s + 3.0 * op.N;
+}
+double prec_flops_per_vec(const DevOperator &op) {
+  double s = 0.0;
+  for (int k = 0; k < op.nmodes; ++k) s += op.n[k];
+  return 4.0 * op.N * s + (double)op.N;
+}
+
+void apply_h_timed(Ctx &c, const double *in, double *out, int nvec, const double *theta) {
+  PhaseTiming &t = c.w.tm;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t.on) {
+    a = t.get();
+    b = t.get();
+    cudaEventRecord(a, c.s);
+  }
+  launch_apply_h(c.op, in, out, nvec, theta, 0.0, c.s);
+  if (t.on) {
+    cudaEventRecord(b, c.s);
+    t.pend[0].push_back({a, b});
+  }
+  t.flops[0] += nvec * h_flops_per_vec(c.op);
+  t.launches[0] += 1;
+}
+
+void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double shift) {
+  PhaseTiming &t = c.w.tm;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t.on) {
+    a = t.get();
+    b = t.get();
+    cudaEventRecord(a, c.s);
+  }
+  launch_apply_prec(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
+  if (t.on) {
+    cudaEventRecord(b, c.s);
+    t.pend[1].push_back({a, b});
+  }
+  t.flops[1] += nvec * prec_flops_per_vec(c.op);
+  t.launches[1] += 1;
+}
+
 // diag(A^T A) for ncols columns -> out[ncols] (device)
 void col_norms2(Ctx &c, const double *A, int ncols, double *out) {
   launch_gram(A, c.N, c.N, 1, A, c.N, c.N, 1, c.N, out, 1, 1, ncols, c.ctx->gscr, c.s);
@@ -142,7 +235,7 @@ void kt_inverse(Ctx &c, const double *Qt, int nq, const double *KQt, int use_pre
                 const double *Yin, int nsys, double *Out) {
   SolverWorkspace &w = c.w;
   if (use_prec) {
-    launch_apply_prec(c.op, Yin, Out, nsys, shift, c.ctx->ws, c.s);
+    apply_prec_timed(c, Yin, Out, nsys, shift);
     if (nq > 0) {
       launch_gram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
       // C2 = Minv * C, stored after C
@@ -243,6 +336,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
 
 void free_solver_workspace(tps_ctx *ctx) {
   if (!ctx->sw) return;
+  ctx->sw->tm.destroy();
   cudaFree(ctx->sw->arena);
   cudaFreeHost(ctx->sw->h_pinned);
   cudaFreeHost(ctx->sw->hi_pinned);
@@ -268,8 +362,8 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
       TPS_CUDA_TRY(ctx, cudaMemcpyAsync(KQt, KQt_cached, (size_t)nq_cached * N * sizeof(double),
                                         cudaMemcpyDeviceToDevice, s));
     if (nq > nq_cached) {
-      launch_apply_prec(op, Qt + (long long)nq_cached * N, KQt + (long long)nq_cached * N,
-                        nq - nq_cached, shift, ctx->ws, s);
+      apply_prec_timed(c, Qt + (long long)nq_cached * N, KQt + (long long)nq_cached * N,
+                       nq - nq_cached, shift);
       *prec_applies += nq - nq_cached;
     }
     launch_gram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s);
@@ -285,7 +379,13 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
   launch_scale_cols(nsys, N, Z, N, w.gm.scale, 0, Z, N, s);
   for (int j = 0; j < sst; ++j) {
     double *zj = Z + (long long)j * nsys * N;
-    launch_apply_h(op, zj, w.W, nsys, theta, 0.0, s);
+    // right projector of Eq. jdcor, applied explicitly: rounding in the Q directions
+    // would otherwise grow by 1/h_{j+1,j} per Arnoldi step
+    if (nq > 0) {
+      launch_gram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s);
+      launch_update(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s);
+    }
+    apply_h_timed(c, zj, w.W, nsys, theta);
     *h_applies += nsys;
     kt_inverse(c, Qt, nq, KQt, use_prec, shift, w.W, nsys, w.P);
     if (use_prec) *prec_applies += nsys;
@@ -314,6 +414,8 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   tps_solver_opts opts;
   tps_default_opts(&opts);
   if (opts_in) opts = *opts_in;
+  const int k_req = k;
+  k = k_req + std::max(0, opts.guard);  // converge k + guard pairs, return the lowest k
   const int b = std::min(block, k);
   int mmin = opts.m_min > 0 ? opts.m_min : std::max(2 * k, 8);
   mmin = ((mmin + b - 1) / b) * b;
@@ -335,11 +437,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   }
   const DevOperator &op = *opp;
   const long long N = op.N;
-  if (k > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
+  if (k_req > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
+  if (k > N / 2) k = (int)(N / 2);
   int st = alloc_workspace(ctx, N, mmax, b, k, steps);
   if (st) return st;
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
+  w.tm.reset(opts.timing != 0);
+  const long long launches0 = g_kernel_launches.load();
   double hnorm = 0.0;
   tps_get_info(ctx, nullptr, &hnorm);
 
@@ -361,8 +466,17 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
                                           cudaMemcpyDeviceToDevice, s));
     }
     if (nw < b) {
-      st = fill_random(c, w.V + (long long)nw * N, b - nw, opts.seed, rng_counter);
+      double *Rb = w.V + (long long)nw * N;
+      st = fill_random(c, Rb, b - nw, opts.seed, rng_counter);
       if (st) return st;
+      // low-pass filter the random columns: (T - s)^-1 applied smooth_start times
+      const double s_smooth = op.lam_min_sum - 1e-3 * hnorm;
+      for (int it = 0; it < opts.smooth_start && opts.use_prec; ++it) {
+        launch_apply_prec(op, Rb, w.P, b - nw, s_smooth, ctx->ws, s);
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(Rb, w.P, (size_t)(b - nw) * N * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+        stt.prec_applies += b - nw;
+      }
     }
   }
   int m = 0, nlock = 0;
@@ -385,7 +499,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     bn = rank;
     // (2) H applied to the new block
     double *HT = w.HV + (long long)m * N;
-    launch_apply_h(op, T, HT, bn, nullptr, 0.0, s);
+    apply_h_timed(c, T, HT, bn, nullptr);
     stt.h_applies += bn;
     // (3) projected matrix G = V^T H V, new columns and their mirror
     if (m > 0) launch_gram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * mmax, mmax, 0, 1,
@@ -409,6 +523,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     TPS_CUDA_TRY(ctx, cudaGetLastError());
+    w.tm.drain();
     int nconv = 0;
     while (nconv < nact && std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) <= tol * hnorm) {
       lam[nlock + nconv] = w.h_pinned[nconv];
@@ -448,21 +563,21 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       launch_residual(nact2, N, w.HX, X, w.theta, w.R, s);
     }
     // (7) correction equations for the active Ritz pairs
+    // Preconditioner shift.  The kinetic part T is positive semi-definite with its
+    // bottom at lam_min_sum (= 0), so K = T - shift is positive definite for any
+    // shift below it.  The paper's choice is the two-body threshold -E0 (Sec. 4.2),
+    // just above the wanted bound states; without E0 the adaptive choice is the
+    // lowest active Ritz value when it lies below the kinetic spectrum, else its
+    // mirror image below it (a positive shift would make K indefinite).
     double shift = opts.prec_shift;
     if (!std::isfinite(shift)) {
       const double th0 = w.h_pinned[nconv < nact ? nconv : 0];
-      shift = th0;
+      const double floor_gap = std::max(std::fabs(th0 - op.lam_min_sum), 1e-8 * hnorm);
+      shift = op.lam_min_sum - floor_gap;
     }
-    if (opts.use_prec) {
-      if (!(shift == cached_shift)) {
-        kq_valid = 0;
-        cached_shift = shift;
-      }
-      // singular shift: move it just below the kinetic spectrum's bottom
-      if (shift > op.lam_min_sum - 1e-12 * std::max(1.0, op.lam_max_sum)) {
-        if (std::fabs(shift - op.lam_min_sum) < 1e-10 * std::max(1.0, op.lam_max_sum))
-          shift = op.lam_min_sum - 1e-6 * std::max(1.0, op.lam_max_sum);
-      }
+    if (opts.use_prec && !(shift == cached_shift)) {
+      kq_valid = 0;
+      cached_shift = shift;
     }
     const int nq = nlock + nact2;
     // K^-1 of newly locked columns is recomputed each time (kq_valid tracks the cache)
@@ -476,34 +591,37 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   }
   stt.outer_iters = outer;
   // final Rayleigh quotients and residuals with a fresh H-apply of the locked vectors
-  const int nret = std::min(nlock, k);
-  if (nret > 0) {
-    double *HQ = w.V2;  // at least mmax >= nret columns
-    launch_apply_h(op, w.QX, HQ, nret, nullptr, 0.0, s);
-    stt.h_applies += nret;
-    launch_gram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nret, ctx->gscr, s);
-    col_norms2(c, w.QX, nret, w.ref);
-    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta2, nret * sizeof(double),
+  const int nlocked = std::min(nlock, k);
+  int nret = 0;
+  if (nlocked > 0) {
+    const int nl = nlocked;
+    double *HQ = w.V2;  // at least max(mmax, kmax) columns
+    apply_h_timed(c, w.QX, HQ, nl, nullptr);
+    stt.h_applies += nl;
+    launch_gram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nl, ctx->gscr, s);
+    col_norms2(c, w.QX, nl, w.ref);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta2, nl * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
-    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 64, w.ref, nret * sizeof(double),
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 1024, w.ref, nl * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    for (int i = 0; i < nret; ++i) lam[i] = w.h_pinned[i] / w.h_pinned[64 + i];
+    for (int i = 0; i < nl; ++i) lam[i] = w.h_pinned[i] / w.h_pinned[1024 + i];
     // final residual norms ||H x - lambda x|| / ||H||_est
-    for (int i = 0; i < nret; ++i) w.h_pinned[128 + i] = lam[i];
-    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.theta2, w.h_pinned + 128, nret * sizeof(double),
+    for (int i = 0; i < nl; ++i) w.h_pinned[2048 + i] = lam[i];
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.theta2, w.h_pinned + 2048, nl * sizeof(double),
                                       cudaMemcpyHostToDevice, s));
-    launch_residual(nret, N, HQ, w.QX, w.theta2, w.HV2, s);
-    col_norms2(c, w.HV2, nret, w.ref);
-    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 256, w.ref, nret * sizeof(double),
+    launch_residual(nl, N, HQ, w.QX, w.theta2, w.HV2, s);
+    col_norms2(c, w.HV2, nl, w.ref);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 3072, w.ref, nl * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    for (int i = 0; i < nret; ++i) resid[i] = std::sqrt(std::max(w.h_pinned[256 + i], 0.0)) / hnorm;
+    for (int i = 0; i < nl; ++i) resid[i] = std::sqrt(std::max(w.h_pinned[3072 + i], 0.0)) / hnorm;
     // sort ascending (locking order is ascending up to rounding within clusters)
-    std::vector<int> order(nret);
-    for (int i = 0; i < nret; ++i) order[i] = i;
+    std::vector<int> order(nl);
+    for (int i = 0; i < nl; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int bb) { return lam[a] < lam[bb]; });
-    // expand to the full grid in sorted order
+    // expand the lowest k_req to the full grid in sorted order
+    nret = std::min(nl, k_req);
     for (int i = 0; i < nret; ++i) {
       const double *src = w.QX + (long long)order[i] * N;
       double *dst = evecs_dev + (long long)i * ctx->full.N;
@@ -518,7 +636,15 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     TPS_CUDA_TRY(ctx, cudaGetLastError());
   }
+  w.tm.drain();
   stt.n_converged = nret;
+  stt.h_ms = w.tm.ms[0];
+  stt.prec_ms = w.tm.ms[1];
+  stt.h_flops = w.tm.flops[0];
+  stt.prec_flops = w.tm.flops[1];
+  stt.h_launches = w.tm.launches[0];
+  stt.prec_launches = w.tm.launches[1];
+  stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;
   if (!converged) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "outer-iteration cap reached");
@@ -537,6 +663,8 @@ void tps_default_opts(tps_solver_opts *o) {
   o->use_prec = 1;
   o->prec_shift = NAN;
   o->seed = 12345;
+  o->guard = 2;
+  o->smooth_start = 2;
 }
 
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
@@ -586,6 +714,7 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
     if (st) return st;
   }
   int ha = 0, pa = 0;
+  ctx->sw->tm.reset(false);
   st = correction_impl(ctx, ctx->full, Qt_dev, nq, nullptr, 0, R_dev, theta_dev, nsys, steps,
                        use_prec, shift, 0.0, T_dev, &ha, &pa, stream);
   if (st) return st;

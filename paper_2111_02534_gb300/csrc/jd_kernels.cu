@@ -145,36 +145,45 @@ inline unsigned nb(long long n, int t = 128) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 void launch_gmres_init(int nsys, int s, const double *nrm2, GmresState &st, cudaStream_t str) {
+  count_launch();
   k_gmres_init<<<nb(nsys), 128, 0, str>>>(nsys, s, nrm2, st.beta, st.g, st.Hb, st.done, st.mvalid,
                                            st.scale);
 }
 void launch_hess_add(int nsys, int s, int j, const double *h, int ldh, GmresState &st,
                      cudaStream_t str) {
+  count_launch();
   k_hess_add<<<nb((long long)nsys * (j + 1)), 128, 0, str>>>(nsys, s, j, h, ldh, st.Hb, st.done);
 }
 void launch_gmres_givens(int nsys, int s, int j, const double *nrm2, GmresState &st, double tol,
                          cudaStream_t str) {
+  count_launch();
   k_gmres_givens<<<nb(nsys), 128, 0, str>>>(nsys, s, j, nrm2, st.Hb, st.cs, st.sn, st.g, st.beta,
                                              st.done, st.mvalid, st.scale, tol);
 }
 void launch_gmres_solve(int nsys, int s, GmresState &st, cudaStream_t str) {
+  count_launch();
   k_gmres_solve<<<nb(nsys), 128, 0, str>>>(nsys, s, st.Hb, st.g, st.mvalid, st.y);
 }
 void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str) {
+  count_launch();
   k_mirror_block<<<nb((long long)(m0 + bn) * bn), 128, 0, str>>>(G, ldg, m0, bn);
 }
 void launch_set_diag(double *G, int ldg, const double *d, int m, cudaStream_t str) {
+  count_launch();
   k_set_diag<<<nb((long long)m * m), 128, 0, str>>>(G, ldg, d, m);
 }
 void launch_copy_small(const double *src, double *dst, int n, cudaStream_t str) {
+  count_launch();
   k_copy_small<<<nb(n), 128, 0, str>>>(src, dst, n);
 }
 void launch_sqrt_div(const double *nrm2, double *out, int n, double div, cudaStream_t str) {
+  count_launch();
   k_sqrt_div<<<nb(n), 128, 0, str>>>(nrm2, out, n, div);
 }
 void launch_small_gemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,
                        int ldb, double beta, double *C, int ldc, cudaStream_t str) {
   if (m <= 0 || n <= 0) return;
+  count_launch();
   k_small_gemm<<<nb((long long)m * n), 128, 0, str>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -12,6 +13,10 @@
 #include "../../include/tps.h"
 
 namespace tps {
+
+// Every kernel launch of the library is counted (reported by tps_solve's stats).
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // A discretised Kronecker-sum operator resident on the device:

@@ -38,13 +38,17 @@ F64 = 0
 class SolverOpts(C.Structure):
     _fields_ = [("m_min", C.c_int), ("m_max", C.c_int), ("inner_steps", C.c_int),
                 ("max_outer", C.c_int), ("use_prec", C.c_int), ("prec_shift", C.c_double),
-                ("seed", C.c_ulonglong), ("inner_tol", C.c_double)]
+                ("seed", C.c_ulonglong), ("inner_tol", C.c_double), ("timing", C.c_int),
+                ("guard", C.c_int), ("smooth_start", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("h_applies", C.c_int), ("prec_applies", C.c_int),
                 ("inner_steps", C.c_int), ("restarts", C.c_int), ("n_converged", C.c_int),
-                ("hnorm_est", C.c_double), ("time_ms", C.c_double), ("resid", C.c_double * 64)]
+                ("hnorm_est", C.c_double), ("time_ms", C.c_double), ("h_ms", C.c_double),
+                ("prec_ms", C.c_double), ("h_flops", C.c_double), ("prec_flops", C.c_double),
+                ("h_launches", C.c_longlong), ("prec_launches", C.c_longlong),
+                ("kernel_launches", C.c_longlong), ("resid", C.c_double * 64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "resid"}

@@ -1,0 +1,52 @@
+"""Host logic of bench.py on the CPU: the N > 1 replica aggregation over gloo ranks and the
+1e-10 accuracy gate that decides which eigenpairs count."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, p = bench.aggregate(1.0 + rank, 8 - rank, world, device="cpu")
+    q.put((rank, t, p))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    # max time over ranks, pairs summed over ranks
+    assert got == [(0, 2.0, 15), (1, 2.0, 15)]
+
+
+def test_accuracy_gate():
+    import bench
+    ref = np.array([-2e-3, -1e-3, 5e-4])
+    lam = ref * (1 + np.array([0.0, 5e-11, 2e-10]))
+    n, worst = bench.passing_pairs(lam, ref)
+    assert n == 2 and worst == pytest.approx(2e-10, rel=1e-3)
+    assert bench.aggregate(3.0, 5, 1) == (3.0, 5)

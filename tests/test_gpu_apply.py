@@ -16,6 +16,14 @@ from paper_2111_02534_gb300.inputs import random_block, WORKLOADS
 pytestmark = pytest.mark.gpu
 
 
+def prec_tol(P, theta):
+    """Relative tolerance for (T - theta)^-1 from the arithmetic: 64 eps kappa, kappa =
+    (lambda_max - theta) / (lambda_min - theta) of T - theta, floored at 1e-11."""
+    lam_max = sum(abs(a) * (np.pi * n / (2 * L)) ** 2 for a, n, L in zip(P.a, P.n, P.L))
+    kappa = (lam_max - theta) / (0.0 - theta)
+    return max(1e-11, 64 * np.finfo(float).eps * kappa)
+
+
 def _check_h(P, ctx, nvec, theta, seed, rows=None):
     psi = random_block(nvec, P.N, seed)
     out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
@@ -149,8 +157,11 @@ def test_apply_prec_1d_full_size():
     ctx.apply_prec(dev(r), out, -1e-3)
     got = host(out)
     ref = apply_sylvester(P, r[:1], -1e-3)
-    assert np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0]) <= 1e-11
-    assert kinetic_residual(P, got, r, -1e-3) <= 1e-11
+    # shift 1e-3 below the kinetic spectrum: D2's two constructions differ by
+    # O(eps ||T||), which the solve amplifies by ||T|| / 1e-3 (condition ~ 9e5)
+    tol = prec_tol(P, -1e-3)
+    assert np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0]) <= tol
+    assert kinetic_residual(P, got, r, -1e-3) <= tol
 
 
 @pytest.mark.parametrize("n", [(6, 6, 4, 4), (8, 8, 6, 6)])

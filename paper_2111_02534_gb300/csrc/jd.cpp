@@ -575,6 +575,12 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       const double floor_gap = std::max(std::fabs(th0 - op.lam_min_sum), 1e-8 * hnorm);
       shift = op.lam_min_sum - floor_gap;
     }
+    // keep the previous shift (and the cached K^-1 of the locked vectors) while the
+    // adaptive choice moves by less than 10 %: the preconditioner only approximates
+    // (H - theta)^-1, so a slightly older shift costs nothing in convergence
+    if (!std::isfinite(opts.prec_shift) && std::isfinite(cached_shift) &&
+        std::fabs(shift - cached_shift) <= 0.1 * std::fabs(cached_shift))
+      shift = cached_shift;
     if (opts.use_prec && !(shift == cached_shift)) {
       kq_valid = 0;
       cached_shift = shift;

@@ -222,6 +222,21 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
                    const double *theta_dev, int nsys, int steps, int use_prec, double shift,
                    double *T_dev, cudaStream_t stream);
 
+/* Allocation-free Gram product G = A^T B (p, q <= 64), same layout and result as
+ * tps_gram, for callers that cannot allocate device memory: programs whose device
+ * memory is owned by a memory manager that hands out all of it up front (a
+ * framework's caching allocator, a service with a fixed memory budget).  It needs no
+ * context and calls no allocator; its partial sums live in a 1 MiB array compiled into
+ * the library, one per device.  The paper has no counterpart to this entry point.
+ *  - The first call on each device looks the array's address up (with that device
+ *    current); make that first call before any stream capture.
+ *  - Every call on a device shares the array and it keeps the last call's contents;
+ *    calls that overlap on the GPU (e.g. on two streams at once) race on it.
+ *  - Returns TPS_ERR_INVALID_ARG for p or q outside 1..64 or bad strides/pointers,
+ *    TPS_ERR_CUDA if the address look-up or the launch fails.  Asynchronous on stream. */
+int tps_gram_noalloc(const double *A_dev, long long lda, int p, const double *B_dev, long long ldb,
+                     int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ _sig = {
     "tps_small_eigh": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp]),
     "tps_correction": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int,
                                  C.c_double, _vp, _vp]),
+    "tps_gram_noalloc": (C.c_int, [_vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -115,6 +116,14 @@ def default_opts() -> SolverOpts:
     o = SolverOpts()
     _lib.tps_default_opts(C.byref(o))
     return o
+
+
+def gram_noalloc(A, p, B, q, nrows, G, ldg=None, stream=None):
+    """G = A^T B through the allocation-free entry point (no context needed)."""
+    st = _lib.tps_gram_noalloc(_ptr(A), nrows, p, _ptr(B), nrows, q, nrows, _ptr(G), ldg or p,
+                               _stream(stream))
+    if st != OK:
+        raise TpsError(st, "tps_gram_noalloc")
 
 
 def two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L) -> float:

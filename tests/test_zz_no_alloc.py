@@ -1,0 +1,56 @@
+"""The allocation-free Gram entry point, tps_gram_noalloc, against tps_gram.
+
+tps_gram_noalloc exists for callers that cannot allocate device memory (their device
+memory belongs to a memory manager that hands all of it out up front).  It keeps its
+partial sums in a fixed array inside the library, so this test checks that two calls in
+a row -- the second one reusing the array the first one left behind -- both agree with
+the context-based tps_gram, and that sizes beyond its limits are refused.  The file is
+named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_common import torch, require_gpu, dev, host
+from paper_2111_02534_gb300.inputs import random_block
+
+pytestmark = pytest.mark.gpu
+
+
+def _gram_with_context(ctx, A, p, B, q, nrows):
+    G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+    ctx.gram(dev(A), p, dev(B), q, nrows, G)
+    return host(G)
+
+
+def test_noalloc_gram_matches_context_gram_twice():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    ctx = tps.Context(1, 0)
+    cases = [(131584, 24, 8, 1), (1000003, 64, 5, 2)]   # second call reuses the scratch array
+    for nrows, p, q, seed in cases:
+        A = random_block(p, nrows, seed)
+        B = random_block(q, nrows, seed + 10)
+        ref = _gram_with_context(ctx, A, p, B, q, nrows)
+        G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+        st = tps._lib.tps_gram_noalloc(ctypes.c_void_p(dev(A).data_ptr()), nrows, p,
+                                       ctypes.c_void_p(dev(B).data_ptr()), nrows, q, nrows,
+                                       ctypes.c_void_p(G.data_ptr()), p,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == tps.OK
+        got = host(G)
+        scale = max(1.0, np.sqrt(nrows)) * max(1.0, np.abs(ref).max())
+        assert np.max(np.abs(got - ref)) <= 1e-14 * scale
+        assert np.max(np.abs(got.T - A @ B.T)) <= 1e-14 * scale
+    ctx.close()
+
+
+def test_noalloc_gram_refuses_sizes_beyond_its_limit():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    A = torch.zeros(65, 8, dtype=torch.float64, device="cuda")
+    G = torch.zeros(65 * 65, dtype=torch.float64, device="cuda")
+    with pytest.raises(tps.TpsError) as e:
+        tps.gram_noalloc(A, 65, A, 1, 8, G, ldg=65)
+    assert e.value.status == tps.ERR_INVALID_ARG

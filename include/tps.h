@@ -56,7 +56,7 @@ typedef enum tps_status {
 
 enum { TPS_GAUSS = 0, TPS_LORENTZ3 = 1 };          /* f_G = exp(-xi^2), f_L = (1+xi^2)^-3 */
 enum { TPS_ANY = 0, TPS_X_EVEN = 1, TPS_X_ODD = 2 }; /* heavy-exchange sector (Sec. 5.1) */
-enum { TPS_F64 = 0 };                                /* arithmetic of apply calls */
+enum { TPS_F64 = 0, TPS_F32 = 1 };                   /* arithmetic of apply calls (data stay FP64) */
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -118,7 +118,8 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
  * H (V neglected), by fast diagonalisation S ((S^T r S) ./ (Lambda (+) .. - theta)) S^T
  * over all 2*dim modes.  Returns TPS_ERR_SINGULAR when
  * min |lambda_sum - theta| < 1e-14 * max |lambda_sum|.  r_dev, out_dev: device
- * [nvec][N], must not overlap. */
+ * [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32: FP32
+ * arithmetic (the preconditioner is an approximation; the solver's default). */
 int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, double theta,
                    int dtype, cudaStream_t stream);
 
@@ -141,6 +142,8 @@ typedef struct tps_solver_opts {
                          absent from the early search space is not skipped (default 2) */
   int smooth_start;   /* applications of the kinetic preconditioner (shift -1e-3 ||H||_est) to
                          the random part of the start block, a low-pass filter (default 2) */
+  int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_F32 (default)
+                         or TPS_F64; residuals, Ritz values and H stay FP64 */
 } tps_solver_opts;
 
 typedef struct tps_stats {

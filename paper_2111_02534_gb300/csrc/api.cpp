@@ -157,6 +157,13 @@ int upload(tps_ctx *ctx, double **dst, const std::vector<double> &src) {
   return TPS_OK;
 }
 
+int upload_f32(tps_ctx *ctx, float **dst, const std::vector<double> &src) {
+  std::vector<float> f(src.begin(), src.end());
+  TPS_CUDA_TRY(ctx, cudaMalloc((void **)dst, f.size() * sizeof(float)));
+  TPS_CUDA_TRY(ctx, cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return TPS_OK;
+}
+
 int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &modes,
                    const std::vector<double> *V) {
   free_operator(op);
@@ -173,6 +180,9 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
     if ((st = upload(ctx, &op.S[k], m.S))) return st;
     if ((st = upload(ctx, &op.ST[k], transpose(m.S, m.n)))) return st;
     if ((st = upload(ctx, &op.lam[k], m.lam))) return st;
+    if ((st = upload_f32(ctx, &op.Sf[k], m.S))) return st;
+    if ((st = upload_f32(ctx, &op.STf[k], transpose(m.S, m.n)))) return st;
+    if ((st = upload_f32(ctx, &op.lamf[k], m.lam))) return st;
     op.lam_h[k] = m.lam;
     lmin += *std::min_element(m.lam.begin(), m.lam.end());
     lmax += *std::max_element(m.lam.begin(), m.lam.end());
@@ -242,7 +252,11 @@ void free_operator(DevOperator &op) {
     cudaFree(op.S[k]);
     cudaFree(op.ST[k]);
     cudaFree(op.lam[k]);
+    cudaFree(op.Sf[k]);
+    cudaFree(op.STf[k]);
+    cudaFree(op.lamf[k]);
     op.K[k] = op.KT[k] = op.S[k] = op.ST[k] = op.lam[k] = nullptr;
+    op.Sf[k] = op.STf[k] = op.lamf[k] = nullptr;
     op.lam_h[k].clear();
   }
   cudaFree(op.V);
@@ -597,7 +611,8 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
                    int dtype, cudaStream_t stream) {
   int st = check_ready(ctx);
   if (st) return st;
-  if (dtype != TPS_F64 || nvec < 0 || (nvec > 0 && (!r_dev || !out_dev)) || !std::isfinite(theta))
+  if ((dtype != TPS_F64 && dtype != TPS_F32) || nvec < 0 || (nvec > 0 && (!r_dev || !out_dev)) ||
+      !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_prec arguments");
   const char *a = (const char *)r_dev, *b = (const char *)out_dev;
   const size_t bytes = (size_t)nvec * ctx->full.N * sizeof(double);
@@ -610,8 +625,12 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
   if (cap < 1) return set_error(ctx, TPS_ERR_NOT_CONFIGURED, "no preconditioner workspace");
   for (int v0 = 0; v0 < nvec; v0 += (int)cap) {
     const int nv = (int)std::min<long long>(cap, nvec - v0);
-    launch_apply_prec(ctx->full, (const double *)r_dev + (long long)v0 * ctx->full.N,
-                      (double *)out_dev + (long long)v0 * ctx->full.N, nv, theta, ctx->ws, stream);
+    const double *rin = (const double *)r_dev + (long long)v0 * ctx->full.N;
+    double *o = (double *)out_dev + (long long)v0 * ctx->full.N;
+    if (dtype == TPS_F32)
+      launch_apply_prec_f32(ctx->full, rin, o, nv, theta, ctx->ws, stream);
+    else
+      launch_apply_prec(ctx->full, rin, o, nv, theta, ctx->ws, stream);
   }
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;

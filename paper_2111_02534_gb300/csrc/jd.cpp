@@ -70,6 +70,7 @@ struct PhaseTiming {
 
 struct SolverWorkspace {
   PhaseTiming tm;
+  int prec_dtype = TPS_F64;  // arithmetic of the preconditioner applications
   long long N = 0;
   int mmax = 0, b = 0, kmax = 0, steps = 0;
   double *arena = nullptr;
@@ -172,7 +173,10 @@ void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double sh
     b = t.get();
     cudaEventRecord(a, c.s);
   }
-  launch_apply_prec(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
+  if (c.w.prec_dtype == TPS_F32)
+    launch_apply_prec_f32(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
+  else
+    launch_apply_prec(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
   if (t.on) {
     cudaEventRecord(b, c.s);
     t.pend[1].push_back({a, b});
@@ -444,6 +448,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
+  w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64 : TPS_F32;
   const long long launches0 = g_kernel_launches.load();
   double hnorm = 0.0;
   tps_get_info(ctx, nullptr, &hnorm);
@@ -472,7 +477,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       // low-pass filter the random columns: (T - s)^-1 applied smooth_start times
       const double s_smooth = op.lam_min_sum - 1e-3 * hnorm;
       for (int it = 0; it < opts.smooth_start && opts.use_prec; ++it) {
-        launch_apply_prec(op, Rb, w.P, b - nw, s_smooth, ctx->ws, s);
+        apply_prec_timed(c, Rb, w.P, b - nw, s_smooth);
         TPS_CUDA_TRY(ctx, cudaMemcpyAsync(Rb, w.P, (size_t)(b - nw) * N * sizeof(double),
                                           cudaMemcpyDeviceToDevice, s));
         stt.prec_applies += b - nw;
@@ -671,6 +676,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->seed = 12345;
   o->guard = 2;
   o->smooth_start = 2;
+  o->prec_dtype = TPS_F32;
 }
 
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
@@ -721,6 +727,7 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
   }
   int ha = 0, pa = 0;
   ctx->sw->tm.reset(false);
+  ctx->sw->prec_dtype = TPS_F64;
   st = correction_impl(ctx, ctx->full, Qt_dev, nq, nullptr, 0, R_dev, theta_dev, nsys, steps,
                        use_prec, shift, 0.0, T_dev, &ha, &pa, stream);
   if (st) return st;

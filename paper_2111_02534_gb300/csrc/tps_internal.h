@@ -35,6 +35,9 @@ struct DevOperator {
   double *S[4] = {nullptr, nullptr, nullptr, nullptr};   // row-major, columns = eigenvectors
   double *ST[4] = {nullptr, nullptr, nullptr, nullptr};  // S^T
   double *lam[4] = {nullptr, nullptr, nullptr, nullptr}; // eigenvalues of K_k
+  float *Sf[4] = {nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the FP32 preconditioner
+  float *STf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *lamf[4] = {nullptr, nullptr, nullptr, nullptr};
   double *V = nullptr;                                   // [N]
   std::vector<double> lam_h[4];                          // host copies (singularity test)
   double lam_min_sum = 0.0, lam_max_sum = 0.0;
@@ -54,6 +57,9 @@ void launch_apply_h(const DevOperator &op, const double *psi, double *out, int n
 // out[v] = (T - sigma)^-1 r[v] by fast diagonalisation (needs 2 * nvec * N workspace).
 void launch_apply_prec(const DevOperator &op, const double *r, double *out, int nvec,
                        double sigma, ApplyWorkspace &ws, cudaStream_t s);
+// The same with FP32 arithmetic (FP64 r and out).
+void launch_apply_prec_f32(const DevOperator &op, const double *r, double *out, int nvec,
+                           double sigma, ApplyWorkspace &ws, cudaStream_t s);
 
 // Skinny block kernels.  Column c of block X is X + c*ldx; batch s adds s*bsx.
 struct GramScratch {

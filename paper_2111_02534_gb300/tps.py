@@ -33,13 +33,14 @@ ERR_TIMEOUT = -7
 GAUSS, LORENTZ3 = 0, 1
 ANY, X_EVEN, X_ODD = 0, 1, 2
 F64 = 0
+F32 = 1
 
 
 class SolverOpts(C.Structure):
     _fields_ = [("m_min", C.c_int), ("m_max", C.c_int), ("inner_steps", C.c_int),
                 ("max_outer", C.c_int), ("use_prec", C.c_int), ("prec_shift", C.c_double),
                 ("seed", C.c_ulonglong), ("inner_tol", C.c_double), ("timing", C.c_int),
-                ("guard", C.c_int), ("smooth_start", C.c_int)]
+                ("guard", C.c_int), ("smooth_start", C.c_int), ("prec_dtype", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -195,9 +196,9 @@ class Context:
         self._check(_lib.tps_apply_h(self._h, _ptr(psi), _ptr(out), nvec, theta, F64,
                                      _stream(stream)), "apply_h")
 
-    def apply_prec(self, r, out, theta, stream=None):
+    def apply_prec(self, r, out, theta, stream=None, dtype=F64):
         nvec = r.numel() // self.info()[0]
-        self._check(_lib.tps_apply_prec(self._h, _ptr(r), _ptr(out), nvec, theta, F64,
+        self._check(_lib.tps_apply_prec(self._h, _ptr(r), _ptr(out), nvec, theta, dtype,
                                         _stream(stream)), "apply_prec")
 
     # ---- solver -----------------------------------------------------------------

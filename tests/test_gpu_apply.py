@@ -187,3 +187,36 @@ def test_apply_prec_2d_full_size_property():
     out = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
     ctx.apply_prec(dev(r), out, -0.3)
     assert kinetic_residual(P, host(out), r, -0.3) <= 1e-11
+
+
+@pytest.mark.parametrize("n,theta", [((64, 64), -0.5), ((100, 70), -1.3), ((130, 200), -0.01)])
+def test_apply_prec_1d_fp32(n, theta):
+    # FP32 arithmetic, FP64 data: error bounded by 64 eps_32 times the condition of T - theta
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    L = (20.0, 15.0)
+    P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+    ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    r = random_block(3, P.N, seed=9)
+    out = torch.empty(3, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, theta, dtype=tps.F32)
+    got = host(out)
+    ref = apply_sylvester(P, r, theta)
+    tol = prec_tol(P, theta) * np.finfo(np.float32).eps / np.finfo(float).eps
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol, (err.max(), tol)
+    assert err.max() > 1e-12        # it really ran in FP32
+
+
+def test_apply_prec_2d_fp32():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    n, L = (8, 8, 6, 6), (4.0, 4.0, 3.0, 3.0)
+    P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+    ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    r = random_block(2, P.N, seed=2)
+    out = torch.empty(2, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, -0.4, dtype=tps.F32)
+    ref = apply_dense(P, r, -0.4)
+    tol = prec_tol(P, -0.4) * np.finfo(np.float32).eps / np.finfo(float).eps
+    assert np.max(np.linalg.norm(host(out) - ref, axis=1) / np.linalg.norm(ref, axis=1)) <= tol

@@ -122,15 +122,15 @@ def test_solve_harmonic_closed_form():
     assert np.max(np.abs(lam - levels) / levels) <= 1e-10
 
 
-@pytest.mark.parametrize("use_prec,block", [(0, 4), (1, 1), (0, 1)])
-def test_solve_variants_agree(use_prec, block):
+@pytest.mark.parametrize("use_prec,block,prec_dtype", [(0, 4, 1), (1, 1, 1), (0, 1, 1), (1, 4, 0)])
+def test_solve_variants_agree(use_prec, block, prec_dtype):
     # no-prec-JDQR and the paper's single-vector JDQR reach the same eigenpairs
     require_gpu()
     n, L = (48, 48), (15.0, 15.0)
     P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
     ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
     lam, X, st = _solve(ctx, 3, 1, block, use_prec=use_prec, max_outer=3000,
-                        inner_steps=20 if not use_prec else 10)
+                        inner_steps=20 if not use_prec else 10, prec_dtype=prec_dtype)
     ref, _ = lowest_dense(P, 3, O_EVEN)
     assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
     _check_vectors(P, lam, X, parity_sign=1.0)

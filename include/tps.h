@@ -110,7 +110,8 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est);
 
 /* Eq. tensor_op1D (1D) and Eq. tensor_op2D (2D): out = (H - theta) psi for nvec
  * vectors, H = sum_k a_k (I x .. x D2_k x .. x I) + diag(V).  psi_dev, out_dev:
- * device, [nvec][N] FP64, must not overlap.  dtype: TPS_F64. */
+ * device, [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32:
+ * FP32 arithmetic (error ~ n eps_32 ||H|| |psi|), the low-precision phase's operator. */
 int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, double theta,
                 int dtype, cudaStream_t stream);
 
@@ -128,7 +129,9 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
 typedef struct tps_solver_opts {
   int m_min;          /* search-space size kept at restart (0: max(2k, 8) rounded up to the block) */
   int m_max;          /* search-space size that triggers a restart (0: m_min + 2*block; at most 64) */
-  int inner_steps;    /* GMRES steps per correction equation (0: 10; Sec. 4.1) */
+  int inner_steps;    /* GMRES steps per correction equation (Sec. 4.1).  0: adaptive -- one
+                         step (the correction is the projected preconditioned residual
+                         -Kt^-1 r), widened to 3, 7, 10 when the outer residual stalls */
   int max_outer;      /* outer-iteration cap (0: 500) */
   int use_prec;       /* 1: prec-JDQR (Sec. 4.2 preconditioner), 0: no-prec-JDQR */
   double prec_shift;  /* fixed preconditioner shift (the paper's -E0); NaN: adaptive, -|theta| of
@@ -143,7 +146,15 @@ typedef struct tps_solver_opts {
   int smooth_start;   /* applications of the kinetic preconditioner (shift -1e-3 ||H||_est) to
                          the random part of the start block, a low-pass filter (default 2) */
   int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_F32 (default)
-                         or TPS_F64; residuals, Ritz values and H stay FP64 */
+                         or TPS_F64 */
+  int h_dtype;        /* TPS_F32 (default): mixed precision -- a first phase runs the H mode
+                         products in FP32 until every pair's residual is below switch_tol,
+                         then an FP64 refinement phase converges them to tol; TPS_F64: FP64
+                         throughout.  Gram matrices, Ritz values and QR steps are FP64 always */
+  double switch_tol;  /* relative residual ending the FP32 phase (0: 1e-6) */
+  int refine_block;   /* block size of the FP64 refinement phase (0: k + guard, at most 32) */
+  int refine_inner_steps; /* GMRES steps in the refinement phase (0: adaptive as above) */
+  int refine_inner_dtype; /* arithmetic of H inside the refinement's GMRES (TPS_F64 default) */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -162,6 +173,9 @@ typedef struct tps_stats {
   long long h_launches;      /* H-application launches (each over a block of vectors) */
   long long prec_launches;   /* preconditioner-application launches */
   long long kernel_launches; /* all CUDA kernels launched by this call */
+  double h32_ms;      /* with opts.timing: device time of the FP32 H applications */
+  double h32_flops;   /* algorithmic flops of the FP32 H applications */
+  long long h32_launches;
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

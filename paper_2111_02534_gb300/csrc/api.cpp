@@ -183,6 +183,8 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
     if ((st = upload_f32(ctx, &op.Sf[k], m.S))) return st;
     if ((st = upload_f32(ctx, &op.STf[k], transpose(m.S, m.n)))) return st;
     if ((st = upload_f32(ctx, &op.lamf[k], m.lam))) return st;
+    if ((st = upload_f32(ctx, &op.Kf[k], m.K))) return st;
+    if ((st = upload_f32(ctx, &op.KTf[k], transpose(m.K, m.n)))) return st;
     op.lam_h[k] = m.lam;
     lmin += *std::min_element(m.lam.begin(), m.lam.end());
     lmax += *std::max_element(m.lam.begin(), m.lam.end());
@@ -192,8 +194,12 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
   TPS_CUDA_TRY(ctx, cudaMalloc((void **)&op.V, op.N * sizeof(double)));
   if (V) {
     TPS_CUDA_TRY(ctx, cudaMemcpy(op.V, V->data(), op.N * sizeof(double), cudaMemcpyHostToDevice));
+    int st = upload_f32(ctx, &op.Vf, *V);
+    if (st) return st;
   } else {
     TPS_CUDA_TRY(ctx, cudaMemset(op.V, 0, op.N * sizeof(double)));
+    TPS_CUDA_TRY(ctx, cudaMalloc((void **)&op.Vf, op.N * sizeof(float)));
+    TPS_CUDA_TRY(ctx, cudaMemset(op.Vf, 0, op.N * sizeof(float)));
   }
   return TPS_OK;
 }
@@ -255,12 +261,16 @@ void free_operator(DevOperator &op) {
     cudaFree(op.Sf[k]);
     cudaFree(op.STf[k]);
     cudaFree(op.lamf[k]);
+    cudaFree(op.Kf[k]);
+    cudaFree(op.KTf[k]);
     op.K[k] = op.KT[k] = op.S[k] = op.ST[k] = op.lam[k] = nullptr;
-    op.Sf[k] = op.STf[k] = op.lamf[k] = nullptr;
+    op.Sf[k] = op.STf[k] = op.lamf[k] = op.Kf[k] = op.KTf[k] = nullptr;
     op.lam_h[k].clear();
   }
   cudaFree(op.V);
+  cudaFree(op.Vf);
   op.V = nullptr;
+  op.Vf = nullptr;
   op.nmodes = 0;
   op.N = 0;
 }
@@ -430,6 +440,11 @@ int tps_set_potential(tps_ctx *ctx, const double *V, int on_device) {
     std::memcpy(ctx->V_host.data(), V, bytes);
   }
   TPS_CUDA_TRY(ctx, cudaMemcpy(ctx->full.V, ctx->V_host.data(), bytes, cudaMemcpyHostToDevice));
+  {
+    std::vector<float> vf(ctx->V_host.begin(), ctx->V_host.end());
+    TPS_CUDA_TRY(ctx, cudaMemcpy(ctx->full.Vf, vf.data(), vf.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice));
+  }
   for (int p = 0; p < 3; ++p) {
     free_operator(ctx->sect[p]);
     ctx->sect_ready[p] = false;
@@ -595,14 +610,26 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
                 int dtype, cudaStream_t stream) {
   int st = check_ready(ctx);
   if (st) return st;
-  if (dtype != TPS_F64 || nvec < 0 || (nvec > 0 && (!psi_dev || !out_dev)) || !std::isfinite(theta))
+  if ((dtype != TPS_F64 && dtype != TPS_F32) || nvec < 0 || (nvec > 0 && (!psi_dev || !out_dev)) ||
+      !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_h arguments");
   const char *a = (const char *)psi_dev, *b = (const char *)out_dev;
   const size_t bytes = (size_t)nvec * ctx->full.N * sizeof(double);
   if (nvec > 0 && a < b + bytes && b < a + bytes)
     return set_error(ctx, TPS_ERR_INVALID_ARG, "psi and out overlap");
-  launch_apply_h(ctx->full, (const double *)psi_dev, (double *)out_dev, nvec, nullptr, theta,
-                 stream);
+  if (dtype == TPS_F32) {
+    // the FP32 path converts psi into the workspace: at most its capacity per launch
+    const long long cap = 2 * ctx->ws.capacity / ctx->full.N;
+    for (int v0 = 0; v0 < nvec; v0 += (int)cap) {
+      const int nv = (int)std::min<long long>(cap, nvec - v0);
+      launch_apply_h_f32(ctx->full, (const double *)psi_dev + (long long)v0 * ctx->full.N,
+                         (double *)out_dev + (long long)v0 * ctx->full.N, nv, nullptr, theta,
+                         ctx->ws, stream);
+    }
+  } else {
+    launch_apply_h(ctx->full, (const double *)psi_dev, (double *)out_dev, nvec, nullptr, theta,
+                   stream);
+  }
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;
 }

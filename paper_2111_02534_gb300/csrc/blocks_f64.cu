@@ -3,9 +3,13 @@
 // vectors, restarts, Arnoldi), the small dense eigen/Cholesky/Givens work on one
 // CTA, and elementwise helpers.  Everything stays on the device; the host only
 // reads a few scalars per outer iteration to steer the loop.
+#include <cooperative_groups.h>
+
 #include <cstring>
 
 #include "tps_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace tps {
 namespace {
@@ -125,46 +129,81 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
 }
 
 // ------------------------------ Jacobi eigh ----------------------------------
-// Cyclic Jacobi with round-robin (tournament) ordering: each round rotates m/2
+// Cyclic Jacobi with round-robin (tournament) ordering: each round rotates mm/2
 // disjoint pairs at once (Golub & Van Loan, symmetric Schur decomposition and the
-// parallel ordering of the cyclic Jacobi method).  A' = J^T A J is formed element by
-// element from the two pairs an element's row and column belong to.
+// parallel ordering of the cyclic Jacobi method); A' = J^T A J is formed element by
+// element from the two pairs an element's row and column belong to, V' = V J likewise.
+//
+// GB300 executes FP64 at a small fraction of the FP32 rate, and a round's update is
+// O(m^2) FP64 work, so the matrix is spread over a thread-block cluster: CTA r owns a
+// slab of rows of A and V and reads the partner rows it needs from the other CTAs'
+// shared memory.  Every CTA computes the (identical) rotation parameters of a round
+// itself, so one cluster barrier per round is the only cross-CTA synchronisation, and
+// the exit decision of each sweep is CTA 0's, read by all.
 constexpr int JMAX = 64;
-__global__ void __launch_bounds__(512)
+constexpr int JCL = 8;                 // CTAs per cluster
+constexpr int JROWS = JMAX / JCL;      // rows per CTA at most
+constexpr int JT = 256;
+
+__global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
 k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ theta,
          double *__restrict__ Yout, int ldy) {
-  extern __shared__ double jsm[];
-  typedef double Mat[JMAX][JMAX + 1];
-  Mat *A = reinterpret_cast<Mat *>(jsm);                       // A[2]
-  Mat *Vv = reinterpret_cast<Mat *>(jsm + 2 * JMAX * (JMAX + 1));  // Vv[2]
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  __shared__ double A[2][JROWS][JMAX + 1];
+  __shared__ double Vv[2][JROWS][JMAX + 1];
   __shared__ double rc[JMAX], rs[JMAX];
-  __shared__ double normA;  // per index: coefficient on itself and on its partner
   __shared__ int partner[JMAX];
-  __shared__ int rotated;
-  __shared__ double offsum;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int mm = (m + 1) & ~1;  // even number of players (m odd: one dummy)
-  for (int e = tid; e < mm * mm; e += nt) {
-    const int i = e / mm, j = e % mm;
+  __shared__ double diag[JMAX];
+  __shared__ int perm[JMAX];
+  __shared__ double part[JT / 32];
+  __shared__ double norm_part;  // this CTA's squared Frobenius norm, read by the others
+  __shared__ int rotated[2];    // per sweep parity; CTA 0's flag decides for the cluster
+  __shared__ int act[JMAX];     // index rotates in this round
+  __shared__ int round_rot[2];  // any pair rotates in this round (by running round parity)
+  const int tid = threadIdx.x;
+  const int mm = (m + 1) & ~1;          // even number of players (m odd: one dummy)
+  const int R = (mm + JCL - 1) / JCL;   // rows per CTA
+  const int r0 = rank * R;
+  // element (row, col) of A in buffer buf, wherever its row lives
+  auto Aat = [&](int buf, int row, int col) -> double {
+    const double *p = cluster.map_shared_rank(&A[buf][row % R][col], (unsigned)(row / R));
+    return *p;
+  };
+  double f = 0.0;
+  for (int e = tid; e < R * mm; e += JT) {
+    const int i = e / mm, j = e % mm, gi = r0 + i;
     double v = 0.0;
-    if (i < m && j < m) v = 0.5 * (G[(long long)j * ldg + i] + G[(long long)i * ldg + j]);
+    if (gi < m && j < m) v = 0.5 * (G[(long long)j * ldg + gi] + G[(long long)gi * ldg + j]);
     A[0][i][j] = v;
-    Vv[0][i][j] = (i == j) ? 1.0 : 0.0;
+    Vv[0][i][j] = (gi == j) ? 1.0 : 0.0;
+    f += v * v;
   }
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+  if ((tid & 31) == 0) part[tid >> 5] = f;
   __syncthreads();
   if (tid == 0) {
-    double f = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) f += A[0][i][j] * A[0][i][j];
-    normA = sqrt(f);
+    double t = 0.0;
+    for (int w = 0; w < JT / 32; ++w) t += part[w];
+    norm_part = t;
+    round_rot[0] = round_rot[1] = 0;
   }
-  __syncthreads();
+  cluster.sync();
+  double nrm2 = 0.0;
+  for (int c = 0; c < JCL; ++c) nrm2 += *cluster.map_shared_rank(&norm_part, (unsigned)c);
+  const double normA = sqrt(nrm2);
+  const double inv_norm = normA > 0.0 ? 1.0 / normA : 0.0;
   int cur = 0;
+  long long rnd = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) rotated = 0;
+    const int fl = sweep & 1;
     __syncthreads();
-    for (int r = 0; r < mm - 1; ++r) {
-      // pairs of this round (circle method): (mm-1, r), ((r+k) mod (mm-1), (r-k) mod (mm-1))
+    if (tid == 0) rotated[fl] = 0;
+    __syncthreads();
+    for (int r = 0; r < mm - 1; ++r, ++rnd) {
+      cluster.sync();  // A[cur] complete in every CTA
+      // pairs of this round (circle method): (mm-1, r), ((r+k) mod (mm-1), (r-k) mod (mm-1));
+      // all pairs in one warp: FP64 work is paid per warp instruction
       if (tid < mm / 2) {
         const int k = tid;
         int pi, qi;
@@ -176,77 +215,97 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ thet
           qi = (r - k + (mm - 1)) % (mm - 1);
         }
         const int p = pi < qi ? pi : qi, q = pi < qi ? qi : pi;
-        double c = 1.0, s = 0.0;
-        const double apq = A[cur][p][q];
-        if (q < m && apq != 0.0) {
-          const double app = A[cur][p][p], aqq = A[cur][q][q];
-          // rotate unless a_pq is negligible both relative to its diagonal pair and
-          // in absolute terms (rounding-level entries are not chased)
-          const double thr = 1e-18 * sqrt(fabs(app * aqq));
-          if (fabs(apq) > thr && fabs(apq) > 1e-17 * normA && fabs(apq) > 1e-300) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            double t;
-            if (fabs(tau) > 1e150)
-              t = 0.5 / tau;
-            else
-              t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-            rotated = 1;
+        double c = 1.0, sn = 0.0;
+        if (q < m) {
+          // the three loads go out together (one DSMEM round trip)
+          const double apq = Aat(cur, p, q), app = Aat(cur, p, p), aqq = Aat(cur, q, q);
+          // rotate unless a_pq is negligible relative to its diagonal pair or below the
+          // rounding noise that rotations of the largest entries leave behind (4 eps
+          // ||A||_F); chasing entries under that floor never terminates.  Squared forms:
+          // an FP64 square root or division costs about ten FMAs' latency on this GPU.
+          if (apq * apq > 1e-36 * fabs(app * aqq) && fabs(apq) > 8.9e-16 * normA) {
+            // t = tan(angle) zeroing a_pq: sign(d) a_pq / (|d| + sqrt(d^2 + a_pq^2)),
+            // d = (a_qq - a_pp)/2, in FP32 on normA-scaled values; the rotation below is
+            // orthogonal for any t, and a slightly inexact t leaves a_pq reduced by ~1e7
+            const float df = (float)(0.5 * (aqq - app) * inv_norm);
+            const float af = (float)(apq * inv_norm);
+            const float tf = (df >= 0.f ? af : -af) / (fabsf(df) + sqrtf(df * df + af * af));
+            const double t = (double)tf;
+            // c = (1 + t^2)^(-1/2): FP32 estimate and two FP64 Newton steps (orthogonal to
+            // FP64 rounding), s = t c
+            const double u = 1.0 + t * t;
+            double cc = (double)rsqrtf((float)u);
+            cc = cc * (1.5 - 0.5 * u * cc * cc);
+            cc = cc * (1.5 - 0.5 * u * cc * cc);
+            c = cc;
+            sn = t * cc;
+            rotated[fl] = 1;
+            round_rot[rnd & 1] = 1;
           }
         }
+        act[p] = act[q] = (sn != 0.0);
         // column p of J = c e_p - s e_q ; column q of J = s e_p + c e_q
         partner[p] = q;
         partner[q] = p;
         rc[p] = c;
-        rs[p] = -s;
+        rs[p] = -sn;
         rc[q] = c;
-        rs[q] = s;
+        rs[q] = sn;
       }
       __syncthreads();
+      // a round without rotations changes nothing: keep the buffers.  Every CTA computed
+      // the same parameters, so all of them take the same branch (and the barrier count
+      // per round does not depend on it either way).  The other parity's flag is reset
+      // here: its last readers passed the barrier above, its next writers come after the
+      // next cluster barrier.
+      const int any_rot = round_rot[rnd & 1];
+      if (tid == 0) round_rot[(rnd + 1) & 1] = 0;
+      if (!any_rot) continue;
       const int nxt = cur ^ 1;
-      for (int e = tid; e < mm * mm; e += nt) {
-        const int i = e / mm, j = e % mm;
-        const int pi = partner[i], pj = partner[j];
-        const double ci = rc[i], si = rs[i], cj = rc[j], sj = rs[j];
+      for (int e = tid; e < R * mm; e += JT) {
+        const int i = e / mm, j = e % mm, gi = r0 + i;
+        if (gi >= mm) continue;
+        if (!act[gi] && !act[j]) {  // both rotations are the identity here
+          A[nxt][i][j] = A[cur][i][j];
+          Vv[nxt][i][j] = Vv[cur][i][j];
+          continue;
+        }
+        const int pi = partner[gi], pj = partner[j];
+        const double ci = rc[gi], si = rs[gi], cj = rc[j], sj = rs[j];
         // A'[i][j] = sum_{a in {i,pi}, b in {j,pj}} J[a][i] J[b][j] A[a][b]
         const double v = ci * (cj * A[cur][i][j] + sj * A[cur][i][pj]) +
-                         si * (cj * A[cur][pi][j] + sj * A[cur][pi][pj]);
+                         si * (cj * Aat(cur, pi, j) + sj * Aat(cur, pi, pj));
         A[nxt][i][j] = v;
         Vv[nxt][i][j] = cj * Vv[cur][i][j] + sj * Vv[cur][i][pj];
       }
-      __syncthreads();
       cur = nxt;
     }
-    if (tid == 0) {
-      double off = 0.0;
-      for (int i = 0; i < m; ++i)
-        for (int j = i + 1; j < m; ++j) off += A[cur][i][j] * A[cur][i][j];
-      offsum = off;
-    }
+    // every CTA takes CTA 0's decision, so all of them run the same number of barriers;
+    // CTA 0 resets the other parity's flag next sweep, so this read cannot race with it
     __syncthreads();
-    if (!rotated || offsum == 0.0) break;
-    __syncthreads();
+    cluster.sync();
+    const int go = *cluster.map_shared_rank(&rotated[fl], 0u);
+    if (!go) break;
   }
-  // sort ascending (selection by one thread; m <= 64)
-  __shared__ int perm[JMAX];
-  if (tid == 0) {
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int i = 0; i < m; ++i) {
-      int best = i;
-      for (int j = i + 1; j < m; ++j)
-        if (A[cur][perm[j]][perm[j]] < A[cur][perm[best]][perm[best]]) best = j;
-      const int t = perm[i];
-      perm[i] = perm[best];
-      perm[best] = t;
-    }
+  cluster.sync();  // final A and V complete everywhere
+  for (int i = tid; i < m; i += JT) diag[i] = Aat(cur, i, i);
+  __syncthreads();
+  // ascending order by rank (ties by index)
+  for (int i = tid; i < m; i += JT) {
+    int rk = 0;
+    const double di = diag[i];
+    for (int j = 0; j < m; ++j) rk += (diag[j] < di) || (diag[j] == di && j < i);
+    perm[rk] = i;
   }
   __syncthreads();
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    Yout[(long long)j * ldy + i] = Vv[cur][i][perm[j]];
+  // Y[:, j] = V[:, perm[j]] for this CTA's rows; theta from CTA 0
+  for (int e = tid; e < R * m; e += JT) {
+    const int i = e / m, j = e % m, gi = r0 + i;
+    if (gi < m) Yout[(long long)j * ldy + gi] = Vv[cur][i][perm[j]];
   }
-  for (int j = tid; j < m; j += nt) theta[j] = A[cur][perm[j]][perm[j]];
+  if (rank == 0)
+    for (int j = tid; j < m; j += JT) theta[j] = diag[perm[j]];
+  cluster.sync();  // keep this CTA's shared memory alive until the others are done
 }
 
 // ------------------------------ Cholesky QR ----------------------------------
@@ -442,27 +501,29 @@ __global__ void k_sector_expand(int parity, int nx, int ny, int ncols, const dou
   }
 }
 
-// sign fix: one CTA per column, argmax |x| (lowest index on ties), flip if negative
+// sign fix: one CTA per column, argmax |x| (lowest index on ties), flip if negative.
+// |x| is compared through its bit pattern (sign cleared): for IEEE doubles that order is
+// the numeric one, and integer compares avoid the slow FP64 pipe.
 __global__ void k_fix_sign(long long nrows, double *X) {
   const long long c = blockIdx.x;
   double *x = X + c * nrows;
-  double best = -1.0;
+  unsigned long long best = 0;
   long long bi = 0;
   for (long long r = threadIdx.x; r < nrows; r += blockDim.x) {
-    const double a = fabs(x[r]);
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x[r]) & 0x7fffffffffffffffULL;
     if (a > best) {
       best = a;
       bi = r;
     }
   }
-  __shared__ double sb[256];
+  __shared__ unsigned long long sb[256];
   __shared__ long long si[256];
   sb[threadIdx.x] = best;
   si[threadIdx.x] = bi;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      const double a = sb[threadIdx.x + o];
+      const unsigned long long a = sb[threadIdx.x + o];
       const long long ai = si[threadIdx.x + o];
       if (a > sb[threadIdx.x] || (a == sb[threadIdx.x] && ai < si[threadIdx.x])) {
         sb[threadIdx.x] = a;
@@ -471,9 +532,9 @@ __global__ void k_fix_sign(long long nrows, double *X) {
     }
     __syncthreads();
   }
-  const double sgn = x[si[0]] < 0.0 ? -1.0 : 1.0;
+  const bool neg = __double_as_longlong(x[si[0]]) < 0;
   __syncthreads();
-  if (sgn < 0.0)
+  if (neg)
     for (long long r = threadIdx.x; r < nrows; r += blockDim.x) x[r] = -x[r];
 }
 
@@ -531,14 +592,8 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
                         cudaStream_t s) {
-  const size_t smem = 4 * (size_t)JMAX * (JMAX + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
   count_launch();
-  k_jacobi<<<1, 512, smem, s>>>(G, m, ldg, theta, Y, ldy);
+  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,

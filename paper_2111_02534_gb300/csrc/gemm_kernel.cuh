@@ -36,9 +36,10 @@ struct GemmArgs {
   void *C;
   long long ldc, bsc;
   int epi;
-  // EPI_HAPPLY (FP64 only): C += (V[(z % vmod) * vbs + m * ldv + n] - theta_z) * E[z][m][n]
+  // EPI_HAPPLY: C += (V[(z % vmod) * vbs + m * ldv + n] - theta_z) * E[z][m][n]
+  // (V and E in the accumulator's type)
   Opnd E;
-  const double *V;
+  const void *V;
   long long ldv, vbs, vmod;
   const double *theta;
   long long theta_div;
@@ -174,10 +175,9 @@ k_gemm(const GemmArgs g) {
       Acc c = acc[i][j];
       TC *dst = Cz + (long long)m * g.ldc + n;
       if (g.epi == EPI_HAPPLY) {
-        const double v = g.V[(z % g.vmod) * g.vbs + (long long)m * g.ldv + n];
-        const double p =
-            static_cast<const double *>(g.E.p)[z * g.E.bs + (long long)m * g.E.rs + n];
-        c = static_cast<Acc>(fma(v - th, p, static_cast<double>(c)));
+        const Acc v = static_cast<const Acc *>(g.V)[(z % g.vmod) * g.vbs + (long long)m * g.ldv + n];
+        const Acc p = static_cast<const Acc *>(g.E.p)[z * g.E.bs + (long long)m * g.E.rs + n];
+        c = fma(v - static_cast<Acc>(th), p, c);
       } else if (g.epi == EPI_DIVIDE2) {
         c = c / (lamM[m] + lamN[n] - static_cast<Acc>(g.sigma));
       } else if (g.epi == EPI_DIVIDE4) {

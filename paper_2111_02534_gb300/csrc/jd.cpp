@@ -30,13 +30,15 @@ namespace tps {
 struct PhaseTiming {
   bool on = false;
   std::vector<cudaEvent_t> all, free_ev;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[2];
-  double ms[2] = {0, 0}, flops[2] = {0, 0};
-  long long launches[2] = {0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[3];  // FP64 H, preconditioner, FP32 H
+  double ms[3] = {0, 0, 0}, flops[3] = {0, 0, 0};
+  long long launches[3] = {0, 0, 0};
   void reset(bool enable) {
     on = enable;
-    ms[0] = ms[1] = flops[0] = flops[1] = 0.0;
-    launches[0] = launches[1] = 0;
+    for (int k = 0; k < 3; ++k) {
+      ms[k] = flops[k] = 0.0;
+      launches[k] = 0;
+    }
   }
   cudaEvent_t get() {
     if (free_ev.empty()) {
@@ -50,7 +52,7 @@ struct PhaseTiming {
     return e;
   }
   void drain() {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       for (auto &pr : pend[k]) {
         cudaEventSynchronize(pr.second);
         float t = 0.f;
@@ -148,21 +150,26 @@ double prec_flops_per_vec(const DevOperator &op) {
   return 4.0 * op.N * s + (double)op.N;
 }
 
-void apply_h_timed(Ctx &c, const double *in, double *out, int nvec, const double *theta) {
+void apply_h_timed(Ctx &c, const double *in, double *out, int nvec, const double *theta,
+                   bool low) {
   PhaseTiming &t = c.w.tm;
+  const int kind = low ? 2 : 0;
   cudaEvent_t a = nullptr, b = nullptr;
   if (t.on) {
     a = t.get();
     b = t.get();
     cudaEventRecord(a, c.s);
   }
-  launch_apply_h(c.op, in, out, nvec, theta, 0.0, c.s);
+  if (low)
+    launch_apply_h_f32(c.op, in, out, nvec, theta, 0.0, c.ctx->ws, c.s);
+  else
+    launch_apply_h(c.op, in, out, nvec, theta, 0.0, c.s);
   if (t.on) {
     cudaEventRecord(b, c.s);
-    t.pend[0].push_back({a, b});
+    t.pend[kind].push_back({a, b});
   }
-  t.flops[0] += nvec * h_flops_per_vec(c.op);
-  t.launches[0] += 1;
+  t.flops[kind] += nvec * h_flops_per_vec(c.op);
+  t.launches[kind] += 1;
 }
 
 void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double shift) {
@@ -275,11 +282,12 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->kmax = kmax;
   w->steps = steps;
   const int mk2 = std::max(mmax, kmax);  // V2/HV2 also hold the final H Q and residuals
+  const int bw = std::max(b, kmax);       // widest block orthonormalised (refinement start)
   const long long nbig = 2LL * mmax + 2LL * mk2 + 2LL * (kmax + b) + 4LL * b +
-                         (long long)(steps + 1) * b + b;
+                         (long long)(steps + 1) * b + bw;
   const int q = kmax + b;
   const long long nsmall = 2LL * mmax * mmax + 2LL * mmax + 2LL * std::max(q, mmax) +
-                           2LL * (q + mmax + b) * std::max(b, q) + 2LL * q * q + (long long)b * b +
+                           2LL * (q + mmax + b) * std::max(b, q) + 2LL * q * q + (long long)bw * bw + bw +
                            /* gmres */ (long long)b * ((steps + 1) * steps + 2 * steps + (steps + 1) +
                                                       3 + steps + (steps + 1)) + 64;
   const size_t bytes = ((size_t)nbig * N + (size_t)nsmall) * sizeof(double) + 4096 * 4;
@@ -302,7 +310,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->P = take((long long)b * N);
   w->W = take((long long)b * N);
   w->Z = take((long long)(steps + 1) * b * N);
-  w->T2 = take((long long)b * N);
+  w->T2 = take((long long)bw * N);
   w->G = take((long long)mmax * mmax);
   w->Y = take((long long)mmax * mmax);
   w->theta = take(mmax);
@@ -312,7 +320,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->C = take(2LL * (q + mmax + b) * std::max(b, q));
   w->Mq = take((long long)q * q);
   w->Minv = take((long long)q * q);
-  w->Rinv = take((long long)b * b);
+  w->Rinv = take((long long)bw * bw);
   w->gm.Hb = take((long long)b * (steps + 1) * steps);
   w->gm.cs = take((long long)b * steps);
   w->gm.sn = take((long long)b * steps);
@@ -322,7 +330,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.y = take((long long)b * steps);
   w->gm.h = take((long long)b * (steps + 1));
   w->gm.nrm2 = take(b);
-  w->keep = reinterpret_cast<int *>(take(b));
+  w->keep = reinterpret_cast<int *>(take(bw));
   w->gm.done = reinterpret_cast<int *>(take(b));
   w->gm.mvalid = reinterpret_cast<int *>(take(b));
   if ((char *)p > (char *)w->arena + bytes) return set_error(ctx, TPS_ERR_CUDA, "arena overflow");
@@ -356,7 +364,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                     const double *KQt_cached, int nq_cached, const double *R,
                     const double *theta, int nsys, int steps, int use_prec, double shift,
                     double inner_tol, double *T, int *h_applies, int *prec_applies,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool direction_only, bool low) {
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, op.N};
   const long long N = op.N;
@@ -378,6 +386,13 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
   double *Z = w.Z;
   kt_inverse(c, Qt, nq, KQt, use_prec, shift, R, nsys, Z);
   if (use_prec) *prec_applies += nsys;
+  if (direction_only && sst == 1) {
+    // one GMRES step only scales z_0, and the caller normalises the correction: the
+    // correction direction is the projected, preconditioned residual -Kt^-1 r
+    launch_axpby_cols(nsys, N, -1.0, Z, N, 0.0, T, N, s);
+    TPS_CUDA_TRY(ctx, cudaGetLastError());
+    return TPS_OK;
+  }
   col_norms2(c, Z, nsys, w.gm.nrm2);
   launch_gmres_init(nsys, sst, w.gm.nrm2, w.gm, s);
   launch_scale_cols(nsys, N, Z, N, w.gm.scale, 0, Z, N, s);
@@ -389,7 +404,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
       launch_gram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s);
       launch_update(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s);
     }
-    apply_h_timed(c, zj, w.W, nsys, theta);
+    apply_h_timed(c, zj, w.W, nsys, theta, low);
     *h_applies += nsys;
     kt_inverse(c, Qt, nq, KQt, use_prec, shift, w.W, nsys, w.P);
     if (use_prec) *prec_applies += nsys;
@@ -427,10 +442,21 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   mmax = std::min(mmax, 64);
   if (mmin > mmax - b) mmin = std::max(b, mmax - b);
   if (mmin < k) mmin = std::min(k, mmax - b);
-  const int steps = opts.inner_steps > 0 ? opts.inner_steps : 10;
+  // GMRES steps per correction: fixed when given, else adaptive -- start with one step
+  // (the projected preconditioned residual) and widen when the outer residual stalls
+  const bool adaptive_steps = opts.inner_steps <= 0;
+  const int steps_max = adaptive_steps ? 10 : opts.inner_steps;
+  int steps = adaptive_steps ? 1 : opts.inner_steps;
   const int max_outer = opts.max_outer > 0 ? opts.max_outer : 500;
   const double inner_tol = opts.inner_tol > 0 ? opts.inner_tol : 1e-3;
-  if (mmax < 2 * b || steps > 40)
+  const bool mixed = opts.h_dtype == TPS_F32;
+  // refinement phase block (default: all k + guard pairs at once) and search space
+  const int rb = std::min(32, std::min(k, opts.refine_block > 0 ? opts.refine_block : k));
+  int rmmin = ((std::max(2 * k, 8) + rb - 1) / rb) * rb;
+  int rmmax = std::min(64, rmmin + 2 * rb);
+  if (rmmin > rmmax - rb) rmmin = std::max(rb, rmmax - rb);
+  const double switch_tol = opts.switch_tol > 0 ? std::max(opts.switch_tol, tol) : std::max(1e-6, tol);
+  if (mmax < 2 * b || steps_max > 40)
     return set_error(ctx, TPS_ERR_INVALID_ARG, "search space too small for the block");
 
   const DevOperator *opp = &ctx->full;
@@ -443,7 +469,8 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   const long long N = op.N;
   if (k_req > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
   if (k > N / 2) k = (int)(N / 2);
-  int st = alloc_workspace(ctx, N, mmax, b, k, steps);
+  int st = alloc_workspace(ctx, N, std::max(mmax, rmmax), std::max(b, rb), k,
+                           std::max(steps_max, opts.refine_inner_steps));
   if (st) return st;
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
@@ -484,12 +511,28 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       }
     }
   }
-  int m = 0, nlock = 0;
+  // one phase of the outer loop: starts from the bn columns in V, locks pairs whose
+  // residual reaches tol_p * ||H||_est into QX; low = true runs the H-applies in FP32
+  int m = 0, nlock = 0, outer = 0, bn_phase = bn;
+  bool converged = false;
+  // bp/mminp/mmaxp: block and search-space sizes of the phase; inner_low: FP32 H inside
+  // the GMRES correction solves
+  // G and Y are stored with the allocated search-space size as leading dimension, which
+  // covers every phase's m_max
+  const int ldG = w.mmax;
+  auto run_phase = [&](bool low, double tol_p, int bn0, int bp, int mminp, int mmaxp,
+                       bool fixed_steps, int steps_p, bool inner_low) -> int {
+  if (fixed_steps) steps = steps_p;
+  m = 0;
+  nlock = 0;
+  converged = false;
+  int bn = bn0;
   double cached_shift = NAN;
   int kq_valid = 0;  // locked columns of KQX valid for cached_shift
-  int outer = 0;
-  bool converged = false;
-  for (outer = 0; outer < max_outer; ++outer) {
+  double prev_res = INFINITY;
+  int stall = 0, prev_nlock = -1;
+  int st = TPS_OK;
+  for (; outer < max_outer; ++outer) {
     // (1) orthonormalise the new block against the locked vectors and the basis
     double *T = w.V + (long long)m * N;
     int rank = 0;
@@ -504,21 +547,21 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     bn = rank;
     // (2) H applied to the new block
     double *HT = w.HV + (long long)m * N;
-    apply_h_timed(c, T, HT, bn, nullptr);
+    apply_h_timed(c, T, HT, bn, nullptr, low);
     stt.h_applies += bn;
     // (3) projected matrix G = V^T H V, new columns and their mirror
-    if (m > 0) launch_gram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * mmax, mmax, 0, 1,
+    if (m > 0) launch_gram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * ldG, ldG, 0, 1,
                            ctx->gscr, s);
-    launch_gram(T, N, 0, bn, HT, N, 0, bn, N, w.G + (long long)m * mmax + m, mmax, 0, 1, ctx->gscr,
+    launch_gram(T, N, 0, bn, HT, N, 0, bn, N, w.G + (long long)m * ldG + m, ldG, 0, 1, ctx->gscr,
                 s);
-    launch_mirror_block(w.G, mmax, m, bn, s);
+    launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_jacobi_eigh(w.G, m, mmax, w.theta, w.Y, mmax, s);
-    const int nact = std::min(b, std::min(k - nlock, m));
+    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s);
+    const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
-    launch_update(w.V, N, 0, m, w.Y, mmax, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
-    launch_update(w.HV, N, 0, m, w.Y, mmax, 0, nact, 1.0, 0.0, w.HX, N, 0, N, 1, s);
+    launch_update(w.V, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
+    launch_update(w.HV, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, w.HX, N, 0, N, 1, s);
     launch_residual(nact, N, w.HX, X, w.theta, w.R, s);
     col_norms2(c, w.R, nact, w.nrm2);
     // (5) read back Ritz values and residual norms
@@ -530,7 +573,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     TPS_CUDA_TRY(ctx, cudaGetLastError());
     w.tm.drain();
     int nconv = 0;
-    while (nconv < nact && std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) <= tol * hnorm) {
+    while (nconv < nact && std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) <= tol_p * hnorm) {
       lam[nlock + nconv] = w.h_pinned[nconv];
       resid[nlock + nconv] = std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0)) / hnorm;
       ++nconv;
@@ -543,23 +586,39 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       ++outer;
       break;
     }
+    if (adaptive_steps && !fixed_steps && nconv < nact) {
+      // stall detection on the lowest unconverged pair: two outer iterations in a row
+      // without halving its residual widen the inner solve
+      const double res0 = std::sqrt(std::max(w.h_pinned[64 + nconv], 0.0));
+      if (nlock != prev_nlock) {
+        prev_nlock = nlock;
+        stall = 0;
+      } else {
+        stall = (res0 > 0.5 * prev_res) ? stall + 1 : 0;
+      }
+      prev_res = res0;
+      if (stall >= 2 && steps < steps_max) {
+        steps = std::min(2 * steps + 1, steps_max);
+        stall = 0;
+      }
+    }
     // (6) lock and/or restart: keep Ritz vectors nconv .. nconv+mk-1
     int nact2 = nact;
-    if (nconv > 0 || m + b > mmax) {
+    if (nconv > 0 || m + bp > mmaxp) {
       const int avail = m - nconv;
-      const int mk = (m + b > mmax) ? std::min(avail, mmin) : avail;
-      launch_update(w.V, N, 0, m, w.Y + (long long)nconv * mmax, mmax, 0, mk, 1.0, 0.0, w.V2, N, 0,
+      const int mk = (m + bp > mmaxp) ? std::min(avail, mminp) : avail;
+      launch_update(w.V, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.V2, N, 0,
                     N, 1, s);
-      launch_update(w.HV, N, 0, m, w.Y + (long long)nconv * mmax, mmax, 0, mk, 1.0, 0.0, w.HV2, N,
+      launch_update(w.HV, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.HV2, N,
                     0, N, 1, s);
       std::swap(w.V, w.V2);
       std::swap(w.HV, w.HV2);
       launch_copy_small(w.theta + nconv, w.theta2, mk, s);
       std::swap(w.theta, w.theta2);
-      launch_set_diag(w.G, mmax, w.theta, mk, s);
+      launch_set_diag(w.G, ldG, w.theta, mk, s);
       m = mk;
       ++stt.restarts;
-      nact2 = std::min(b, std::min(k - nlock, m));
+      nact2 = std::min(bp, std::min(k - nlock, m));
       X = w.QX + (long long)nlock * N;
       TPS_CUDA_TRY(ctx, cudaMemcpyAsync(X, w.V, (size_t)nact2 * N * sizeof(double),
                                         cudaMemcpyDeviceToDevice, s));
@@ -594,11 +653,32 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     // K^-1 of newly locked columns is recomputed each time (kq_valid tracks the cache)
     st = correction_impl(ctx, op, w.QX, nq, w.KQX, opts.use_prec ? std::min(kq_valid, nlock) : 0,
                          w.R, w.theta, nact2, steps, opts.use_prec, shift, inner_tol,
-                         w.V + (long long)m * N, &stt.h_applies, &stt.prec_applies, s);
+                         w.V + (long long)m * N, &stt.h_applies, &stt.prec_applies, s, true,
+                         low || inner_low);
     if (st) return st;
     kq_valid = nlock;
     stt.inner_steps += steps * nact2;
     bn = nact2;
+  }
+  return TPS_OK;
+  };
+  if (!mixed) {
+    st = run_phase(false, tol, bn_phase, b, mmin, mmax, false, 0, false);
+    if (st) return st;
+  } else {
+    // low-precision phase: FP32 mode products until every pair reaches switch_tol, then
+    // an FP64 refinement from that subspace, all pairs in the first block
+    st = run_phase(true, switch_tol, bn_phase, b, mmin, mmax, false, 0, false);
+    if (st) return st;
+    if (converged) {
+      const int nk = std::min(nlock, k);
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.V, w.QX, (size_t)nk * N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+      stt.restarts += 1;
+      st = run_phase(false, tol, nk, rb, rmmin, rmmax, opts.refine_inner_steps > 0,
+                     opts.refine_inner_steps, opts.refine_inner_dtype == TPS_F32);
+      if (st) return st;
+    }
   }
   stt.outer_iters = outer;
   // final Rayleigh quotients and residuals with a fresh H-apply of the locked vectors
@@ -607,7 +687,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   if (nlocked > 0) {
     const int nl = nlocked;
     double *HQ = w.V2;  // at least max(mmax, kmax) columns
-    apply_h_timed(c, w.QX, HQ, nl, nullptr);
+    apply_h_timed(c, w.QX, HQ, nl, nullptr, false);
     stt.h_applies += nl;
     launch_gram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nl, ctx->gscr, s);
     col_norms2(c, w.QX, nl, w.ref);
@@ -655,6 +735,9 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.prec_flops = w.tm.flops[1];
   stt.h_launches = w.tm.launches[0];
   stt.prec_launches = w.tm.launches[1];
+  stt.h32_ms = w.tm.ms[2];
+  stt.h32_flops = w.tm.flops[2];
+  stt.h32_launches = w.tm.launches[2];
   stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;
@@ -677,6 +760,11 @@ void tps_default_opts(tps_solver_opts *o) {
   o->guard = 2;
   o->smooth_start = 2;
   o->prec_dtype = TPS_F32;
+  o->h_dtype = TPS_F32;
+  o->switch_tol = 1e-6;
+  o->refine_block = 0;
+  o->refine_inner_steps = 0;
+  o->refine_inner_dtype = TPS_F64;
 }
 
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
@@ -729,7 +817,7 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
   ctx->sw->tm.reset(false);
   ctx->sw->prec_dtype = TPS_F64;
   st = correction_impl(ctx, ctx->full, Qt_dev, nq, nullptr, 0, R_dev, theta_dev, nsys, steps,
-                       use_prec, shift, 0.0, T_dev, &ha, &pa, stream);
+                       use_prec, shift, 0.0, T_dev, &ha, &pa, stream, false, false);
   if (st) return st;
   TPS_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
   return TPS_OK;

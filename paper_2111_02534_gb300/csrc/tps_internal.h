@@ -35,9 +35,12 @@ struct DevOperator {
   double *S[4] = {nullptr, nullptr, nullptr, nullptr};   // row-major, columns = eigenvectors
   double *ST[4] = {nullptr, nullptr, nullptr, nullptr};  // S^T
   double *lam[4] = {nullptr, nullptr, nullptr, nullptr}; // eigenvalues of K_k
-  float *Sf[4] = {nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the FP32 preconditioner
+  float *Sf[4] = {nullptr, nullptr, nullptr, nullptr};   // FP32 copies for the FP32 paths
   float *STf[4] = {nullptr, nullptr, nullptr, nullptr};
   float *lamf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *Kf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *KTf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *Vf = nullptr;
   double *V = nullptr;                                   // [N]
   std::vector<double> lam_h[4];                          // host copies (singularity test)
   double lam_min_sum = 0.0, lam_max_sum = 0.0;
@@ -57,6 +60,11 @@ void launch_apply_h(const DevOperator &op, const double *psi, double *out, int n
 // out[v] = (T - sigma)^-1 r[v] by fast diagonalisation (needs 2 * nvec * N workspace).
 void launch_apply_prec(const DevOperator &op, const double *r, double *out, int nvec,
                        double sigma, ApplyWorkspace &ws, cudaStream_t s);
+// out[v] = (H - theta_v) psi[v] with FP32 arithmetic (FP64 psi and out; psi is converted
+// once into the workspace, which must hold nvec * N floats).
+void launch_apply_h_f32(const DevOperator &op, const double *psi, double *out, int nvec,
+                        const double *theta_dev, double theta, ApplyWorkspace &ws,
+                        cudaStream_t s);
 // The same with FP32 arithmetic (FP64 r and out).
 void launch_apply_prec_f32(const DevOperator &op, const double *r, double *out, int nvec,
                            double sigma, ApplyWorkspace &ws, cudaStream_t s);
@@ -143,7 +151,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                     const double *KQt_cached, int nq_cached, const double *R,
                     const double *theta, int nsys, int steps, int use_prec, double shift,
                     double inner_tol, double *T, int *h_applies, int *prec_applies,
-                    cudaStream_t s);
+                    cudaStream_t s, bool direction_only, bool low);
 }  // namespace tps
 
 #define TPS_CUDA_TRY(ctx, expr)                                   \

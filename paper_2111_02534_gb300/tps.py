@@ -40,7 +40,9 @@ class SolverOpts(C.Structure):
     _fields_ = [("m_min", C.c_int), ("m_max", C.c_int), ("inner_steps", C.c_int),
                 ("max_outer", C.c_int), ("use_prec", C.c_int), ("prec_shift", C.c_double),
                 ("seed", C.c_ulonglong), ("inner_tol", C.c_double), ("timing", C.c_int),
-                ("guard", C.c_int), ("smooth_start", C.c_int), ("prec_dtype", C.c_int)]
+                ("guard", C.c_int), ("smooth_start", C.c_int), ("prec_dtype", C.c_int),
+                ("h_dtype", C.c_int), ("switch_tol", C.c_double), ("refine_block", C.c_int),
+                ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -49,7 +51,9 @@ class Stats(C.Structure):
                 ("hnorm_est", C.c_double), ("time_ms", C.c_double), ("h_ms", C.c_double),
                 ("prec_ms", C.c_double), ("h_flops", C.c_double), ("prec_flops", C.c_double),
                 ("h_launches", C.c_longlong), ("prec_launches", C.c_longlong),
-                ("kernel_launches", C.c_longlong), ("resid", C.c_double * 64)]
+                ("kernel_launches", C.c_longlong), ("h32_ms", C.c_double),
+                ("h32_flops", C.c_double), ("h32_launches", C.c_longlong),
+                ("resid", C.c_double * 64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "resid"}
@@ -191,9 +195,9 @@ class Context:
         return N.value, h.value
 
     # ---- operator applications -------------------------------------------------
-    def apply_h(self, psi, out, theta=0.0, stream=None):
+    def apply_h(self, psi, out, theta=0.0, stream=None, dtype=F64):
         nvec = psi.numel() // self.info()[0]
-        self._check(_lib.tps_apply_h(self._h, _ptr(psi), _ptr(out), nvec, theta, F64,
+        self._check(_lib.tps_apply_h(self._h, _ptr(psi), _ptr(out), nvec, theta, dtype,
                                      _stream(stream)), "apply_h")
 
     def apply_prec(self, r, out, theta, stream=None, dtype=F64):

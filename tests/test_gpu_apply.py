@@ -220,3 +220,27 @@ def test_apply_prec_2d_fp32():
     ref = apply_dense(P, r, -0.4)
     tol = prec_tol(P, -0.4) * np.finfo(np.float32).eps / np.finfo(float).eps
     assert np.max(np.linalg.norm(host(out) - ref, axis=1) / np.linalg.norm(ref, axis=1)) <= tol
+
+
+@pytest.mark.parametrize("dim,n", [(1, (64, 64)), (1, (130, 200)), (1, (512, 512)), (2, (8, 8, 6, 6))])
+def test_apply_h_fp32(dim, n):
+    # FP32 mode products: norm-wise error within 8 sqrt(n_max) eps_32 of ||H||_est ||psi||
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    if dim == 1:
+        L = (20.0, 15.0)
+        P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+        ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    else:
+        L = (5.0, 5.0, 4.0, 4.0)
+        P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+        ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    psi = random_block(3, P.N, 31)
+    out = torch.empty(3, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_h(dev(psi), out, -0.2, dtype=tps.F32)
+    got = host(out)
+    ref = P.apply_kron(psi, -0.2)
+    err = np.linalg.norm(got - ref, axis=1) / (P.norm_estimate() * np.linalg.norm(psi, axis=1))
+    tol = 8 * np.sqrt(max(n)) * np.finfo(np.float32).eps
+    assert err.max() <= tol, (err.max(), tol)
+    assert err.max() > 1e-13          # it really ran in FP32

@@ -122,15 +122,18 @@ def test_solve_harmonic_closed_form():
     assert np.max(np.abs(lam - levels) / levels) <= 1e-10
 
 
-@pytest.mark.parametrize("use_prec,block,prec_dtype", [(0, 4, 1), (1, 1, 1), (0, 1, 1), (1, 4, 0)])
-def test_solve_variants_agree(use_prec, block, prec_dtype):
+@pytest.mark.parametrize("use_prec,block,prec_dtype,h_dtype", [(0, 4, 1, 1), (1, 1, 1, 1), (0, 1, 1, 1),
+                                                         (1, 4, 0, 0), (1, 4, 1, 0)])
+def test_solve_variants_agree(use_prec, block, prec_dtype, h_dtype):
+    # FP64-only and mixed-precision solvers, no-prec-JDQR and the single-vector JDQR
     # no-prec-JDQR and the paper's single-vector JDQR reach the same eigenpairs
     require_gpu()
     n, L = (48, 48), (15.0, 15.0)
     P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
     ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
     lam, X, st = _solve(ctx, 3, 1, block, use_prec=use_prec, max_outer=3000,
-                        inner_steps=20 if not use_prec else 10, prec_dtype=prec_dtype)
+                        inner_steps=20 if not use_prec else 10, prec_dtype=prec_dtype,
+                        h_dtype=h_dtype)
     ref, _ = lowest_dense(P, 3, O_EVEN)
     assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
     _check_vectors(P, lam, X, parity_sign=1.0)
@@ -228,3 +231,21 @@ def test_solve_workload_2d_n48_certified():
     P = problem_2d(w.M, w.m, w.hbar, w.n, w.L, w.v0, w.sigma)
     res = _check_vectors(P, lam, X)
     assert np.all(res <= 1e-10 * np.abs(lam))
+
+
+@pytest.mark.parametrize("h_dtype", [0, 1])
+def test_full_size_fp64_and_mixed_agree(h_dtype):
+    # the FP64-only solver and the mixed-precision one on the 1d_n512 workload
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
+    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, h_dtype=h_dtype, timing=1)
+    ref = np.array(gold["evals"])
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+    if h_dtype == 1:
+        assert st.h32_launches > 0 and st.h32_flops > 0
+    else:
+        assert st.h32_launches == 0

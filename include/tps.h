@@ -103,6 +103,12 @@ int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma);
 int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, double sigma,
                     int n, double L, double *v0_out);
 
+/* Tile autotuning of the mode-product GEMMs (on by default, process-wide): the first
+ * launch of each GEMM shape times the candidate tile shapes on the caller's stream (which
+ * adds a host synchronisation to that first call) and later launches use the fastest.
+ * Results are bitwise identical for every tile shape.  Skipped during stream capture. */
+int tps_set_autotune(int on);
+
 /* Number of unknowns N and the norm estimate ||H||_est = sum_k |a_k| (pi/h_k)^2 + max|V|. */
 int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est);
 
@@ -194,6 +200,19 @@ void tps_default_opts(tps_solver_opts *opts);
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,
               int n_x0, const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
               tps_stats *stats, cudaStream_t stream);
+
+/* Batched parameter sweep (Sec. 5.2 solves a sequence of problems; the batched sweep
+ * over mass ratio and coupling): solves ninst independent problems, instance i described
+ * by its own context ctxs[i] (all on one device) with k[i] pairs, concurrently.  nstreams
+ * host threads (1..64) each drive a non-blocking CUDA stream of their own and take
+ * instances from a shared queue.  evals_host: [ninst][kstride] (k[i] <= kstride);
+ * evecs_dev[i]: device [k[i]][N_i]; stats: nullable [ninst]; status: [ninst] per-instance
+ * tps_status.  Returns TPS_OK when every instance succeeded, else the first failing status
+ * (or TPS_ERR_CUDA if a stream could not be created).  Synchronous.  kernel_launches in
+ * the per-instance stats count launches of all instances running at the same time. */
+int tps_solve_batch(tps_ctx **ctxs, int ninst, const int *k, int parity, double tol, int block,
+                    const tps_solver_opts *opts, double *evals_host, int kstride,
+                    double **evecs_dev, tps_stats *stats, int *status, int nstreams);
 
 /* ---- hot path: Jacobi-Davidson building blocks (device FP64) -------------
  * Column blocks are column-major: column c of an nrows x p block A starts at

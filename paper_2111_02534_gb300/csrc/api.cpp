@@ -17,6 +17,7 @@
 namespace tps {
 
 std::atomic<long long> g_kernel_launches{0};
+std::atomic<int> g_autotune{1};
 
 int set_error(tps_ctx *ctx, int code, const std::string &msg) {
   if (ctx) ctx->err = msg;
@@ -485,6 +486,11 @@ int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma) {
           }
   }
   return tps_set_potential(ctx, V.data(), 0);
+}
+
+int tps_set_autotune(int on) {
+  g_autotune.store(on ? 1 : 0);
+  return TPS_OK;
 }
 
 int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est) {

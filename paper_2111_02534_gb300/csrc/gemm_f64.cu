@@ -9,6 +9,11 @@
 
 namespace tps {
 
+gemm::TileCache &gemm::tile_cache() {
+  static TileCache cache;
+  return cache;
+}
+
 using gemm::GemmArgs;
 using gemm::base_args;
 using gemm::left;

@@ -15,6 +15,9 @@
 #pragma once
 
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <utility>
 
 #include "tps_internal.h"
 
@@ -221,15 +224,83 @@ void run(GemmArgs g, cudaStream_t s) {
 }
 
 template <typename Acc, typename TA, typename TB, typename TC>
-void gemm(GemmArgs g, cudaStream_t s) {
-  int tm, tn;
-  pick_tiles(g, tm, tn);
+void run_tiles(const GemmArgs &g, int tm, int tn, cudaStream_t s) {
 #define TPS_TILE_CASE(X, Y) \
   if (tm == X && tn == Y) return run<Acc, TA, TB, TC, X, Y>(g, s);
   TPS_TILE_CASE(64, 64) TPS_TILE_CASE(64, 48) TPS_TILE_CASE(64, 32)
   TPS_TILE_CASE(48, 64) TPS_TILE_CASE(48, 48) TPS_TILE_CASE(48, 32)
   TPS_TILE_CASE(32, 64) TPS_TILE_CASE(32, 48) TPS_TILE_CASE(32, 32)
 #undef TPS_TILE_CASE
+}
+
+// Tile autotuner.  The k-loop order of k_gemm does not depend on the tile shape, so every
+// candidate computes bitwise-identical results and the choice only changes speed.  The
+// first launch of a GEMM shape (precision, M, Nc, K, batch, phases) times the nine
+// candidates with CUDA events on the caller's stream (each run twice, best kept), caches
+// the fastest, and runs it; later launches of that shape use the cache.  Accumulating
+// epilogues (C += ...) cannot be re-run and keep the cost-model choice, as does every
+// launch while tuning is off or the stream is being captured.
+struct TileKey {
+  int prec, M, Nc, K0, K1, batch, nphase, epi;
+  bool operator==(const TileKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+struct TileKeyHash {
+  size_t operator()(const TileKey &k) const {
+    size_t h = 1469598103934665603ULL;
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&k);
+    for (size_t i = 0; i < sizeof(k); ++i) h = (h ^ p[i]) * 1099511628211ULL;
+    return h;
+  }
+};
+struct TileCache {
+  std::mutex mu;
+  std::unordered_map<TileKey, std::pair<int, int>, TileKeyHash> best;
+};
+TileCache &tile_cache();
+
+template <typename Acc, typename TA, typename TB, typename TC>
+void gemm(GemmArgs g, cudaStream_t s) {
+  int tm, tn;
+  pick_tiles(g, tm, tn);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (!autotune_enabled() || g.epi == EPI_ACCUM || cap != cudaStreamCaptureStatusNone)
+    return run_tiles<Acc, TA, TB, TC>(g, tm, tn, s);
+  TileKey key{(int)sizeof(Acc) * 100 + (int)sizeof(TA) * 10 + (int)sizeof(TC), g.M, g.Nc,
+              g.K[0], g.nphase > 1 ? g.K[1] : 0, g.batch, g.nphase, g.epi};
+  TileCache &tc = tile_cache();
+  {
+    std::lock_guard<std::mutex> lock(tc.mu);
+    auto it = tc.best.find(key);
+    if (it != tc.best.end()) return run_tiles<Acc, TA, TB, TC>(g, it->second.first, it->second.second, s);
+  }
+  const int cand[3] = {32, 48, 64};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  int bm = tm, bn = tn;
+  for (int a : cand)
+    for (int b : cand)
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        run_tiles<Acc, TA, TB, TC>(g, a, b, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          bm = a;
+          bn = b;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(tc.mu);
+    tc.best[key] = {bm, bn};
+  }
+  run_tiles<Acc, TA, TB, TC>(g, bm, bn, s);
 }
 
 // One left mode product: C[z] = A (M x M, shared) * B[z] (M x Nc), rows strided by rs.

@@ -17,6 +17,9 @@ namespace tps {
 // Every kernel launch of the library is counted (reported by tps_solve's stats).
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+// GEMM tile autotuning switch (tps_set_autotune).
+extern std::atomic<int> g_autotune;
+inline bool autotune_enabled() { return g_autotune.load(std::memory_order_relaxed) != 0; }
 
 // ---------------------------------------------------------------------------
 // A discretised Kronecker-sum operator resident on the device:

@@ -76,6 +76,7 @@ _sig = {
     "tps_two_body_v0": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                   C.c_double, C.c_int, C.c_double, _dp]),
     "tps_get_info": (C.c_int, [_vp, C.POINTER(_ll), _dp]),
+    "tps_set_autotune": (C.c_int, [C.c_int]),
     "tps_apply_h": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
     "tps_apply_prec": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
     "tps_default_opts": (None, [C.POINTER(SolverOpts)]),
@@ -89,6 +90,10 @@ _sig = {
     "tps_correction": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int,
                                  C.c_double, _vp, _vp]),
     "tps_gram_noalloc": (C.c_int, [_vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
+    "tps_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int,
+                                  C.c_double, C.c_int, C.POINTER(SolverOpts), _dp, C.c_int,
+                                  C.POINTER(C.c_void_p), C.POINTER(Stats), C.POINTER(C.c_int),
+                                  C.c_int]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -129,6 +134,27 @@ def gram_noalloc(A, p, B, q, nrows, G, ldg=None, stream=None):
                                _stream(stream))
     if st != OK:
         raise TpsError(st, "tps_gram_noalloc")
+
+
+def solve_batch(contexts, ks, parity, tol, block, evecs, opts=None, nstreams=8):
+    """Solve independent problems concurrently (tps_solve_batch).  contexts: list of
+    Context; ks: pairs per instance; evecs: list of float64 CUDA tensors [k_i, N_i].
+    Returns (list of eigenvalue arrays, list of Stats, list of statuses)."""
+    n = len(contexts)
+    kstride = max(ks) if n else 1
+    ctx_arr = (C.c_void_p * n)(*[c._h for c in contexts])
+    k_arr = (C.c_int * n)(*ks)
+    ev = (C.c_double * (n * kstride))()
+    vec_arr = (C.c_void_p * n)(*[e.data_ptr() for e in evecs])
+    stats = (Stats * n)()
+    status = (C.c_int * n)()
+    st = _lib.tps_solve_batch(ctx_arr, n, k_arr, parity, tol, block,
+                              C.byref(opts) if opts is not None else None, ev, kstride, vec_arr,
+                              stats, status, nstreams)
+    if st != OK and st != ERR_NOT_CONVERGED:
+        raise TpsError(st, "tps_solve_batch")
+    lam = [np.array(ev[i * kstride: i * kstride + ks[i]]) for i in range(n)]
+    return lam, list(stats), list(status)
 
 
 def two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L) -> float:

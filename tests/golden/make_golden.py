@@ -3,7 +3,8 @@
 Calls only oracle/ (never the CUDA path).  Usage: python tests/golden/make_golden.py [name ...]
   1d_n512 : M/m = 40, n = 512 per coordinate on [-20, 20), v0 tuned to E0 = 1e-3 on the
             y grid (heavy-light reduced mass), sigma = 1, 8 lowest x-even eigenpairs.
-  2d_n16  : 2D, M/m = 20, n = 16 per component on [-20, 20)... see WORKLOADS_2D below.
+  2d_n16  : 2D, M/m = 20, n = 16 per component on [-10, 10), v0 = 2, 4 lowest pairs.
+  sweep   : the 256 instances of inputs.sweep_instances(), 4 lowest x-even pairs each.
 """
 import json
 import os
@@ -48,7 +49,33 @@ def make_2d_n16():
             "seconds": time.time() - t, "method": "oracle.eig.lowest_iterative (LOBPCG), all states"}
 
 
-MAKERS = {"1d_n512": make_1d_n512, "2d_n16": make_2d_n16}
+def _sweep_one(args):
+    import os
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    i, inst = args
+    _, _, mu_hl = coefficients_from_masses(inst["M"], inst["m"], 1.0)
+    v0 = tune_v0(inst["E0"], mu_hl, inst["sigma"], GAUSS, inst["n"], inst["L"])
+    P = problem_1d(inst["M"], inst["m"], 1.0, (inst["n"], inst["n"]), (inst["L"], inst["L"]), v0,
+                   inst["sigma"])
+    lam, X = lowest_iterative(P, 4, X_EVEN, tol=1e-13, extra=4, seed=i)
+    res = residual_norms(P, X, lam) / P.norm_estimate()
+    return {"index": i, **inst, "v0": v0, "evals": lam.tolist(), "rel_resid": res.tolist()}
+
+
+def make_sweep():
+    # the 256-instance sweep: 4 lowest x-even eigenpairs per instance
+    import multiprocessing as mp
+    from paper_2111_02534_gb300.inputs import sweep_instances
+    insts = sweep_instances()
+    t = time.time()
+    with mp.get_context("spawn").Pool(int(os.environ.get("GOLDEN_PROCS", "8"))) as pool:
+        out = pool.map(_sweep_one, list(enumerate(insts)), chunksize=1)
+    return {"workload": "sweep", "count": len(out), "instances": out, "evals": [o["evals"] for o in out],
+            "seconds": time.time() - t,
+            "method": "oracle.eig.lowest_iterative (LOBPCG), x-even sector, 4 pairs per instance"}
+
+
+MAKERS = {"1d_n512": make_1d_n512, "2d_n16": make_2d_n16, "sweep": make_sweep}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(MAKERS)

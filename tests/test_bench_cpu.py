@@ -45,8 +45,12 @@ def test_replica_aggregation_gloo_two_ranks():
 
 def test_accuracy_gate():
     import bench
-    ref = np.array([-2e-3, -1e-3, 5e-4])
-    lam = ref * (1 + np.array([0.0, 5e-11, 2e-10]))
+    ref = np.array([-2e-3, -1e-3, 5e-4, 4e-3])
+    lam = ref * (1 + np.array([0.0, 5e-11, 2e-10, 2e-10]))
     n, worst = bench.passing_pairs(lam, ref)
-    assert n == 2 and worst == pytest.approx(2e-10, rel=1e-3)
+    # the third level is measured against |lambda_0| = 2e-3 (error 5e-11), the fourth fails
+    assert n == 3 and worst == pytest.approx(2e-10, rel=1e-3)
+    lam = ref.copy()
+    lam[2] += 3e-13                       # 6e-10 of |lambda_2| but 1.5e-10 of |lambda_0|
+    assert bench.passing_pairs(lam, ref)[0] == 3
     assert bench.aggregate(3.0, 5, 1) == (3.0, 5)

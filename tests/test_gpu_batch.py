@@ -1,0 +1,68 @@
+"""Batched sweep (tps_solve_batch): independent instances of uneven grid size solved
+concurrently, each eigenvalue within 1e-10 of the oracle's (tests/golden/evals_sweep.json,
+written by oracle-only code), and identical to solving the instances one by one."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import torch, require_gpu, host
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _contexts(insts):
+    from paper_2111_02534_gb300 import tps
+    ctxs = []
+    for inst in insts:
+        c = tps.Context(1, 0)
+        c.set_masses(inst["M"], inst["m"], 1.0)
+        c.set_grid([inst["n"], inst["n"]], [inst["L"], inst["L"]])
+        mu = inst["M"] * inst["m"] / (inst["M"] + inst["m"])
+        v0 = tps.two_body_v0(1, mu, 1.0, inst["E0"], tps.GAUSS, inst["sigma"], inst["n"], inst["L"])
+        assert v0 == pytest.approx(inst["v0"], rel=1e-11)
+        c.set_pair_potential(tps.GAUSS, v0, inst["sigma"])
+        ctxs.append(c)
+    return ctxs
+
+
+def test_batch_matches_oracle_and_serial():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    with open(os.path.join(GOLD, "evals_sweep.json")) as f:
+        gold = json.load(f)["instances"][:12]
+    assert len({g["n"] for g in gold}) >= 3       # uneven grid sizes in one batch
+    ctxs = _contexts(gold)
+    evecs = [torch.empty(4, c.info()[0], dtype=torch.float64, device="cuda") for c in ctxs]
+    lam, stats, status = tps.solve_batch(ctxs, [4] * len(ctxs), tps.X_EVEN, 1e-12, 4, evecs,
+                                         nstreams=6)
+    assert all(s == tps.OK for s in status)
+    for l, g in zip(lam, gold):
+        ref = np.array(g["evals"])
+        # relative to |lambda_i|, floored at the ground-state binding energy |lambda_0|
+        scale = np.maximum(np.abs(ref), abs(ref[0]))
+        assert np.max(np.abs(l - ref) / scale) <= 1e-10
+    # the same instances one at a time give the same eigenvalues
+    for i in (0, 5):
+        ev = torch.empty(4, ctxs[i].info()[0], dtype=torch.float64, device="cuda")
+        l1, _ = ctxs[i].solve(4, tps.X_EVEN, 1e-12, 4, ev)
+        assert np.max(np.abs(l1 - lam[i]) / np.abs(lam[i])) <= 1e-11
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_argument_checks():
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    c = tps.Context(1, 0)
+    c.set_masses(20.0, 1.0, 1.0)
+    c.set_grid([16, 16], [5.0, 5.0])
+    c.set_pair_potential(tps.GAUSS, 1.0, 1.0)
+    ev = torch.empty(2, c.info()[0], dtype=torch.float64, device="cuda")
+    with pytest.raises(tps.TpsError):
+        tps.solve_batch([c], [2], tps.X_EVEN, 1e-12, 2, [ev], nstreams=0)
+    lam, stats, status = tps.solve_batch([], [], tps.X_EVEN, 1e-12, 2, [])
+    assert lam == []
+    c.close()

@@ -61,3 +61,34 @@ def test_2d_dense_and_iterative_agree():
     a = tune_v0(0.2, 1.0, 1.0, GAUSS, 24, 8.0, dim=2)
     b = tune_v0_2d_iterative(0.2, 1.0, 1.0, GAUSS, 24, 8.0)
     assert a == pytest.approx(b, rel=1e-11)
+
+
+def _v0_rayleigh_long_double(v0, E0, mu, sigma, n, L):
+    """v0 as the Rayleigh quotient psi^T (T + E0) psi / psi^T F psi of the pencil, in
+    extended precision, with T from the closed-form D2 entries and psi the FP64 ground
+    state of T - v0 F.  The quotient is stationary at the eigenvector, so an FP64 psi
+    gives v0 to extended-precision rounding."""
+    ld = np.longdouble
+    pi = 4 * np.arctan(ld(1))          # pi to extended precision (np.pi is FP64)
+    x = -ld(L) + np.arange(n, dtype=ld) * (2 * ld(L) / n)
+    h = 2 * pi / n
+    d = np.subtract.outer(np.arange(n), np.arange(n))
+    with np.errstate(divide="ignore"):
+        D = -np.where(d % 2 == 0, ld(1), ld(-1)) / (2 * np.sin(d.astype(ld) * h / 2) ** 2)
+    D[np.arange(n), np.arange(n)] = -ld(n) ** 2 / 12 - ld(1) / 6     # -pi^2/(3h^2) - 1/6
+    T = -D * (pi / ld(L)) ** 2 / (2 * ld(mu))
+    f = np.exp(-(np.abs(x) / ld(sigma)) ** 2)
+    w, V = np.linalg.eigh(T.astype(np.float64) - v0 * np.diag(f.astype(np.float64)))
+    psi = V[:, 0].astype(ld)
+    return float((psi @ (T @ psi) + ld(E0) * (psi @ psi)) / (psi @ (f * psi)))
+
+
+@pytest.mark.parametrize("E0,mu,sigma,n", [(1e-4, 0.95, 2.0, 128), (3e-4, 0.97, 0.5, 192),
+                                           (0.3, 0.8, 1.0, 128)])
+def test_v0_small_binding_extended_precision(E0, mu, sigma, n):
+    # near threshold T + E0 is ill-conditioned (cond ~ 1e6); v0 must still be accurate to
+    # the FP64 representation of the grid operators (~2e-14 observed), which a
+    # Cholesky-based generalized eigensolver does not reach (1e-11 .. 1e-10 observed)
+    v0 = tune_v0(E0, mu, sigma, GAUSS, n, 20.0)
+    ref = _v0_rayleigh_long_double(v0, E0, mu, sigma, n, 20.0)
+    assert abs(v0 - ref) <= 1e-13 * ref

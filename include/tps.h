@@ -51,12 +51,16 @@ typedef enum tps_status {
   TPS_ERR_NOMEM = -4,         /* a device allocation failed */
   TPS_ERR_SINGULAR = -5,      /* the preconditioner's shift hits the kinetic spectrum */
   TPS_ERR_NOT_CONVERGED = -6, /* solver hit its iteration cap; results valid for stats->n_converged pairs */
-  TPS_ERR_TIMEOUT = -7        /* reserved: a bounded device wait expired */
+  TPS_ERR_TIMEOUT = -7        /* a bounded device wait expired (tps_device_status, tps_solve) */
 } tps_status;
 
 enum { TPS_GAUSS = 0, TPS_LORENTZ3 = 1 };          /* f_G = exp(-xi^2), f_L = (1+xi^2)^-3 */
 enum { TPS_ANY = 0, TPS_X_EVEN = 1, TPS_X_ODD = 2 }; /* heavy-exchange sector (Sec. 5.1) */
-enum { TPS_F64 = 0, TPS_F32 = 1 };                   /* arithmetic of apply calls (data stay FP64) */
+enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2 };  /* arithmetic of apply calls (data stay FP64) */
+/* TPS_F64_TC: FP64-accurate mode products emulated on the BF16 tensor cores by error-free
+ * splitting into six-bit digit slices per operand row (9 for the wave function, 10 for the
+ * mode matrices; Ozaki scheme), exact FP32 accumulation per digit level, FP64
+ * recombination; 1D H-apply only. */
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -67,6 +71,10 @@ int tps_create(tps_ctx **out, int dim, int device);
 int tps_destroy(tps_ctx *ctx);
 const char *tps_last_error(const tps_ctx *ctx);
 const char *tps_status_string(int status);
+/* Synchronise the context's device and report whether a tensor-core kernel of this
+ * context gave up a bounded wait since the last call (TPS_ERR_TIMEOUT; its outputs are
+ * then invalid) -- each such wait ends after about one second instead of hanging. */
+int tps_device_status(tps_ctx *ctx);
 
 /* ---- problem definition ------------------------------------------------- */
 
@@ -117,7 +125,11 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est);
 /* Eq. tensor_op1D (1D) and Eq. tensor_op2D (2D): out = (H - theta) psi for nvec
  * vectors, H = sum_k a_k (I x .. x D2_k x .. x I) + diag(V).  psi_dev, out_dev:
  * device, [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32:
- * FP32 arithmetic (error ~ n eps_32 ||H|| |psi|), the low-precision phase's operator. */
+ * FP32 arithmetic (error ~ n eps_32 ||H|| |psi|), the low-precision phase's operator;
+ * TPS_F64_TC (1D only): FP64-accurate products on the tensor cores (error below
+ * 2^-53 n of row max x column max per product, like FP64 arithmetic).  The first
+ * TPS_F64_TC call on a context builds the operator's digit slices (a few MB) and a
+ * slice workspace of up to 256 MB; TPS_ERR_INVALID_ARG in 2D. */
 int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, double theta,
                 int dtype, cudaStream_t stream);
 
@@ -161,6 +173,9 @@ typedef struct tps_solver_opts {
   int refine_block;   /* block size of the FP64 refinement phase (0: k + guard, at most 32) */
   int refine_inner_steps; /* GMRES steps in the refinement phase (0: adaptive as above) */
   int refine_inner_dtype; /* arithmetic of H inside the refinement's GMRES (TPS_F64 default) */
+  int h64_dtype;      /* how every FP64 H-apply of the solver runs (refinement phase, FP64-only
+                         mode, final Rayleigh quotients): TPS_F64 (FP64 FMA pipe, default) or
+                         TPS_F64_TC (tensor-core emulation, 1D only) */
 } tps_solver_opts;
 
 typedef struct tps_stats {

@@ -202,6 +202,9 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
     TPS_CUDA_TRY(ctx, cudaMalloc((void **)&op.Vf, op.N * sizeof(float)));
     TPS_CUDA_TRY(ctx, cudaMemset(op.Vf, 0, op.N * sizeof(float)));
   }
+  // the uploads above go through the legacy default stream, which the solver's
+  // non-blocking streams do not wait for: finish them before any kernel can read them
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));
   return TPS_OK;
 }
 
@@ -268,6 +271,8 @@ void free_operator(DevOperator &op) {
     op.Sf[k] = op.STf[k] = op.lamf[k] = op.Kf[k] = op.KTf[k] = nullptr;
     op.lam_h[k].clear();
   }
+  free_tc_operator(op.tc);
+  op.tc = nullptr;
   cudaFree(op.V);
   cudaFree(op.Vf);
   op.V = nullptr;
@@ -450,6 +455,7 @@ int tps_set_potential(tps_ctx *ctx, const double *V, int on_device) {
     free_operator(ctx->sect[p]);
     ctx->sect_ready[p] = false;
   }
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));  // uploads complete (see above)
   ctx->have_V = true;
   return TPS_OK;
 }
@@ -616,9 +622,11 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
                 int dtype, cudaStream_t stream) {
   int st = check_ready(ctx);
   if (st) return st;
-  if ((dtype != TPS_F64 && dtype != TPS_F32) || nvec < 0 || (nvec > 0 && (!psi_dev || !out_dev)) ||
-      !std::isfinite(theta))
+  if ((dtype != TPS_F64 && dtype != TPS_F32 && dtype != TPS_F64_TC) || nvec < 0 ||
+      (nvec > 0 && (!psi_dev || !out_dev)) || !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_h arguments");
+  if (dtype == TPS_F64_TC && ctx->dim != 1)
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "TPS_F64_TC is implemented for 1D only");
   const char *a = (const char *)psi_dev, *b = (const char *)out_dev;
   const size_t bytes = (size_t)nvec * ctx->full.N * sizeof(double);
   if (nvec > 0 && a < b + bytes && b < a + bytes)
@@ -632,11 +640,25 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
                          (double *)out_dev + (long long)v0 * ctx->full.N, nv, nullptr, theta,
                          ctx->ws, stream);
     }
+  } else if (dtype == TPS_F64_TC) {
+    TPS_CUDA_TRY(ctx, launch_apply_h_tc(ctx->full, (const double *)psi_dev, (double *)out_dev,
+                                        nvec, nullptr, theta, stream));
   } else {
     launch_apply_h(ctx->full, (const double *)psi_dev, (double *)out_dev, nvec, nullptr, theta,
                    stream);
   }
   TPS_CUDA_TRY(ctx, cudaGetLastError());
+  return TPS_OK;
+}
+
+int tps_device_status(tps_ctx *ctx) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  TPS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  TPS_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  int flag = tc_operator_status(ctx->full);
+  for (int p = 0; p < 3; ++p) flag |= tc_operator_status(ctx->sect[p]);
+  if (flag < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
+  if (flag) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   return TPS_OK;
 }
 

@@ -145,9 +145,20 @@ constexpr int JCL = 8;                 // CTAs per cluster
 constexpr int JROWS = JMAX / JCL;      // rows per CTA at most
 constexpr int JT = 256;
 
+// Warm start (mp > 0): the leading mp x mp block of G is the projection onto a basis
+// whose Ritz pairs (Y[:mp, :mp], theta[:mp]) the previous call returned, and only the
+// trailing columns are new.  The kernel then diagonalises A0 = Q0^T G Q0 with
+// Q0 = diag(Y_prev, I): its leading block is diag(theta_prev) (exactly, up to the
+// rounding the previous call left below its threshold), and the coupling block
+// Y_prev^T G_12 holds the previous Ritz vectors' residuals against the new columns, so
+// far fewer sweeps are needed than from the identity.  The result is Q0 V.  theta and
+// Y are read before the first cluster barrier / before the final write, so they may be
+// updated in place.
+constexpr int JOUT = (JROWS * JMAX + JT - 1) / JT;  // output elements per thread
+
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
-k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ theta,
-         double *__restrict__ Yout, int ldy) {
+k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
+         int mp) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   __shared__ double A[2][JROWS][JMAX + 1];
@@ -170,11 +181,27 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ thet
     const double *p = cluster.map_shared_rank(&A[buf][row % R][col], (unsigned)(row / R));
     return *p;
   };
+  // symmetric part of G
+  auto Gs = [&](int r, int c) -> double {
+    return 0.5 * (G[(long long)c * ldg + r] + G[(long long)r * ldg + c]);
+  };
   double f = 0.0;
   for (int e = tid; e < R * mm; e += JT) {
     const int i = e / mm, j = e % mm, gi = r0 + i;
     double v = 0.0;
-    if (gi < m && j < m) v = 0.5 * (G[(long long)j * ldg + gi] + G[(long long)gi * ldg + j]);
+    if (gi < m && j < m) {
+      if (gi < mp && j < mp) {
+        v = (gi == j) ? theta[gi] : 0.0;
+      } else if (gi < mp) {  // (Y_prev^T G)[gi][j] = sum_a Y[a][gi] G[a][j]
+#pragma unroll 8
+        for (int a = 0; a < mp; ++a) v = fma(Yout[(long long)gi * ldy + a], Gs(a, j), v);
+      } else if (j < mp) {   // (G Y_prev)[gi][j], the same terms in the same order
+#pragma unroll 8
+        for (int a = 0; a < mp; ++a) v = fma(Yout[(long long)j * ldy + a], Gs(gi, a), v);
+      } else {
+        v = Gs(gi, j);
+      }
+    }
     A[0][i][j] = v;
     Vv[0][i][j] = (gi == j) ? 1.0 : 0.0;
     f += v * v;
@@ -298,10 +325,35 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *__restrict__ thet
     perm[rk] = i;
   }
   __syncthreads();
-  // Y[:, j] = V[:, perm[j]] for this CTA's rows; theta from CTA 0
-  for (int e = tid; e < R * m; e += JT) {
-    const int i = e / m, j = e % m, gi = r0 + i;
-    if (gi < m) Yout[(long long)j * ldy + gi] = Vv[cur][i][perm[j]];
+  // Y[:, j] = (Q0 V)[:, perm[j]] for this CTA's rows, formed in registers first: with a
+  // warm start every CTA reads the previous Y, which is overwritten in place
+  double yv[JOUT];
+#pragma unroll
+  for (int t = 0; t < JOUT; ++t) {
+    const int e = tid + t * JT;
+    double v = 0.0;
+    if (e < R * m) {
+      const int i = e / m, j = e % m, gi = r0 + i;
+      const int pj = perm[j];
+      if (gi < mp) {  // sum_a Y_prev[gi][a] V[a][pj]; row a of V lives in CTA a / R
+#pragma unroll 8
+        for (int a = 0; a < mp; ++a)
+          v = fma(Yout[(long long)a * ldy + gi],
+                  *cluster.map_shared_rank(&Vv[cur][a % R][pj], (unsigned)(a / R)), v);
+      } else if (gi < m) {
+        v = Vv[cur][i][pj];
+      }
+    }
+    yv[t] = v;
+  }
+  cluster.sync();  // every CTA is done reading the previous Y
+#pragma unroll
+  for (int t = 0; t < JOUT; ++t) {
+    const int e = tid + t * JT;
+    if (e < R * m) {
+      const int i = e / m, j = e % m, gi = r0 + i;
+      if (gi < m) Yout[(long long)j * ldy + gi] = yv[t];
+    }
   }
   if (rank == 0)
     for (int j = tid; j < m; j += JT) theta[j] = diag[perm[j]];
@@ -591,9 +643,9 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 }
 
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s) {
+                        cudaStream_t s, int mp) {
   count_launch();
-  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy);
+  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,

@@ -73,6 +73,7 @@ struct PhaseTiming {
 struct SolverWorkspace {
   PhaseTiming tm;
   int prec_dtype = TPS_F64;  // arithmetic of the preconditioner applications
+  int h64_dtype = TPS_F64;   // FP64 H-applies on the FMA pipe or the tensor cores
   long long N = 0;
   int mmax = 0, b = 0, kmax = 0, steps = 0;
   double *arena = nullptr;
@@ -162,6 +163,8 @@ void apply_h_timed(Ctx &c, const double *in, double *out, int nvec, const double
   }
   if (low)
     launch_apply_h_f32(c.op, in, out, nvec, theta, 0.0, c.ctx->ws, c.s);
+  else if (c.w.h64_dtype == TPS_F64_TC)
+    launch_apply_h_tc(c.op, in, out, nvec, theta, 0.0, c.s);  // errors surface at the next sync
   else
     launch_apply_h(c.op, in, out, nvec, theta, 0.0, c.s);
   if (t.on) {
@@ -335,6 +338,8 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.mvalid = reinterpret_cast<int *>(take(b));
   if ((char *)p > (char *)w->arena + bytes) return set_error(ctx, TPS_ERR_CUDA, "arena overflow");
   TPS_CUDA_TRY(ctx, cudaMemset(w->arena, 0, bytes));
+  // the memset runs on the legacy default stream; the solve's stream may be non-blocking
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));
   TPS_CUDA_TRY(ctx, cudaMallocHost((void **)&w->h_pinned, 4096 * sizeof(double)));
   TPS_CUDA_TRY(ctx, cudaMallocHost((void **)&w->hi_pinned, 4096 * sizeof(int)));
   // the Gram scratch must hold the largest skinny product of the loop
@@ -476,6 +481,12 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
   w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64 : TPS_F32;
+  w.h64_dtype = opts.h64_dtype == TPS_F64_TC ? TPS_F64_TC : TPS_F64;
+  if (w.h64_dtype == TPS_F64_TC) {
+    if (op.nmodes != 2)
+      return set_error(ctx, TPS_ERR_INVALID_ARG, "h64_dtype TPS_F64_TC is implemented for 1D only");
+    TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));  // allocation errors here, not mid-solve
+  }
   const long long launches0 = g_kernel_launches.load();
   double hnorm = 0.0;
   tps_get_info(ctx, nullptr, &hnorm);
@@ -531,6 +542,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   int kq_valid = 0;  // locked columns of KQX valid for cached_shift
   double prev_res = INFINITY;
   int stall = 0, prev_nlock = -1;
+  int warm_mp = 0;  // leading block of G already diagonalised by the last Jacobi call
   int st = TPS_OK;
   for (; outer < max_outer; ++outer) {
     // (1) orthonormalise the new block against the locked vectors and the basis
@@ -557,7 +569,8 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s);
+    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp);
+    warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
     launch_update(w.V, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
@@ -617,6 +630,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       std::swap(w.theta, w.theta2);
       launch_set_diag(w.G, ldG, w.theta, mk, s);
       m = mk;
+      warm_mp = 0;  // G's leading block is diagonal by construction
       ++stt.restarts;
       nact2 = std::min(bp, std::min(k - nlock, m));
       X = w.QX + (long long)nlock * N;
@@ -741,6 +755,12 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;
+  if (w.h64_dtype == TPS_F64_TC) {
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const int f = tc_operator_status(op);
+    if (f < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
+    if (f) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+  }
   if (!converged) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "outer-iteration cap reached");
   return TPS_OK;
 }
@@ -765,6 +785,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->refine_block = 0;
   o->refine_inner_steps = 0;
   o->refine_inner_dtype = TPS_F64;
+  o->h64_dtype = TPS_F64;
 }
 
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,

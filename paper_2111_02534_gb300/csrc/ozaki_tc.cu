@@ -1,0 +1,627 @@
+// FP64-accurate mode products on the tcgen05 tensor cores (1D H-apply, Eq. tensor_op1D).
+//
+// GB300's FP64 FMA pipe peaks at 1.26 TFLOP/s while its BF16 tensor cores run three
+// orders of magnitude faster, so the FP64 mode products are emulated by error-free
+// splitting (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), with BF16 digits and exact FP32
+// accumulation:
+//
+//  * Every row r of an FP64 operand X (rows = output index, columns = contraction index)
+//    gets the exponent E_r with |X[r][k]| < 2^E_r.  X[r][k] 2^(S*beta - E_r) is rounded to
+//    an integer and written in S balanced base-2^beta digits d_1..d_S (beta = 6),
+//    |d_1| <= 64 and |d_i| <= 32 otherwise, so
+//    X[r][k] = 2^E_r sum_i d_i[r][k] 2^(-i beta) up to 2^(E_r - S beta - 1).  Small
+//    integers are exact in BF16.
+//  * C = A B^T is the sum over digit pairs (i, j) of 2^(E_A + E_B - (i+j) beta) times the
+//    integer matrix D_ij = d_i(A) d_j(B)^T.  Pairs with i + j <= 11 (1-based) are kept.  The
+//    pairs of one level l = i + j accumulate in one FP32 TMEM accumulator: every partial
+//    sum is an integer of magnitude at most K 2^10 (l + 1) < 2^24 for K <= 1365, hence
+//    exact.
+//  * The wave function gets 9 digits (54 bits, rounding error random from element to
+//    element).  The mode matrices get 10: their rows are dominated by the diagonal, so a
+//    per-row scale leaves the small far-off-diagonal entries with an absolute rounding of
+//    2^-55 of the diagonal, and since D2 is circulant these errors repeat in every row;
+//    their row sum would act on smooth wave functions like a constant potential of
+//    ~1e-13 (measured as a uniform eigenvalue shift).  The tenth digit (pairs with the
+//    wave function's leading digit) puts that sum near 1e-16.
+//  * The epilogue converts each level to an integer, combines the levels in two int64
+//    Horner sums (exact) and forms the FP64 result with one conversion pair and one FMA.
+//
+// The 1D H-apply out = K_x P + P K_y^T + (V - theta) P (P = psi as n_x x n_y) runs as two
+// such products in the transposed orientation (rows of C = the y index, so that one warp
+// stores 32 consecutive y of an output row):
+//    C1[y][x] = sum_y' K_y[y][y'] P[x][y']     A = slices of K_y,  B = slices of P
+//    C2[y][x] = sum_x' P^T[y][x'] K_x[x][x']   A = slices of P^T,  B = slices of K_x
+// with the potential term fused into the first epilogue and the second accumulating.
+// Operand tiles reach shared memory by TMA (128-byte swizzle, K-major), one thread issues
+// tcgen05.mma into tensor memory, and four warps drain it.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "ozaki_tc.cuh"
+#include "tps_internal.h"
+
+namespace tps {
+
+namespace {
+
+constexpr int kBeta = 6;
+constexpr int kPsiSlices = 9;  // wave-function digits: 54 bits
+constexpr int kOpSlices = 10;  // mode-matrix digits: 60 bits (see below)
+constexpr int kLevels = 10;    // digit-pair levels kept: i + j <= 9 (0-based)
+constexpr int kMaxSlices = 10;
+constexpr int kBM = 128;       // output rows per CTA (TMEM lanes)
+constexpr int kBN = 48;        // output columns per CTA; kLevels * kBN <= 512 TMEM columns
+constexpr int kBK = 64;        // contraction depth per stage (128-byte rows)
+constexpr int kAStages = 4;
+constexpr int kBStages = 2;
+constexpr int kThreads = 128;
+constexpr uint32_t kATileBytes = kBM * 128;
+constexpr uint32_t kTmemCols = 512;
+static_assert(kLevels * kBN <= (int)kTmemCols, "levels must fit in tensor memory");
+static_assert(kBN % 16 == 0 && kBN >= 16 && kBN <= 256, "N of a 128-row MMA");
+
+__host__ __device__ constexpr uint32_t b_slice_bytes() { return kBN * 128; }
+
+size_t oz_smem_bytes(int SB) {
+  return 1024 /* alignment slack */ + (size_t)kBStages * SB * b_slice_bytes() +
+         (size_t)kAStages * kATileBytes + 8 * (2 * kAStages + 2 * kBStages + 1) + 16;
+}
+
+// -------------------------------- splitting ----------------------------------
+__device__ __forceinline__ unsigned raw_exponent(double x) {
+  return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// BF16 bit pattern of a small integer (|d| <= 255), exact.
+__device__ __forceinline__ uint16_t bf16_of_int(int d) {
+  if (d == 0) return 0;
+  const unsigned s = d < 0 ? 0x8000u : 0u;
+  const unsigned a = d < 0 ? -d : d;
+  const int p = 31 - __clz(a);                    // a in [2^p, 2^(p+1))
+  const unsigned man = (a << (7 - p)) & 0x7Fu;    // p <= 7
+  return (uint16_t)(s | ((unsigned)(p + 127) << 7) | man);
+}
+
+// round(x * 2^(S*beta - E)) with E = raw_max - 1022 the row exponent, by integer
+// arithmetic on the FP64 fields (subnormals are flushed: they lie 2^-1022 below any row
+// scale that matters here).  |result| <= 2^(S*beta).
+__device__ __forceinline__ long long scaled_integer(double x, unsigned raw_max, int S) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  if (ex == 0 || raw_max == 0) return 0;
+  const long long mant = (long long)((u & ((1ULL << 52) - 1)) | (1ULL << 52));
+  const int E = (int)raw_max - 1022;
+  const int sh = ex - 1075 + S * kBeta - E;
+  long long q;
+  if (sh >= 0) {
+    q = mant << sh;                     // |x| < 2^E keeps this below 2^(S beta)
+  } else if (sh > -63) {
+    q = (mant + (1LL << (-sh - 1))) >> (-sh);
+  } else {
+    q = 0;
+  }
+  return (u >> 63) ? -q : q;
+}
+
+// Row and column exponent maxima of a batch of R x C FP64 matrices (C contiguous):
+// rexp[b][r] = max_c raw exponent, cexp[b][c] = max_r (either may be null).  The
+// arrays must be zeroed before.  Block 32 x 8 over a 32 x 32 tile.
+__global__ void k_exponents(const double *__restrict__ X, int R, int C, long long bs,
+                            unsigned *__restrict__ rexp, unsigned *__restrict__ cexp) {
+  const int b = blockIdx.z;
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * 32;
+  const double *Xb = X + b * bs;
+  unsigned cmax = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + threadIdx.y + 8 * j;
+    const unsigned e = (r < R && c < C) ? raw_exponent(Xb[(long long)r * C + c]) : 0u;
+    cmax = e > cmax ? e : cmax;
+    if (rexp) {
+      unsigned m = e;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+      }
+      if (threadIdx.x == 0 && r < R && m) atomicMax(&rexp[(long long)b * R + r], m);
+    }
+  }
+  if (cexp) {
+    __shared__ unsigned red[8][32];
+    red[threadIdx.y][threadIdx.x] = cmax;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+      unsigned m = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) m = red[k][threadIdx.x] > m ? red[k][threadIdx.x] : m;
+      if (c < C && m) atomicMax(&cexp[(long long)b * C + c], m);
+    }
+  }
+}
+
+// Digit slices of a batch of R x C FP64 matrices:
+//   natural   outN[b][i][r][c] (ld ldn)  with the row exponents rexp  (may be null)
+//   transposed outT[b][i][c][r] (ld ldt) with the column exponents cexp (may be null)
+// Slice i = 0 holds the most significant digit.
+__global__ void k_split(const double *__restrict__ X, int R, int C, long long bs, int S,
+                        const unsigned *__restrict__ rexp, uint16_t *__restrict__ outN, int ldn,
+                        const unsigned *__restrict__ cexp, uint16_t *__restrict__ outT, int ldt) {
+  __shared__ double tile[32][33];
+  const int b = blockIdx.z;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const double *Xb = X + b * bs;
+  const long long sN = (long long)R * ldn, sT = (long long)C * ldt;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + threadIdx.y + 8 * j, c = c0 + threadIdx.x;
+    double x = 0.0;
+    if (r < R && c < C) x = Xb[(long long)r * C + c];
+    tile[threadIdx.y + 8 * j][threadIdx.x] = x;
+    if (outN && r < R && c < C) {
+      long long q = scaled_integer(x, rexp[(long long)b * R + r], S);
+      uint16_t *dst = outN + (long long)b * S * sN + (long long)r * ldn + c;
+      for (int i = S - 1; i > 0; --i) {
+        long long d = q & 63;
+        if (d >= 32) d -= 64;
+        dst[i * sN] = bf16_of_int((int)d);
+        q = (q - d) >> kBeta;
+      }
+      dst[0] = bf16_of_int((int)q);
+    }
+  }
+  if (!outT) return;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + threadIdx.y + 8 * j, r = r0 + threadIdx.x;
+    if (r < R && c < C) {
+      long long q = scaled_integer(tile[threadIdx.x][threadIdx.y + 8 * j],
+                                   cexp[(long long)b * C + c], S);
+      uint16_t *dst = outT + (long long)b * S * sT + (long long)c * ldt + r;
+      for (int i = S - 1; i > 0; --i) {
+        long long d = q & 63;
+        if (d >= 32) d -= 64;
+        dst[i * sT] = bf16_of_int((int)d);
+        q = (q - d) >> kBeta;
+      }
+      dst[0] = bf16_of_int((int)q);
+    }
+  }
+}
+
+
+// ------------------------------ the product kernel ------------------------------
+struct OzArgs {
+  int M, N, K;
+  int SA, SB, L;                 // digit slices of A and of B, digit-pair levels kept
+  int zA, zB;                    // slice-plane offset per vector (slices if per vector, 0 if shared)
+  const unsigned *expA;          // raw row exponents of A [.][M], vector stride expA_bs
+  long long expA_bs;
+  const unsigned *expB;          // raw row exponents of B [.][N]
+  long long expB_bs;
+  double *out;                   // out[v * out_bs + n * ldo + m]
+  long long ldo, out_bs;
+  int epi;                       // 0 store, 1 accumulate, 2 store + (V - theta_v) psi
+  const double *V;               // [n * ldo + m]
+  const double *psi;             // psi[v * out_bs + n * ldo + m]
+  const double *theta_dev;       // theta_v (null: theta0)
+  double theta0;
+  int *err;                      // nonzero after a timed-out wait
+};
+
+__device__ __forceinline__ double pow2i(int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// One CTA computes the 128 x kBN tile (m0, n0) of C = A B^T for vector blockIdx.z.
+// Warp 0 lane 0 loads (TMA), warp 1 lane 0 issues the MMAs, warp 2 owns the tensor
+// memory, all four warps run the epilogue (warp w reads TMEM lanes 32w .. 32w + 31).
+__global__ void __launch_bounds__(kThreads, 1)
+k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const OzArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int SA = g.SA, SB = g.SB, L = g.L;
+  const uint32_t bstage = (uint32_t)SB * b_slice_bytes();
+  uint8_t *sB = base;
+  uint8_t *sA = base + kBStages * bstage;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sA + kAStages * kATileBytes);
+  uint64_t *fullA = bars, *emptyA = bars + kAStages;
+  uint64_t *fullB = bars + 2 * kAStages, *emptyB = fullB + kBStages;
+  uint64_t *accum = emptyB + kBStages;
+  uint32_t *holder = reinterpret_cast<uint32_t *>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, v = blockIdx.z;
+  const int KB = (g.K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kAStages; ++i) {
+      tc::mbar_init(&fullA[i], 1);
+      tc::mbar_init(&emptyA[i], 1);
+    }
+    for (int i = 0; i < kBStages; ++i) {
+      tc::mbar_init(&fullB[i], 1);
+      tc::mbar_init(&emptyB[i], 1);
+    }
+    tc::mbar_init(accum, 1);
+    abort_flag = 0;
+    tc::fence_barrier_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 2) tc::tmem_alloc(holder, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *holder;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: per K block, all B slices (one stage), then the A slices one by one
+    int lastA[kAStages], lastB[kBStages];
+    for (int i = 0; i < kAStages; ++i) lastA[i] = -1;
+    for (int i = 0; i < kBStages; ++i) lastB[i] = -1;
+    bool ok = true;
+    int acount = 0;
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      const int sb = kb % kBStages;
+      const uint32_t rb = (uint32_t)(kb / kBStages);
+      if (!tc::mbar_wait(&emptyB[sb], (rb & 1u) ^ 1u, g.err, 1)) {
+        ok = false;
+        break;
+      }
+      tc::mbar_arrive_expect_tx(&fullB[sb], bstage);
+      for (int j = 0; j < SB; ++j)
+        tc::tma_load_3d(sB + sb * bstage + j * b_slice_bytes(), &tmB, &fullB[sb], kb * kBK, n0,
+                        v * g.zB + j);
+      lastB[sb] = (int)(rb & 1u);
+      for (int i = 0; i < SA; ++i, ++acount) {
+        const int sa = acount % kAStages;
+        const uint32_t ra = (uint32_t)(acount / kAStages);
+        if (!tc::mbar_wait(&emptyA[sa], (ra & 1u) ^ 1u, g.err, 2)) {
+          ok = false;
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&fullA[sa], kATileBytes);
+        tc::tma_load_3d(sA + sa * kATileBytes, &tmA, &fullA[sa], kb * kBK, m0, v * g.zA + i);
+        lastA[sa] = (int)(ra & 1u);
+      }
+    }
+    if (!ok) {
+      // wind down: let every copy this thread started land before the CTA exits
+      atomicExch(&abort_flag, 1);
+      for (int i = 0; i < kAStages; ++i)
+        if (lastA[i] >= 0) tc::mbar_wait(&fullA[i], (uint32_t)lastA[i], nullptr, 0);
+      for (int i = 0; i < kBStages; ++i)
+        if (lastB[i] >= 0) tc::mbar_wait(&fullB[i], (uint32_t)lastB[i], nullptr, 0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: level l = i + j of the digit pairs accumulates at column l * kBN
+    const uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
+    bool ok = true;
+    int acount = 0;
+    uint32_t seen = 0;  // levels already written (the first MMA of a level overwrites it)
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      const int sb = kb % kBStages;
+      const uint32_t rb = (uint32_t)(kb / kBStages);
+      if (!tc::mbar_wait(&fullB[sb], rb & 1u, g.err, 3)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t bbase = tc::smem_addr(sB + sb * bstage);
+      for (int i = 0; i < SA; ++i, ++acount) {
+        const int sa = acount % kAStages;
+        const uint32_t ra = (uint32_t)(acount / kAStages);
+        if (!tc::mbar_wait(&fullA[sa], ra & 1u, g.err, 4)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t abase = tc::smem_addr(sA + sa * kATileBytes);
+        for (int j = 0; j < SB && i + j < L; ++j) {
+          const int l = i + j;
+          const uint32_t d = tmem + (uint32_t)(l * kBN);
+          const uint32_t fresh = ((seen >> l) & 1u) ^ 1u;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            tc::mma_bf16(d, tc::smem_desc_sw128(abase + kk * 32),
+                         tc::smem_desc_sw128(bbase + j * b_slice_bytes() + kk * 32), idesc,
+                         (kk == 0 && fresh) ? 0u : 1u);
+          seen |= 1u << l;
+        }
+        tc::mma_commit(&emptyA[sa]);  // the A stage is free once these MMAs are done
+      }
+      if (ok) tc::mma_commit(&emptyB[sb]);
+    }
+    if (!ok) atomicExch(&abort_flag, 1);
+    // signal the epilogue (after a failure: only so that nothing is in flight at exit)
+    tc::mma_commit(accum);
+  }
+  __syncwarp();
+
+  // ---- epilogue
+  bool ok = tc::mbar_wait(accum, 0, g.err, 5);
+  ok = __all_sync(0xffffffffu, ok);
+  const int aborted = __shfl_sync(0xffffffffu, *((volatile int *)&abort_flag), 0);
+  tc::tc_fence_after();
+  if (ok && !aborted) {
+    const int m = m0 + 32 * warp + lane;
+    const bool mvalid = m < g.M;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const int Em = mvalid ? (int)g.expA[v * g.expA_bs + m] - 1022 : 0;
+    const double th = (g.epi == 2) ? (g.theta_dev ? g.theta_dev[v] : g.theta0) : 0.0;
+    const int h = (L + 1) / 2;
+    for (int c = 0; c < kBN / 8; ++c) {
+      long long hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
+      for (int l = 0; l < L; ++l) {
+        uint32_t r[8];
+        tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const long long d = (long long)__float2int_rn(__uint_as_float(r[q]));
+          if (l < h)
+            hi[q] = hi[q] * 64 + d;
+          else
+            lo[q] = lo[q] * 64 + d;
+        }
+      }
+      if (!mvalid) continue;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + c * 8 + q;
+        if (n >= g.N) break;
+        const int En = (int)g.expB[v * g.expB_bs + n] - 1022;
+        // sum_l D_l 2^(-beta (l + 2)): hi carries levels 0 .. h-1, lo levels h .. L-1
+        const double val = fma((double)lo[q], pow2i(Em + En - kBeta * (L + 1)),
+                               (double)hi[q] * pow2i(Em + En - kBeta * (h + 1)));
+        const long long idx = (long long)n * g.ldo + m;
+        double *o = g.out + v * g.out_bs + idx;
+        if (g.epi == 0)
+          *o = val;
+        else if (g.epi == 1)
+          *o += val;
+        else
+          *o = fma(g.V[idx] - th, g.psi[v * g.out_bs + idx], val);
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+
+// ------------------------------------ host ------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map over a stack of BF16 slice planes [planes][rows][ld] (K = cols contiguous):
+// boxes of 64 columns x box_rows rows of one plane, 128-byte swizzle, zero fill outside
+// cols x rows.
+bool make_slice_map(CUtensorMap *map, const void *base, int cols, int rows, long long planes,
+                    int ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (ld * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows};
+  const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int round8(int n) { return (n + 7) & ~7; }
+
+dim3 split_grid(int R, int C, int batch) { return dim3((C + 31) / 32, (R + 31) / 32, batch); }
+
+void launch_exponents(const double *X, int R, int C, long long bs, int batch, unsigned *rexp,
+                      unsigned *cexp, cudaStream_t s) {
+  count_launch();
+  k_exponents<<<split_grid(R, C, batch), dim3(32, 8), 0, s>>>(X, R, C, bs, rexp, cexp);
+}
+
+void launch_split(const double *X, int R, int C, long long bs, int batch, int S,
+                  const unsigned *rexp, uint16_t *outN, int ldn, const unsigned *cexp,
+                  uint16_t *outT, int ldt, cudaStream_t s) {
+  count_launch();
+  k_split<<<split_grid(R, C, batch), dim3(32, 8), 0, s>>>(X, R, C, bs, S, rexp, outN, ldn, cexp,
+                                                          outT, ldt);
+}
+
+cudaError_t launch_oz(const CUtensorMap &mA, const CUtensorMap &mB, const OzArgs &g, int nvec,
+                      cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oz_smem_bytes(kMaxSlices));
+  });
+  if (attr != cudaSuccess) return attr;
+  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + kBN - 1) / kBN, nvec);
+  count_launch();
+  k_oz_gemm<<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tensor-core (BF16 digit) form of a 1D operator: slices of K_y and K_x, fixed, and a
+// workspace for the slices of up to `chunk` vectors per launch.
+struct TcOperator {
+  int So = kOpSlices, Sp = kPsiSlices;
+  int nx = 0, ny = 0, ldx = 0, ldy = 0, chunk = 0;
+  uint16_t *Ky = nullptr, *Kx = nullptr;    // [So][ny][ldy], [So][nx][ldx]
+  unsigned *eKy = nullptr, *eKx = nullptr;  // raw row exponents [ny], [nx]
+  uint16_t *Pn = nullptr, *PT = nullptr;    // [chunk][Sp][nx][ldy], [chunk][Sp][ny][ldx]
+  unsigned *eP = nullptr;                   // row exponents [chunk][nx], then column [chunk][ny]
+  int *err = nullptr;                       // device flag of timed-out waits
+  CUtensorMap mKy, mKx, mPn, mPT;
+};
+
+void free_tc_operator(TcOperator *t) {
+  if (!t) return;
+  cudaFree(t->Ky);
+  cudaFree(t->Kx);
+  cudaFree(t->eKy);
+  cudaFree(t->eKx);
+  cudaFree(t->Pn);
+  cudaFree(t->PT);
+  cudaFree(t->eP);
+  cudaFree(t->err);
+  delete t;
+}
+
+// Build the tensor-core form of a 1D operator (idempotent).  Returns a cudaError_t.
+cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s) {
+  if (op.tc) return cudaSuccess;
+  if (op.nmodes != 2) return cudaErrorInvalidValue;
+  TcOperator *t = new TcOperator();
+  t->nx = op.n[0];
+  t->ny = op.n[1];
+  t->ldx = round8(t->nx);
+  t->ldy = round8(t->ny);
+  const int So = t->So, Sp = t->Sp;
+  // vectors per launch: as many as keep the slice workspace near 256 MB
+  const long long per_vec = 2LL * Sp * ((long long)t->nx * t->ldy + (long long)t->ny * t->ldx);
+  long long ch = (256LL << 20) / per_vec;
+  t->chunk = (int)(ch < 1 ? 1 : (ch > 64 ? 64 : ch));
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  chk(cudaMalloc(&t->Ky, 2LL * So * t->ny * t->ldy));
+  chk(cudaMalloc(&t->Kx, 2LL * So * t->nx * t->ldx));
+  chk(cudaMalloc(&t->eKy, sizeof(unsigned) * t->ny));
+  chk(cudaMalloc(&t->eKx, sizeof(unsigned) * t->nx));
+  chk(cudaMalloc(&t->Pn, 2LL * Sp * t->chunk * t->nx * t->ldy));
+  chk(cudaMalloc(&t->PT, 2LL * Sp * t->chunk * t->ny * t->ldx));
+  chk(cudaMalloc(&t->eP, sizeof(unsigned) * t->chunk * (t->nx + t->ny)));
+  chk(cudaMalloc(&t->err, sizeof(int)));
+  if (e != cudaSuccess) {
+    free_tc_operator(t);
+    return e;
+  }
+  chk(cudaMemsetAsync(t->err, 0, sizeof(int), s));
+  chk(cudaMemsetAsync(t->eKy, 0, sizeof(unsigned) * t->ny, s));
+  chk(cudaMemsetAsync(t->eKx, 0, sizeof(unsigned) * t->nx, s));
+  launch_exponents(op.K[1], t->ny, t->ny, 0, 1, t->eKy, nullptr, s);
+  launch_split(op.K[1], t->ny, t->ny, 0, 1, So, t->eKy, t->Ky, t->ldy, nullptr, nullptr, 0, s);
+  launch_exponents(op.K[0], t->nx, t->nx, 0, 1, t->eKx, nullptr, s);
+  launch_split(op.K[0], t->nx, t->nx, 0, 1, So, t->eKx, t->Kx, t->ldx, nullptr, nullptr, 0, s);
+  chk(cudaGetLastError());
+  bool ok = make_slice_map(&t->mKy, t->Ky, t->ny, t->ny, So, t->ldy, kBM) &&
+            make_slice_map(&t->mKx, t->Kx, t->nx, t->nx, So, t->ldx, kBN) &&
+            make_slice_map(&t->mPn, t->Pn, t->ny, t->nx, (long long)Sp * t->chunk, t->ldy, kBN) &&
+            make_slice_map(&t->mPT, t->PT, t->nx, t->ny, (long long)Sp * t->chunk, t->ldx, kBM);
+  if (e == cudaSuccess && !ok) e = cudaErrorInvalidValue;
+  if (e != cudaSuccess) {
+    free_tc_operator(t);
+    return e;
+  }
+  op.tc = t;
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *out, int nvec,
+                              const double *theta_dev, double theta, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  cudaError_t e = ensure_tc_operator(op, s);
+  if (e != cudaSuccess) return e;
+  TcOperator &t = *op.tc;
+  const int nx = t.nx, ny = t.ny, So = t.So, Sp = t.Sp;
+  for (int v0 = 0; v0 < nvec; v0 += t.chunk) {
+    const int nv = nvec - v0 < t.chunk ? nvec - v0 : t.chunk;
+    const double *P = psi + (long long)v0 * op.N;
+    double *O = out + (long long)v0 * op.N;
+    unsigned *erow = t.eP, *ecol = t.eP + (long long)t.chunk * nx;
+    e = cudaMemsetAsync(t.eP, 0, sizeof(unsigned) * t.chunk * (nx + ny), s);
+    if (e != cudaSuccess) return e;
+    launch_exponents(P, nx, ny, op.N, nv, erow, ecol, s);
+    launch_split(P, nx, ny, op.N, nv, Sp, erow, t.Pn, t.ldy, ecol, t.PT, t.ldx, s);
+    OzArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.L = kLevels;
+    g.M = ny;
+    g.N = nx;
+    g.out = O;
+    g.ldo = ny;
+    g.out_bs = op.N;
+    g.err = t.err;
+    // K_y P^T with the potential term: A = K_y slices (shared), B = psi slices
+    g.K = ny;
+    g.SA = So;
+    g.SB = Sp;
+    g.zA = 0;
+    g.zB = Sp;
+    g.expA = t.eKy;
+    g.expA_bs = 0;
+    g.expB = erow;
+    g.expB_bs = nx;
+    g.epi = 2;
+    g.V = op.V;
+    g.psi = P;
+    g.theta_dev = theta_dev ? theta_dev + v0 : nullptr;
+    g.theta0 = theta;
+    e = launch_oz(t.mKy, t.mPn, g, nv, s);
+    if (e != cudaSuccess) return e;
+    // P^T K_x^T accumulated: A = psi^T slices, B = K_x slices (shared)
+    g.K = nx;
+    g.SA = Sp;
+    g.SB = So;
+    g.zA = Sp;
+    g.zB = 0;
+    g.expA = ecol;
+    g.expA_bs = ny;
+    g.expB = t.eKx;
+    g.expB_bs = 0;
+    g.epi = 1;
+    e = launch_oz(t.mPT, t.mKx, g, nv, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Reads (synchronously) and clears the operator's timed-out-wait flag.
+int tc_operator_status(const DevOperator &op) {
+  if (!op.tc) return 0;
+  int h = 0;
+  if (cudaMemcpy(&h, op.tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (h && (cudaMemset(op.tc->err, 0, sizeof(int)) != cudaSuccess ||
+            cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess))
+    return -1;
+  return h;
+}
+
+}  // namespace tps

@@ -48,6 +48,8 @@ struct DevOperator {
   std::vector<double> lam_h[4];                          // host copies (singularity test)
   double lam_min_sum = 0.0, lam_max_sum = 0.0;
   bool owns = true;
+  // tensor-core (BF16 digit slice) form of the mode matrices, built on first use
+  mutable struct TcOperator *tc = nullptr;
 };
 
 // Workspace for one operator application (preconditioner intermediates).
@@ -72,6 +74,15 @@ void launch_apply_h_f32(const DevOperator &op, const double *psi, double *out, i
 void launch_apply_prec_f32(const DevOperator &op, const double *r, double *out, int nvec,
                            double sigma, ApplyWorkspace &ws, cudaStream_t s);
 
+// FP64-accurate 1D H-apply on the tensor cores (Ozaki digit splitting); builds op.tc on
+// first use.  Asynchronous on s.
+cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *out, int nvec,
+                              const double *theta_dev, double theta, cudaStream_t s);
+cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s);
+void free_tc_operator(struct TcOperator *t);
+// Synchronously reads and clears the timed-out-wait flag of op's tensor-core kernels.
+int tc_operator_status(const DevOperator &op);
+
 // Skinny block kernels.  Column c of block X is X + c*ldx; batch s adds s*bsx.
 struct GramScratch {
   double *partial = nullptr;
@@ -86,9 +97,13 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
                    long long bsc, long long nrows, int batch, cudaStream_t s);
 
-// Small dense kernels (one CTA each).
+// Small dense kernels (one CTA or one cluster each).
+// Eigenpairs of the symmetric m x m G (ld ldg): theta ascending, Y column-major (ld ldy).
+// mp > 0: the leading mp x mp block of G is unchanged since the previous call, whose
+// outputs theta[:mp] and Y[:mp, :mp] are still in theta and Y; they seed the solve and are
+// overwritten.
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s);
+                        cudaStream_t s, int mp = 0);
 // Cholesky G = R^T R of the b x b Gram matrix (ld b); writes Rinv (upper, ld b) and
 // keep[c] = 1 if column c has a pivot >= tol_rel * ref[c] (ref = squared column norms
 // before projection, device, may be null), else 0 (column dropped, Rinv column zero).

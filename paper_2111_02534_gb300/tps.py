@@ -34,6 +34,7 @@ GAUSS, LORENTZ3 = 0, 1
 ANY, X_EVEN, X_ODD = 0, 1, 2
 F64 = 0
 F32 = 1
+F64_TC = 2
 
 
 class SolverOpts(C.Structure):
@@ -42,7 +43,8 @@ class SolverOpts(C.Structure):
                 ("seed", C.c_ulonglong), ("inner_tol", C.c_double), ("timing", C.c_int),
                 ("guard", C.c_int), ("smooth_start", C.c_int), ("prec_dtype", C.c_int),
                 ("h_dtype", C.c_int), ("switch_tol", C.c_double), ("refine_block", C.c_int),
-                ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int)]
+                ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int),
+                ("h64_dtype", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -68,6 +70,7 @@ _sig = {
     "tps_destroy": (C.c_int, [_vp]),
     "tps_last_error": (C.c_char_p, [_vp]),
     "tps_status_string": (C.c_char_p, [C.c_int]),
+    "tps_device_status": (C.c_int, [_vp]),
     "tps_set_masses": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "tps_set_alpha": (C.c_int, [_vp, C.c_double]),
     "tps_set_grid": (C.c_int, [_vp, _ip, _dp]),
@@ -219,6 +222,10 @@ class Context:
         h = C.c_double()
         self._check(_lib.tps_get_info(self._h, C.byref(N), C.byref(h)), "get_info")
         return N.value, h.value
+
+    def device_status(self):
+        """Synchronise; raise TpsError(TIMEOUT) if a tensor-core kernel gave up a wait."""
+        self._check(_lib.tps_device_status(self._h), "device_status")
 
     # ---- operator applications -------------------------------------------------
     def apply_h(self, psi, out, theta=0.0, stream=None, dtype=F64):

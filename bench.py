@@ -38,9 +38,21 @@ REL_TOL = 1e-10
 FP64_FLOP_PER_CLK_PER_SM = 4
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-# DRAM bytes per H-apply GEMM launch from the ncu capture summarised in
-# profiles/k_gemm_f64_1d_n512.md (None until a capture of the current kernel exists)
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = None
+# digit-pair products of the tensor-core FP64 emulation (9 wave-function digits, 10
+# mode-matrix digits, levels i + j <= 9 kept): each one a BF16 MMA over the full product
+TC_PAIRS = 54
+# DRAM bytes per launch of each kernel from the ncu captures summarised in profiles/
+# (None where no capture of the current kernel exists)
+TRAFFIC_BYTES_PER_LAUNCH = {}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def parse_args():
@@ -318,21 +330,31 @@ def run_ours(args):
         e2e_pairs += passing_pairs(lam, ref)[0]
     E_T, E_pairs = aggregate(e2e_t, e2e_pairs, world, device="cuda")
 
-    # the FP64-only solver on the same input, for the mixed-precision comparison
-    o64 = tps.default_opts()
-    o64.timing = 1
-    o64.h_dtype = tps.F64
-    step(o64)
-    t64 = []
-    for _ in range(max(1, min(3, args.steps))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        lam64, st64 = step(o64)
-        ev1.record(stream)
-        ev1.synchronize()
-        t64.append(ev0.elapsed_time(ev1) / 1000.0)
-    fp64_rate = passing_pairs(lam64, ref)[0] / (sum(t64) / len(t64))
+    # solver variants on the same input: FP64-only and mixed, FP64 H-applies on the
+    # tensor cores (default) or on the FP64 FMA pipe
+    def variant_rate(h_dtype, h64_dtype, reps):
+        o = tps.default_opts()
+        o.h_dtype = h_dtype
+        o.h64_dtype = h64_dtype
+        step(o)
+        ts, ok = [], True
+        for _ in range(reps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            lam_v, _ = step(o)
+            ev1.record(stream)
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1) / 1000.0)
+            ok = ok and passing_pairs(lam_v, ref)[0] == len(ref)
+        return passing_pairs(lam_v, ref)[0] / (sum(ts) / len(ts)), ok
+    reps = max(1, min(3, args.steps))
+    variants = {"fp64_tc (default, per-kernel timers on)": value / world}
+    for name, hd, h64 in (("fp64_tc", tps.F64, tps.F64_TC), ("fp64_fma", tps.F64, tps.F64),
+                          ("mixed_fp32_then_fp64_tc", tps.F32, tps.F64_TC),
+                          ("mixed_fp32_then_fp64_fma", tps.F32, tps.F64)):
+        variants[name], ok = variant_rate(hd, h64, reps)
+        variants[name + "_all_pass"] = ok
     h2d = 8 * N + 8 * w.block * N
     d2h = 8 * w.k * N + 8 * w.k
 
@@ -341,21 +363,67 @@ def run_ours(args):
     if rank == 0 and not args.no_sweep:
         sweep = run_sweep(tps, torch, args.sweep_streams)
 
-    # roofline of the dominant kernel: the FP64 mode-product GEMM of the H-apply
-    # (k_gemm<double>), from the solver's own CUDA-event timers; the preconditioner
-    # runs its mode products in FP32 and is reported beside it
-    h_fl = sum(st.h_flops for st in stats)
-    h_ms = sum(st.h_ms for st in stats)
-    achieved = h_fl / (h_ms / 1000.0) / 1e12
+    # per-kernel rates from the solver's own CUDA-event timers over the timed solves; the
+    # kernel family with the largest share of the step is the roofline
+    pk = measured_peaks()
+    fp64_peak = N_SM * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = N_SM * 256 * SM_MAX_MHZ * 1e6 / 1e12
+    bf16_peak = pk.get("bf16_tflops_sustained")
+    hbm_peak = pk.get("hbm_gbs")
+    tot = lambda f: sum(getattr(st, f) for st in stats)
+    step_s = local_t
+    nx_s, ny = w.n[0] // 2 + 1, w.n[1]
+    fp64_per_vec = 2.0 * nx_s * ny * (nx_s + ny) + 3.0 * nx_s * ny
+    tc_per_vec = 2.0 * TC_PAIRS * nx_s * ny * (nx_s + ny)
+    kernels = {}
+    h_ms, h_fl = tot("h_ms"), tot("h_flops")
+    if h_ms > 0:
+        tflops = h_fl / fp64_per_vec * tc_per_vec / (h_ms / 1000.0) / 1e12
+        kernels["k_oz_gemm"] = {
+            "what": "FP64 H-apply on tcgen05 (BF16 digit products, exact FP32 levels; with its "
+                    "digit-splitting kernels)",
+            "bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": tflops / bf16_peak if bf16_peak else None,
+            "peak_note": "bf16_tflops_sustained of measured (cuBLAS bf16, seconds-long loop)",
+            "fp64_equivalent_tflops": h_fl / (h_ms / 1000.0) / 1e12,
+            "launches": tot("h_launches"), "share": h_ms / 1000.0 / step_s}
+    for key, f, what in (("k_gram", "gram", "FP64 Gram products A^T B (one launch, split rows)"),
+                         ("k_update", "upd", "FP64 block updates C = bC + a A Y")):
+        # every 4th launch is timed (stats doc): rates from the timed ones, the share of
+        # the step scaled up to all launches
+        ms, fl, by = tot(f + "_ms"), tot(f + "_flops"), tot(f + "_bytes")
+        n_all = tot(f + "_launches")
+        n_timed = sum((getattr(st_, f + "_launches") + 3) // 4 for st_ in stats)
+        if ms > 0:
+            a = fl / (ms / 1000.0) / 1e12
+            kernels[key] = {"what": what, "bound": "alu", "achieved": a, "peak": fp64_peak,
+                            "unit": "TFLOP/s", "frac": a / fp64_peak,
+                            "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz "
+                                         "(nominal-derived; a DFMA probe measured 1.19 TFLOP/s)",
+                            "hbm_gbs": by / (ms / 1000.0) / 1e9,
+                            "hbm_frac": by / (ms / 1000.0) / 1e9 / hbm_peak if hbm_peak else None,
+                            "launches": n_all, "timed_launches": n_timed,
+                            "share": ms * n_all / max(n_timed, 1) / 1000.0 / step_s}
+    p_ms, h32_ms = tot("prec_ms"), tot("h32_ms")
+    if p_ms + h32_ms > 0:
+        a = (tot("prec_flops") + tot("h32_flops")) / ((p_ms + h32_ms) / 1000.0) / 1e12
+        kernels["k_gemm<float>"] = {"what": "FP32 mode products (preconditioner, FP32 H-apply)",
+                                    "bound": "alu", "achieved": a, "peak": fp32_peak,
+                                    "unit": "TFLOP/s", "frac": a / fp32_peak,
+                                    "peak_note": "FP32 FMA pipe, nominal-derived",
+                                    "launches": tot("prec_launches") + tot("h32_launches"),
+                                    "share": (p_ms + h32_ms) / 1000.0 / step_s}
+    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    roofline = None
+    if dom is not None:
+        kd = kernels[dom]
+        launches = kd["launches"]
+        roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                    "unit": kd["unit"], "frac": kd["frac"],
+                    "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kernel": dom,
+                    "peak_note": kd["peak_note"], "launches": launches,
+                    "time_share_of_step": kd["share"]}
     clocks = clk.summary()
-    peak = N_SM * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    p_fl = sum(st.prec_flops for st in stats)
-    p_ms = sum(st.prec_ms for st in stats)
-    prec_tf = p_fl / (p_ms / 1000.0) / 1e12 if p_ms > 0 else None
-    h32_fl = sum(st.h32_flops for st in stats)
-    h32_ms = sum(st.h32_ms for st in stats)
-    h32_tf = h32_fl / (h32_ms / 1000.0) / 1e12 if h32_ms > 0 else None
-    h_launches = sum(st.h_launches for st in stats)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -371,25 +439,15 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: 1D heavy-heavy-light, M/m=40, n=512 per Jacobi "
                                    "coordinate on [-20,20), v0 tuned to E0=1e-3, sigma=1, 8 lowest "
-                                   "x-even eigenpairs, block 8, tol 1e-12*||H||; mixed precision "
-                                   "(FP32 mode products, FP64 Gram/Ritz/refinement)",
+                                   "x-even eigenpairs, block 8, tol 1e-12*||H||; FP64 solver, H "
+                                   "mode products FP64-accurate on the tensor cores, FP32 "
+                                   "preconditioner, FP64 Gram/Ritz/orthogonalisation",
                        "parallelism": f"replicas x{world}", "l2": "flushed between timed steps",
                        "unknowns": N, "sector_unknowns": (w.n[0] // 2 + 1) * w.n[1]},
-            "solver_variants": {"mixed_fp32_then_fp64": value / world,
-                                "fp64_only": fp64_rate,
-                                "note": "eigenpairs/s per GPU; both pass the 1e-10 gate"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": GEMM_TRAFFIC_BYTES_PER_LAUNCH,
-                         "kernel": "k_gemm<double> (fused FP64 H-apply mode products)",
-                         "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz "
-                                      "(nominal-derived; a DFMA probe measured 1.19 TFLOP/s)",
-                         "launches": h_launches, "time_share_of_step": h_ms / 1000.0 / local_t},
-            "fp32_mode_products": {"preconditioner_tflops": prec_tf,
-                                   "preconditioner_time_share": p_ms / 1000.0 / local_t,
-                                   "h_apply_fp32_tflops": h32_tf,
-                                   "h_apply_fp32_time_share": h32_ms / 1000.0 / local_t,
-                                   "peak_fp32_tflops": N_SM * 256 * SM_MAX_MHZ * 1e6 / 1e12},
+            "solver_variants": dict(variants, note="eigenpairs/s per GPU; tc = FP64 H-applies "
+                                                   "on the tensor cores, fma = on the FP64 pipe"),
+            "roofline": roofline,
+            "kernels": kernels,
             "e2e": {"value": E_pairs / E_T, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": n_e2e},
             "clocks": clocks,

@@ -165,17 +165,18 @@ typedef struct tps_solver_opts {
                          the random part of the start block, a low-pass filter (default 2) */
   int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_F32 (default)
                          or TPS_F64 */
-  int h_dtype;        /* TPS_F32 (default): mixed precision -- a first phase runs the H mode
-                         products in FP32 until every pair's residual is below switch_tol,
-                         then an FP64 refinement phase converges them to tol; TPS_F64: FP64
-                         throughout.  Gram matrices, Ritz values and QR steps are FP64 always */
+  int h_dtype;        /* TPS_F64 (default): FP64 H products throughout (on the tensor cores,
+                         see h64_dtype); TPS_F32: mixed precision -- a first phase runs the H
+                         mode products in FP32 until every pair's residual is below
+                         switch_tol, then an FP64 refinement phase converges them to tol.
+                         Gram matrices, Ritz values and QR steps are FP64 always */
   double switch_tol;  /* relative residual ending the FP32 phase (0: 1e-6) */
   int refine_block;   /* block size of the FP64 refinement phase (0: k + guard, at most 32) */
   int refine_inner_steps; /* GMRES steps in the refinement phase (0: adaptive as above) */
   int refine_inner_dtype; /* arithmetic of H inside the refinement's GMRES (TPS_F64 default) */
   int h64_dtype;      /* how every FP64 H-apply of the solver runs (refinement phase, FP64-only
-                         mode, final Rayleigh quotients): TPS_F64 (FP64 FMA pipe, default) or
-                         TPS_F64_TC (tensor-core emulation, 1D only) */
+                         mode, final Rayleigh quotients): TPS_F64_TC (default: tensor-core
+                         emulation, 1D; 2D solves use the FMA pipe) or TPS_F64 (FMA pipe) */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -197,6 +198,17 @@ typedef struct tps_stats {
   double h32_ms;      /* with opts.timing: device time of the FP32 H applications */
   double h32_flops;   /* algorithmic flops of the FP32 H applications */
   long long h32_launches;
+  /* Gram products A^T B and block updates C = bC + a A Y (a6, a7), with opts.timing.  To
+   * keep the timing overhead low every 4th launch is timed: *_ms, *_flops and *_bytes
+   * cover the timed launches (so flops / ms is their rate), *_launches counts all. */
+  double gram_ms;     /* device time of the timed Gram launches */
+  double gram_flops;  /* their algorithmic flops, 2 nrows p q each */
+  double gram_bytes;  /* their algorithmic bytes, 8 nrows (p + q) each */
+  long long gram_launches;
+  double upd_ms;      /* device time of the timed block updates */
+  double upd_flops;   /* 2 nrows p q each */
+  double upd_bytes;   /* 8 nrows (p + q) each, + 8 nrows q when C is read */
+  long long upd_launches;
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

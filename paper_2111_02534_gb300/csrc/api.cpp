@@ -296,10 +296,18 @@ int ensure_apply_workspace(tps_ctx *ctx, long long doubles) {
 int ensure_gram_scratch(tps_ctx *ctx, long long doubles) {
   if (ctx->gscr.capacity >= doubles) return TPS_OK;
   cudaFree(ctx->gscr.partial);
+  cudaFree(ctx->gscr.count);
   ctx->gscr.partial = nullptr;
-  ctx->gscr.capacity = 0;
+  ctx->gscr.count = nullptr;
+  ctx->gscr.capacity = ctx->gscr.ncount = 0;
+  // one ticket per 4x4 block: at most one per 16 partial sums
+  const long long ncount = doubles / 16 + 1;
   TPS_CUDA_TRY(ctx, cudaMalloc((void **)&ctx->gscr.partial, doubles * sizeof(double)));
+  TPS_CUDA_TRY(ctx, cudaMalloc((void **)&ctx->gscr.count, ncount * sizeof(unsigned)));
+  TPS_CUDA_TRY(ctx, cudaMemset(ctx->gscr.count, 0, ncount * sizeof(unsigned)));
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));  // see build_operator
   ctx->gscr.capacity = doubles;
+  ctx->gscr.ncount = ncount;
   return TPS_OK;
 }
 
@@ -369,6 +377,7 @@ int tps_destroy(tps_ctx *ctx) {
   cudaFree(ctx->ws.t0);
   cudaFree(ctx->ws.t1);
   cudaFree(ctx->gscr.partial);
+  cudaFree(ctx->gscr.count);
   delete ctx;
   return TPS_OK;
 }

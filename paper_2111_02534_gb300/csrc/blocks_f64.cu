@@ -17,13 +17,18 @@ namespace {
 constexpr int GT = 256;  // threads of the Gram / update kernels
 
 // -------------------------------- Gram ---------------------------------------
-// partial[s][pb][c][16]: the 4x4 block pb of A_s^T B_s summed over the rows of chunk c.
+// G_s = A_s^T B_s in one launch.  CTA (c, s, pb) sums the 4x4 block pb over the rows of
+// chunk c into partial[s][pb][c][16]; the last CTA of a block to finish (ticket counter,
+// after a memory fence) adds the chunks in chunk order -- the same order every call, so
+// the result is deterministic -- writes the block into G and re-arms the counter.
 __global__ void __launch_bounds__(GT)
-k_gram_partial(const double *__restrict__ A, long long lda, long long bsa, int p,
-               const double *__restrict__ B, long long ldb, long long bsb, int q,
-               long long nrows, int nchunk, double *__restrict__ partial) {
+k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
+       const double *__restrict__ B, long long ldb, long long bsb, int q, long long nrows,
+       int nchunk, double *__restrict__ partial, unsigned *__restrict__ count,
+       double *__restrict__ G, int ldg, long long bsg) {
   const int c = blockIdx.x, s = blockIdx.y, pb = blockIdx.z;
   const int qb = (q + 3) / 4;
+  const int npb = ((p + 3) / 4) * qb;
   const int i0 = (pb / qb) * 4, j0 = (pb % qb) * 4;
   const double *As = A + s * bsa;
   const double *Bs = B + s * bsb;
@@ -47,6 +52,7 @@ k_gram_partial(const double *__restrict__ A, long long lda, long long bsa, int p
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
   }
   __shared__ double red[GT / 32][16];
+  __shared__ unsigned ticket;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -58,31 +64,35 @@ k_gram_partial(const double *__restrict__ A, long long lda, long long bsa, int p
       if (lane == 0) red[warp][i * 4 + j] = v;
     }
   __syncthreads();
+  const long long blk = (long long)s * npb + pb;
   if (threadIdx.x < 16) {
     double v = 0.0;
     for (int w = 0; w < GT / 32; ++w) v += red[w][threadIdx.x];
-    const int npb = ((p + 3) / 4) * qb;
-    partial[(((long long)s * npb + pb) * nchunk + c) * 16 + threadIdx.x] = v;
+    partial[(blk * nchunk + c) * 16 + threadIdx.x] = v;
+    __threadfence();  // this chunk's sums are visible before the ticket is taken
   }
-}
-
-__global__ void k_gram_reduce(const double *__restrict__ partial, int p, int q, int nchunk,
-                              int batch, double *__restrict__ G, int ldg, long long bsg) {
-  const int qb = (q + 3) / 4;
-  const int npb = ((p + 3) / 4) * qb;
-  const long long total = (long long)batch * p * q;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e / ((long long)p * q));
-    const int ij = (int)(e % ((long long)p * q));
-    const int i = ij % p, j = ij / p;
-    const int pb = (i / 4) * qb + j / 4;
-    const int w = (i % 4) * 4 + (j % 4);
-    const double *src = partial + ((long long)s * npb + pb) * nchunk * 16 + w;
-    double v = 0.0;
-    for (int c = 0; c < nchunk; ++c) v += src[(long long)c * 16];
-    G[s * bsg + (long long)j * ldg + i] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&count[blk], 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(nchunk - 1)) return;
+  // last CTA of the block: every other chunk's partial sums are in memory
+  if (threadIdx.x < 16) {
+    __threadfence();
+    const double *src = partial + blk * nchunk * 16 + threadIdx.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int cc = 0;
+    for (; cc + 4 <= nchunk; cc += 4) {
+      v0 += __ldcg(src + (long long)(cc + 0) * 16);
+      v1 += __ldcg(src + (long long)(cc + 1) * 16);
+      v2 += __ldcg(src + (long long)(cc + 2) * 16);
+      v3 += __ldcg(src + (long long)(cc + 3) * 16);
+    }
+    for (; cc < nchunk; ++cc) v0 += __ldcg(src + (long long)cc * 16);
+    const double v = (v0 + v1) + (v2 + v3);
+    const int i = i0 + threadIdx.x / 4, j = j0 + threadIdx.x % 4;
+    if (i < p && j < q) G[s * bsg + (long long)j * ldg + i] = v;
   }
+  if (threadIdx.x == 0) count[blk] = 0u;  // re-armed for the next call on this stream
 }
 
 int gram_chunks(long long nrows, int batch, int npb) {
@@ -614,10 +624,8 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
   if (nchunk > cap) nchunk = (int)(cap > 0 ? cap : 1);
   dim3 grid(nchunk, batch, npb);
   count_launch();
-  k_gram_partial<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial);
-  const long long total = (long long)batch * p * q;
-  count_launch();
-  k_gram_reduce<<<grid_for(total), 256, 0, s>>>(scr.partial, p, q, nchunk, batch, G, ldg, bsg);
+  k_gram<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial,
+                             scr.count, G, ldg, bsg);
 }
 
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,

@@ -30,14 +30,22 @@ namespace tps {
 struct PhaseTiming {
   bool on = false;
   std::vector<cudaEvent_t> all, free_ev;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[3];  // FP64 H, preconditioner, FP32 H
-  double ms[3] = {0, 0, 0}, flops[3] = {0, 0, 0};
-  long long launches[3] = {0, 0, 0};
+  // kinds: 0 FP64 H, 1 preconditioner, 2 FP32 H, 3 Gram products, 4 block updates.  The
+  // skinny kinds (hundreds of short launches per solve) are timed on every kSample-th
+  // launch only: their flops, bytes and time then refer to the sampled launches, and
+  // launches[] counts all of them
+  static constexpr int kKinds = 5;
+  static constexpr int kSample = 4;
+  long long seen[kKinds] = {0, 0, 0, 0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[kKinds];
+  double ms[kKinds] = {0, 0, 0, 0, 0}, flops[kKinds] = {0, 0, 0, 0, 0};
+  double bytes[kKinds] = {0, 0, 0, 0, 0};
+  long long launches[kKinds] = {0, 0, 0, 0, 0};
   void reset(bool enable) {
     on = enable;
-    for (int k = 0; k < 3; ++k) {
-      ms[k] = flops[k] = 0.0;
-      launches[k] = 0;
+    for (int k = 0; k < kKinds; ++k) {
+      ms[k] = flops[k] = bytes[k] = 0.0;
+      launches[k] = seen[k] = 0;
     }
   }
   cudaEvent_t get() {
@@ -52,7 +60,7 @@ struct PhaseTiming {
     return e;
   }
   void drain() {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
       for (auto &pr : pend[k]) {
         cudaEventSynchronize(pr.second);
         float t = 0.f;
@@ -116,6 +124,54 @@ void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
     const double r = std::sqrt(-2.0 * std::log(u1));
     v[e] = r * std::cos(two_pi * u2);
     if (e + 1 < v.size()) v[e + 1] = r * std::sin(two_pi * u2);
+  }
+}
+
+// Timers of the running solve (tps_solver_opts.timing), for the skinny-kernel wrappers.
+thread_local PhaseTiming *tl_timing = nullptr;
+
+// launch_gram / launch_update with CUDA-event timing and algorithmic work counts
+void tgram(const double *A, long long lda, long long bsa, int p, const double *B, long long ldb,
+           long long bsb, int q, long long nrows, double *G, int ldg, long long bsg, int batch,
+           GramScratch &scr, cudaStream_t s) {
+  PhaseTiming *t = tl_timing;
+  const bool live = t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  if (live) t->launches[3] += 1;
+  const bool rec = live && (t->seen[3]++ % PhaseTiming::kSample) == 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (rec) {
+    a = t->get();
+    b = t->get();
+    cudaEventRecord(a, s);
+  }
+  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s);
+  if (rec) {
+    cudaEventRecord(b, s);
+    t->pend[3].push_back({a, b});
+    t->flops[3] += 2.0 * nrows * p * q * batch;
+    t->bytes[3] += 8.0 * nrows * (p + q) * batch;
+  }
+}
+
+void tupdate(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
+             long long bsy, int q, double alpha, double beta, double *C, long long ldc,
+             long long bsc, long long nrows, int batch, cudaStream_t s) {
+  PhaseTiming *t = tl_timing;
+  const bool live = t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  if (live) t->launches[4] += 1;
+  const bool rec = live && (t->seen[4]++ % PhaseTiming::kSample) == 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (rec) {
+    a = t->get();
+    b = t->get();
+    cudaEventRecord(a, s);
+  }
+  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s);
+  if (rec) {
+    cudaEventRecord(b, s);
+    t->pend[4].push_back({a, b});
+    t->flops[4] += 2.0 * nrows * p * q * batch;
+    t->bytes[4] += 8.0 * nrows * (p + (beta != 0.0 ? 2 : 1) * q) * batch;
   }
 }
 
@@ -197,7 +253,7 @@ void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double sh
 
 // diag(A^T A) for ncols columns -> out[ncols] (device)
 void col_norms2(Ctx &c, const double *A, int ncols, double *out) {
-  launch_gram(A, c.N, c.N, 1, A, c.N, c.N, 1, c.N, out, 1, 1, ncols, c.ctx->gscr, c.s);
+  tgram(A, c.N, c.N, 1, A, c.N, c.N, 1, c.N, out, 1, 1, ncols, c.ctx->gscr, c.s);
 }
 
 // T (b cols) <- orthonormal basis of span(T) minus span(B1, B2); B1, B2 orthonormal blocks
@@ -208,20 +264,20 @@ int orthonormalize(Ctx &c, const double *B1, int nb1, const double *B2, int nb2,
   col_norms2(c, T, b, w.ref);
   for (int pass = 0; pass < 2; ++pass) {
     if (nb1 > 0) {
-      launch_gram(B1, c.N, 0, nb1, T, c.N, 0, b, c.N, w.C, nb1, 0, 1, c.ctx->gscr, c.s);
-      launch_update(B1, c.N, 0, nb1, w.C, nb1, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+      tgram(B1, c.N, 0, nb1, T, c.N, 0, b, c.N, w.C, nb1, 0, 1, c.ctx->gscr, c.s);
+      tupdate(B1, c.N, 0, nb1, w.C, nb1, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
     }
     if (nb2 > 0) {
-      launch_gram(B2, c.N, 0, nb2, T, c.N, 0, b, c.N, w.C, nb2, 0, 1, c.ctx->gscr, c.s);
-      launch_update(B2, c.N, 0, nb2, w.C, nb2, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+      tgram(B2, c.N, 0, nb2, T, c.N, 0, b, c.N, w.C, nb2, 0, 1, c.ctx->gscr, c.s);
+      tupdate(B2, c.N, 0, nb2, w.C, nb2, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
     }
   }
   // Cholesky QR twice; the first pass drops numerically dependent columns
   for (int pass = 0; pass < 2; ++pass) {
-    launch_gram(T, c.N, 0, b, T, c.N, 0, b, c.N, w.C, b, 0, 1, c.ctx->gscr, c.s);
+    tgram(T, c.N, 0, b, T, c.N, 0, b, c.N, w.C, b, 0, 1, c.ctx->gscr, c.s);
     launch_chol_inv(w.C, b, pass == 0 ? w.ref : nullptr, pass == 0 ? 1e-7 : 1e-12, w.Rinv,
                     w.keep, c.s);
-    launch_update(T, c.N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, c.N, 0, c.N, 1, c.s);
+    tupdate(T, c.N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, c.N, 0, c.N, 1, c.s);
     TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(T, w.T2, (size_t)b * c.N * sizeof(double),
                                         cudaMemcpyDeviceToDevice, c.s));
     if (pass == 0) {
@@ -251,17 +307,17 @@ void kt_inverse(Ctx &c, const double *Qt, int nq, const double *KQt, int use_pre
   if (use_prec) {
     apply_prec_timed(c, Yin, Out, nsys, shift);
     if (nq > 0) {
-      launch_gram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
+      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
       // C2 = Minv * C, stored after C
       double *C2 = w.C + (long long)nq * nsys;
       launch_small_gemm(nq, nsys, nq, 1.0, w.Minv, nq, w.C, nq, 0.0, C2, nq, c.s);
-      launch_update(KQt, c.N, 0, nq, C2, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+      tupdate(KQt, c.N, 0, nq, C2, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
     }
   } else {
     if (Out != Yin) launch_axpby_cols(nsys, c.N, 1.0, Yin, c.N, 0.0, Out, c.N, c.s);
     for (int pass = 0; pass < 2 && nq > 0; ++pass) {
-      launch_gram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
-      launch_update(Qt, c.N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
+      tupdate(Qt, c.N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
     }
   }
 }
@@ -383,7 +439,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                        nq - nq_cached, shift);
       *prec_applies += nq - nq_cached;
     }
-    launch_gram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s);
+    tgram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s);
     launch_spd_inverse(w.Mq, nq, w.Minv, s);
   }
   const int sst = steps;
@@ -406,8 +462,8 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     // right projector of Eq. jdcor, applied explicitly: rounding in the Q directions
     // would otherwise grow by 1/h_{j+1,j} per Arnoldi step
     if (nq > 0) {
-      launch_gram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s);
-      launch_update(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s);
+      tgram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s);
+      tupdate(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s);
     }
     apply_h_timed(c, zj, w.W, nsys, theta, low);
     *h_applies += nsys;
@@ -415,9 +471,9 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     if (use_prec) *prec_applies += nsys;
     // Arnoldi, classical Gram-Schmidt twice, per system: h = Z_i^T p_i ; p_i -= Z_i h
     for (int pass = 0; pass < 2; ++pass) {
-      launch_gram(Z, (long long)nsys * N, N, j + 1, w.P, N, N, 1, N, w.gm.h, sst + 1, sst + 1, nsys,
+      tgram(Z, (long long)nsys * N, N, j + 1, w.P, N, N, 1, N, w.gm.h, sst + 1, sst + 1, nsys,
                   ctx->gscr, s);
-      launch_update(Z, (long long)nsys * N, N, j + 1, w.gm.h, sst + 1, sst + 1, 1, -1.0, 1.0, w.P, N,
+      tupdate(Z, (long long)nsys * N, N, j + 1, w.gm.h, sst + 1, sst + 1, 1, -1.0, 1.0, w.P, N,
                     N, N, nsys, s);
       launch_hess_add(nsys, sst, j, w.gm.h, sst + 1, w.gm, s);
     }
@@ -426,7 +482,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     launch_scale_cols(nsys, N, w.P, N, w.gm.scale, 0, Z + (long long)(j + 1) * nsys * N, N, s);
   }
   launch_gmres_solve(nsys, sst, w.gm, s);
-  launch_update(Z, (long long)nsys * N, N, sst, w.gm.y, sst, sst, 1, 1.0, 0.0, T, N, N, N, nsys, s);
+  tupdate(Z, (long long)nsys * N, N, sst, w.gm.y, sst, sst, 1, 1.0, 0.0, T, N, N, N, nsys, s);
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;
 }
@@ -480,13 +536,15 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
+  struct TimingScope {
+    explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
+    ~TimingScope() { tl_timing = nullptr; }
+  } timing_scope(&w.tm);
   w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64 : TPS_F32;
-  w.h64_dtype = opts.h64_dtype == TPS_F64_TC ? TPS_F64_TC : TPS_F64;
-  if (w.h64_dtype == TPS_F64_TC) {
-    if (op.nmodes != 2)
-      return set_error(ctx, TPS_ERR_INVALID_ARG, "h64_dtype TPS_F64_TC is implemented for 1D only");
+  // the tensor-core FP64 H-apply exists for the 1D operator; 2D solves use the FMA pipe
+  w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && op.nmodes == 2) ? TPS_F64_TC : TPS_F64;
+  if (w.h64_dtype == TPS_F64_TC)
     TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));  // allocation errors here, not mid-solve
-  }
   const long long launches0 = g_kernel_launches.load();
   double hnorm = 0.0;
   tps_get_info(ctx, nullptr, &hnorm);
@@ -562,9 +620,9 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     apply_h_timed(c, T, HT, bn, nullptr, low);
     stt.h_applies += bn;
     // (3) projected matrix G = V^T H V, new columns and their mirror
-    if (m > 0) launch_gram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * ldG, ldG, 0, 1,
+    if (m > 0) tgram(w.V, N, 0, m, HT, N, 0, bn, N, w.G + (long long)m * ldG, ldG, 0, 1,
                            ctx->gscr, s);
-    launch_gram(T, N, 0, bn, HT, N, 0, bn, N, w.G + (long long)m * ldG + m, ldG, 0, 1, ctx->gscr,
+    tgram(T, N, 0, bn, HT, N, 0, bn, N, w.G + (long long)m * ldG + m, ldG, 0, 1, ctx->gscr,
                 s);
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
@@ -573,8 +631,8 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
-    launch_update(w.V, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
-    launch_update(w.HV, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, w.HX, N, 0, N, 1, s);
+    tupdate(w.V, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, X, N, 0, N, 1, s);
+    tupdate(w.HV, N, 0, m, w.Y, ldG, 0, nact, 1.0, 0.0, w.HX, N, 0, N, 1, s);
     launch_residual(nact, N, w.HX, X, w.theta, w.R, s);
     col_norms2(c, w.R, nact, w.nrm2);
     // (5) read back Ritz values and residual norms
@@ -620,9 +678,9 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     if (nconv > 0 || m + bp > mmaxp) {
       const int avail = m - nconv;
       const int mk = (m + bp > mmaxp) ? std::min(avail, mminp) : avail;
-      launch_update(w.V, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.V2, N, 0,
+      tupdate(w.V, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.V2, N, 0,
                     N, 1, s);
-      launch_update(w.HV, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.HV2, N,
+      tupdate(w.HV, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.HV2, N,
                     0, N, 1, s);
       std::swap(w.V, w.V2);
       std::swap(w.HV, w.HV2);
@@ -703,7 +761,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     double *HQ = w.V2;  // at least max(mmax, kmax) columns
     apply_h_timed(c, w.QX, HQ, nl, nullptr, false);
     stt.h_applies += nl;
-    launch_gram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nl, ctx->gscr, s);
+    tgram(w.QX, N, N, 1, HQ, N, N, 1, N, w.theta2, 1, 1, nl, ctx->gscr, s);
     col_norms2(c, w.QX, nl, w.ref);
     TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta2, nl * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
@@ -752,6 +810,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.h32_ms = w.tm.ms[2];
   stt.h32_flops = w.tm.flops[2];
   stt.h32_launches = w.tm.launches[2];
+  stt.gram_ms = w.tm.ms[3];
+  stt.gram_flops = w.tm.flops[3];
+  stt.gram_bytes = w.tm.bytes[3];
+  stt.gram_launches = w.tm.launches[3];
+  stt.upd_ms = w.tm.ms[4];
+  stt.upd_flops = w.tm.flops[4];
+  stt.upd_bytes = w.tm.bytes[4];
+  stt.upd_launches = w.tm.launches[4];
   stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;
@@ -780,12 +846,12 @@ void tps_default_opts(tps_solver_opts *o) {
   o->guard = 2;
   o->smooth_start = 2;
   o->prec_dtype = TPS_F32;
-  o->h_dtype = TPS_F32;
+  o->h_dtype = TPS_F64;
   o->switch_tol = 1e-6;
   o->refine_block = 0;
   o->refine_inner_steps = 0;
   o->refine_inner_dtype = TPS_F64;
-  o->h64_dtype = TPS_F64;
+  o->h64_dtype = TPS_F64_TC;
 }
 
 int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0_dev,

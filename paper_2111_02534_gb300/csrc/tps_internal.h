@@ -86,7 +86,9 @@ int tc_operator_status(const DevOperator &op);
 // Skinny block kernels.  Column c of block X is X + c*ldx; batch s adds s*bsx.
 struct GramScratch {
   double *partial = nullptr;
-  long long capacity = 0;  // doubles
+  long long capacity = 0;     // doubles
+  unsigned *count = nullptr;  // per-block tickets of the one-launch Gram, zero between calls
+  long long ncount = 0;
 };
 // G_s = A_s^T B_s (p x q, column-major ldg) for s < batch.
 void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,

@@ -55,6 +55,10 @@ class Stats(C.Structure):
                 ("h_launches", C.c_longlong), ("prec_launches", C.c_longlong),
                 ("kernel_launches", C.c_longlong), ("h32_ms", C.c_double),
                 ("h32_flops", C.c_double), ("h32_launches", C.c_longlong),
+                ("gram_ms", C.c_double), ("gram_flops", C.c_double), ("gram_bytes", C.c_double),
+                ("gram_launches", C.c_longlong), ("upd_ms", C.c_double),
+                ("upd_flops", C.c_double), ("upd_bytes", C.c_double),
+                ("upd_launches", C.c_longlong),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

@@ -71,3 +71,31 @@ def test_two_body_v0_2d_host_setup_matches_oracle(lib):
     from oracle.two_body import tune_v0
     got = tps.two_body_v0(2, 1.0, 1.0, 0.2, 0, 1.0, 24, 8.0)
     assert got == pytest.approx(tune_v0(0.2, 1.0, 1.0, 0, 24, 8.0, dim=2), rel=1e-11)
+
+
+def test_binding_structs_match_header(tmp_path):
+    # the ctypes mirrors of tps_solver_opts and tps_stats have the C layout: every field
+    # offset and the struct sizes, from a C program compiled against include/tps.h
+    import shutil
+    import subprocess
+    from paper_2111_02534_gb300 import tps
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ['#include <stdio.h>', '#include "tps.h"', "int main(void) {"]
+    for cname, py in (("tps_solver_opts", tps.SolverOpts), ("tps_stats", tps.Stats)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("tps_solver_opts", tps.SolverOpts), ("tps_stats", tps.Stats)):
+        assert got[(cname, "size")] == ctypes.sizeof(py)
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

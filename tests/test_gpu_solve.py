@@ -233,16 +233,19 @@ def test_solve_workload_2d_n48_certified():
     assert np.all(res <= 1e-10 * np.abs(lam))
 
 
-@pytest.mark.parametrize("h_dtype", [0, 1])
-def test_full_size_fp64_and_mixed_agree(h_dtype):
-    # the FP64-only solver and the mixed-precision one on the 1d_n512 workload
+@pytest.mark.parametrize("h_dtype,h64_dtype", [(0, 0), (0, 2), (1, 0), (1, 2)])
+def test_full_size_fp64_and_mixed_agree(h_dtype, h64_dtype):
+    # the FP64-only solver and the mixed-precision one on the 1d_n512 workload, with the
+    # FP64 H-applies on the FMA pipe or the tensor cores
     require_gpu()
     tps = _tps()
     w = WORKLOADS["1d_n512"]
     with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
         gold = json.load(f)
     ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
-    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, h_dtype=h_dtype, timing=1)
+    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, h_dtype=h_dtype, h64_dtype=h64_dtype,
+                        timing=1)
+    assert st.gram_launches > 0 and st.gram_ms > 0 and st.upd_launches > 0
     ref = np.array(gold["evals"])
     assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
     if h_dtype == 1:

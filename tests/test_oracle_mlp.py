@@ -1,0 +1,117 @@
+"""Pins for oracle.mlp (the warm-start network's CPU oracle): every function against
+something other than itself -- finite differences, scalar loops, closed forms."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+from oracle import mlp
+
+RNG = np.random.Generator(np.random.PCG64(5))
+
+
+def _tiny(hidden=5, px=3, py=4, rank=2):
+    dims = mlp.layer_dims(px, py, rank, hidden)
+    params = RNG.normal(size=mlp.n_params(dims)) * 0.7
+    return dims, params
+
+
+def test_gelu_is_z_times_normal_cdf_and_grad_matches_difference():
+    z = np.linspace(-6, 6, 121)
+    assert np.allclose(mlp.gelu(z), z * norm.cdf(z), rtol=0, atol=1e-14)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(z), fd, rtol=0, atol=1e-8)
+
+
+def test_forward_matches_scalar_loops():
+    dims, params = _tiny()
+    X = RNG.normal(size=(3, 4))
+    out, _ = mlp.forward(params, dims, X)
+    # the layer layout written out with scalar loops: W_l[i][j] at offset + i*out + j
+    off = 0
+    a = [list(r) for r in X]
+    for l in range(4):
+        n_in, n_out = dims[l], dims[l + 1]
+        W = params[off: off + n_in * n_out]
+        b = params[off + n_in * n_out: off + n_in * n_out + n_out]
+        off += n_in * n_out + n_out
+        new = []
+        for r in a:
+            row = []
+            for j in range(n_out):
+                z = b[j] + sum(r[i] * W[i * n_out + j] for i in range(n_in))
+                row.append(z * 0.5 * (1 + math.erf(z / math.sqrt(2))) if l < 3 else z)
+            new.append(row)
+        a = new
+    assert np.allclose(out, np.array(a), rtol=1e-13, atol=1e-13)
+
+
+def test_backward_matches_central_differences():
+    dims, params = _tiny()
+    px, py, rank = 3, 4, 2
+    X = RNG.normal(size=(4, 4))
+    T = RNG.normal(size=(4, px, py))
+    _, g = mlp.loss_and_grad(params, dims, X, T, rank, px, py)
+    h = 1e-6
+    idx = RNG.choice(params.size, size=40, replace=False)
+    for i in idx:
+        p1, p2 = params.copy(), params.copy()
+        p1[i] += h
+        p2[i] -= h
+        f1, _ = mlp.loss_and_grad(p1, dims, X, T, rank, px, py)
+        f2, _ = mlp.loss_and_grad(p2, dims, X, T, rank, px, py)
+        fd = (f1 - f2) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_cosine_loss_special_cases():
+    px, py, rank = 3, 2, 1
+    C = RNG.normal(size=(1, rank, px))
+    D = RNG.normal(size=(1, rank, py))
+    o = np.concatenate([C.reshape(1, -1), D.reshape(1, -1)], axis=1)
+    P = np.einsum("sra,srb->sab", C, D)
+    assert mlp.cosine_loss(o, P, rank, px, py)[0] == pytest.approx(0.0, abs=1e-14)
+    assert mlp.cosine_loss(o, -3.0 * P, rank, px, py)[0] == pytest.approx(0.0, abs=1e-14)
+    # a target orthogonal to P
+    Tp = RNG.normal(size=P.shape)
+    Tp -= np.sum(Tp * P) / np.sum(P * P) * P
+    assert mlp.cosine_loss(o, Tp, rank, px, py)[0] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    g = np.array([3.0, -0.5, 1e-3])
+    w, m, v = mlp.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=1e-12)
+    assert np.allclose(w, -0.01 * np.sign(g), rtol=1e-9)
+
+
+@pytest.mark.parametrize("n,na,kind", [(32, 16, 0), (32, 31, 1), (48, 10, 1)])
+def test_mode_matrices_orthonormal(n, na, kind):
+    M = mlp.mode_matrix(kind, n, na)
+    assert np.allclose(M.T @ M, np.eye(na), atol=1e-13)
+    if kind == 0:   # even under x -> -x on the grid: j -> (n - j) mod n
+        refl = (-np.arange(n)) % n
+        assert np.allclose(M[refl], M, atol=1e-13)
+
+
+def test_project_and_assemble_round_trip():
+    nx, ny, px, py, rank = 24, 20, 5, 6, 2
+    C = RNG.normal(size=(2, rank, px))
+    D = RNG.normal(size=(2, rank, py))
+    o = np.concatenate([C.reshape(2, -1), D.reshape(2, -1)], axis=1)
+    psi = mlp.assemble(o, rank, px, py, nx, ny)
+    T = mlp.project(psi, nx, ny, px, py)
+    assert np.allclose(T, np.einsum("sra,srb->sab", C, D), atol=1e-12)
+    # a single product of modes projects onto one coefficient
+    Phi, Chi = mlp.mode_matrix(0, nx, px), mlp.mode_matrix(1, ny, py)
+    one = np.outer(Phi[:, 3], Chi[:, 4]).ravel()[None]
+    T1 = mlp.project(one, nx, ny, px, py)[0]
+    E = np.zeros((px, py))
+    E[3, 4] = 1.0
+    assert np.allclose(T1, E, atol=1e-13)
+
+
+def test_features_are_the_stated_map():
+    X = mlp.features(40.0, math.e ** 5, 2.0, 8)
+    assert np.allclose(X, [[1.0, 1.0, 1.0, 1.0]], atol=1e-15)

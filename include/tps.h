@@ -219,7 +219,9 @@ void tps_default_opts(tps_solver_opts *opts);
  * TPS_X_EVEN, TPS_X_ODD; 2D supports TPS_ANY only) by block Jacobi-Davidson with
  * block size `block` (1..32; 1 is the paper's single-vector JDQR), converged when
  * ||H x - theta x|| <= tol * ||H||_est.  x0_dev: nullable device [n_x0][N] warm
- * start (Sec. 5.2 homotopy).  evals_host: host [k] ascending.  evecs_dev: device
+ * start (Sec. 5.2 homotopy): its first min(n_x0, max(block, k + guard)) columns form the
+ * first search block (completed with smoothed random columns up to `block`).
+ * evals_host: host [k] ascending.  evecs_dev: device
  * [k][N] unit-norm, sign such that the entry of largest magnitude is positive.
  * opts may be NULL (defaults).  Synchronous: returns when results are ready.
  * The first call allocates the solver's device workspace inside the context
@@ -299,6 +301,72 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
  *    TPS_ERR_CUDA if the address look-up or the launch fails.  Asynchronous on stream. */
 int tps_gram_noalloc(const double *A_dev, long long lda, int p, const double *B_dev, long long ldb,
                      int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream);
+
+/* ---- learned warm start (a small MLP trained on the solver's own eigenvectors) ----
+ *
+ * Along a sweep of binding energies the paper starts each Jacobi-Davidson run from the
+ * previous run's subspace (homotopy, Sec. 5.2) and names low-rank vectors as a way
+ * forward (Sec. 6).  This model predicts a low-rank separable start block directly from
+ * the problem parameters, for any grid.  Inputs: four
+ * features of (mass ratio M/m, well depth v0, range sigma, state index) -- see
+ * tps_ws_features.  Network: 4 -> [Linear, GELU(exact erf form)] x 3 (width `hidden`) ->
+ * Linear -> rank (px + py) outputs read as C (rank x px) and D (rank x py), the state
+ *     psi(x, y) = sum_r (sum_a C[r][a] phi_a(x)) (sum_b D[r][b] chi_b(y)),
+ * phi_a = cos(a pi x / L_x) (a < px, even under x -> -x), chi_b the real Fourier modes of y
+ * (1, cos, sin, cos 2, ...; b < py), both sampled on a context's grid and normalised there.
+ * Trained on the GPU (FP32 forward, backward and Adam kernels); inference (tps_ws_predict)
+ * runs with BF16 weights.  Parameters: one FP32 array, per layer l = 0..3 the weights
+ * W_l[in][out] row-major then the biases b_l[out], layer widths 4, hidden, hidden, hidden,
+ * rank (px + py).  Loss per sample against a target T (px x py, from tps_ws_project):
+ *     L = 1 - <P, T>^2 / (|P|^2 |T|^2),  P = C^T D,
+ * invariant under the arbitrary sign and scale of an eigenvector; the mean over the batch
+ * is minimised.  1D only. */
+typedef struct tps_ws tps_ws;
+
+/* Create a model on `device` with He-initialised weights (counter-based generator from
+ * seed).  px, py <= 128, rank <= 64, hidden <= 4096. */
+int tps_ws_create(tps_ws **out, int device, int px, int py, int rank, int hidden,
+                  unsigned long long seed);
+int tps_ws_destroy(tps_ws *ws);
+const char *tps_ws_last_error(const tps_ws *ws);
+/* Number of parameters and output width rank (px + py). */
+int tps_ws_info(const tps_ws *ws, long long *nparam, int *out_dim);
+/* Copy the FP32 parameters out / in (host arrays of exactly nparam floats; synchronous). */
+int tps_ws_get_params(tps_ws *ws, float *params_host, long long nparam);
+int tps_ws_set_params(tps_ws *ws, const float *params_host, long long nparam);
+/* Host feature map, X[i] = (ln(M/m) / ln 40, ln(v0) / 5, ln(sigma) / ln 2, state / 8) for
+ * n states; all inputs positive (state >= 0). */
+int tps_ws_features(int n, const double *mass_ratio, const double *v0, const double *sigma,
+                    const int *state, float *X_host);
+/* Network outputs out[B][rank (px + py)] for features X[B][4] (device FP32); bf16 = 1 uses
+ * the BF16 weights.  Asynchronous on stream. */
+int tps_ws_forward(tps_ws *ws, const float *X_dev, int B, int bf16, float *out_dev,
+                   cudaStream_t stream);
+/* Forward + backward for a batch: mean loss (host, nullable) and dL/dparams kept in the
+ * model for tps_ws_adam_step (also copied to grad_host[nparam] if not null).  Synchronous
+ * when loss_host or grad_host is given. */
+int tps_ws_loss_grad(tps_ws *ws, const float *X_dev, const float *T_dev, int B,
+                     double *loss_host, float *grad_host, cudaStream_t stream);
+/* One Adam step (Kingma & Ba) with the gradient of the last tps_ws_loss_grad call. */
+int tps_ws_adam_step(tps_ws *ws, float lr, float beta1, float beta2, float eps,
+                     cudaStream_t stream);
+/* Training targets: T[v] = Phi^T psi_v Chi (px x py, FP32) of k eigenvectors evecs[k][N]
+ * (device, FP64, the context's full 1D grid).  Needs 2 px <= n_x and py < n_y. */
+int tps_ws_project(tps_ws *ws, tps_ctx *ctx, const double *evecs_dev, int k, float *T_dev,
+                   cudaStream_t stream);
+/* Predicted states on the context's full grid: x0[k][N] (device FP64) for features
+ * X[k][4] (device FP32).  Unnormalised; the solver orthonormalises its start block. */
+int tps_ws_predict(tps_ws *ws, tps_ctx *ctx, const float *X_dev, int k, double *x0_dev,
+                   cudaStream_t stream);
+/* tps_solve started from the model's prediction for states 0 .. k + guard - 1 of
+ * (mass_ratio, v0, sigma) (guard from opts, default 2; the solver's first block then
+ * spans every wanted pair); if that solve does not converge, the cold-started solver
+ * runs instead (*used_warm = 0).  ws = NULL: the cold-started solver.  Same outputs and
+ * errors as tps_solve. */
+int tps_ws_solve(tps_ws *ws, tps_ctx *ctx, double mass_ratio, double v0, double sigma, int k,
+                 int parity, double tol, int block, const tps_solver_opts *opts,
+                 double *evals_host, double *evecs_dev, tps_stats *stats, int *used_warm,
+                 cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -555,10 +555,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   uint64_t rng_counter = 0;
   std::vector<double> lam(k, 0.0), resid(k, 0.0);
 
-  // start block: warm start restricted to the sector, completed with random columns
+  // start block: warm start restricted to the sector, completed with random columns.  A
+  // warm start may fill a first block as wide as all k + guard wanted pairs: a start that
+  // holds only the first b of them leaves the rest to be found late (the corrections aim
+  // at the states already present)
   int bn = b;
   {
-    const int nw = std::min(n_x0, b);
+    const int nw = std::min(n_x0, std::max(b, k));
+    if (nw > b) bn = nw;
     if (nw > 0 && x0) {
       if (parity != TPS_ANY)
         launch_sector_restrict(parity, ctx->n[0], ctx->n[1], nw, x0, w.V, s);

@@ -89,3 +89,19 @@ def sweep_instances(count: int = 256, seed: int = 3):
         n = int(rng.choice([128, 192, 256, 384]))
         out.append(dict(M=float(ratio), m=1.0, E0=E0, sigma=sigma, n=n, L=20.0))
     return out
+
+
+def warmstart_instances(count: int, seed: int, ratio=(1.0, 40.0), E0=(1e-4, 1.0),
+                        sigmas=(0.5, 1.0, 2.0), ns=(128, 192, 256, 384), L: float = 20.0):
+    """Parameters of 1D instances for the learned warm start (same fields as
+    sweep_instances): M/m uniform in `ratio`, E0 log-uniform in `E0`, sigma and n drawn
+    from the given sets."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        r = rng.uniform(*ratio)
+        e = float(np.exp(rng.uniform(np.log(E0[0]), np.log(E0[1]))))
+        s = float(rng.choice(list(sigmas)))
+        n = int(rng.choice(list(ns)))
+        out.append(dict(M=float(r), m=1.0, E0=e, sigma=s, n=n, L=L))
+    return out

@@ -101,6 +101,22 @@ _sig = {
                                   C.c_double, C.c_int, C.POINTER(SolverOpts), _dp, C.c_int,
                                   C.POINTER(C.c_void_p), C.POINTER(Stats), C.POINTER(C.c_int),
                                   C.c_int]),
+    "tps_ws_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int,
+                                C.c_int, C.c_ulonglong]),
+    "tps_ws_destroy": (C.c_int, [_vp]),
+    "tps_ws_last_error": (C.c_char_p, [_vp]),
+    "tps_ws_info": (C.c_int, [_vp, C.POINTER(_ll), C.POINTER(C.c_int)]),
+    "tps_ws_get_params": (C.c_int, [_vp, _vp, _ll]),
+    "tps_ws_set_params": (C.c_int, [_vp, _vp, _ll]),
+    "tps_ws_features": (C.c_int, [C.c_int, _dp, _dp, _dp, _ip, C.POINTER(C.c_float)]),
+    "tps_ws_forward": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp]),
+    "tps_ws_loss_grad": (C.c_int, [_vp, _vp, _vp, C.c_int, _dp, _vp, _vp]),
+    "tps_ws_adam_step": (C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float, _vp]),
+    "tps_ws_project": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "tps_ws_predict": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "tps_ws_solve": (C.c_int, [_vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                               C.c_double, C.c_int, C.POINTER(SolverOpts), _dp, _vp,
+                               C.POINTER(Stats), _ip, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -279,3 +295,106 @@ class Context:
         self._check(_lib.tps_correction(self._h, _ptr(Qt), nq, _ptr(R), _ptr(theta), nsys, steps,
                                         use_prec, shift if use_prec else math.nan, _ptr(T),
                                         _stream(stream)), "correction")
+
+
+class WarmStart:
+    """Learned warm-start model (tps_ws_*): an MLP from (M/m, v0, sigma, state index) to a
+    rank-R separable start vector, trained on the GPU by the library's own kernels."""
+
+    def __init__(self, px=32, py=32, rank=16, hidden=256, seed=1, device=0):
+        h = C.c_void_p()
+        st = _lib.tps_ws_create(C.byref(h), device, px, py, rank, hidden, seed)
+        if st != OK:
+            raise TpsError(st, "tps_ws_create")
+        self._h, self.px, self.py, self.rank, self.hidden = h, px, py, rank, hidden
+        n, d = C.c_longlong(), C.c_int()
+        _lib.tps_ws_info(self._h, C.byref(n), C.byref(d))
+        self.nparam, self.out_dim = n.value, d.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tps_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st, what):
+        if st != OK:
+            raise TpsError(st, f"{what}: {_lib.tps_ws_last_error(self._h).decode()}")
+
+    def get_params(self):
+        a = np.empty(self.nparam, dtype=np.float32)
+        self._check(_lib.tps_ws_get_params(self._h, a.ctypes.data_as(C.c_void_p), self.nparam),
+                    "get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        self._check(_lib.tps_ws_set_params(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+                    "set_params")
+
+    @staticmethod
+    def features(mass_ratio, v0, sigma, state):
+        mr, vv, sg = (np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64)
+                      for a in (mass_ratio, v0, sigma))
+        stt = np.ascontiguousarray(np.atleast_1d(state), dtype=np.int32)
+        n = stt.size
+        out = np.empty((n, 4), dtype=np.float32)
+        st = _lib.tps_ws_features(n, mr.ctypes.data_as(_dp), vv.ctypes.data_as(_dp),
+                                  sg.ctypes.data_as(_dp), stt.ctypes.data_as(_ip),
+                                  out.ctypes.data_as(C.POINTER(C.c_float)))
+        if st != OK:
+            raise TpsError(st, "tps_ws_features")
+        return out
+
+    def forward(self, X, bf16=False, stream=None):
+        import torch
+        out = torch.empty(X.shape[0], self.out_dim, dtype=torch.float32, device=X.device)
+        self._check(_lib.tps_ws_forward(self._h, _ptr(X), X.shape[0], 1 if bf16 else 0,
+                                        _ptr(out), _stream(stream)), "forward")
+        return out
+
+    def loss_grad(self, X, T, want_grad=False, stream=None):
+        loss = C.c_double()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grad else None
+        self._check(_lib.tps_ws_loss_grad(self._h, _ptr(X), _ptr(T), X.shape[0], C.byref(loss),
+                                          g.ctypes.data_as(C.c_void_p) if want_grad else None,
+                                          _stream(stream)), "loss_grad")
+        return loss.value, g
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(_lib.tps_ws_adam_step(self._h, lr, beta1, beta2, eps, _stream(stream)),
+                    "adam_step")
+
+    def project(self, ctx, evecs, stream=None):
+        import torch
+        k = evecs.shape[0]
+        T = torch.empty(k, self.px, self.py, dtype=torch.float32, device=evecs.device)
+        self._check(_lib.tps_ws_project(self._h, ctx._h, _ptr(evecs), k, _ptr(T),
+                                        _stream(stream)), "project")
+        return T
+
+    def predict(self, ctx, X, stream=None):
+        import torch
+        k = X.shape[0]
+        out = torch.empty(k, ctx.info()[0], dtype=torch.float64, device=X.device)
+        self._check(_lib.tps_ws_predict(self._h, ctx._h, _ptr(X), k, _ptr(out), _stream(stream)),
+                    "predict")
+        return out
+
+
+def solve_warm(model, ctx, mass_ratio, v0, sigma, k, parity, tol, block, evecs, opts=None,
+               stream=None):
+    """tps_ws_solve: solve from the model's predicted start (model None: cold start).
+    Returns (eigenvalues, Stats, used_warm)."""
+    ev = (C.c_double * k)()
+    stats = Stats()
+    used = C.c_int()
+    st = _lib.tps_ws_solve(model._h if model is not None else None, ctx._h, mass_ratio, v0,
+                           sigma, k, parity, tol, block,
+                           C.byref(opts) if opts is not None else None, ev, _ptr(evecs),
+                           C.byref(stats), C.byref(used), _stream(stream))
+    if st != OK:
+        raise TpsError(st, f"tps_ws_solve: {_lib.tps_last_error(ctx._h).decode()}")
+    return np.array(ev[:k]), stats, bool(used.value)

@@ -1,0 +1,145 @@
+"""Learned warm start: data generation from the solver's own eigenvectors, training on the
+GPU (tps_ws_loss_grad / tps_ws_adam_step), and warm- versus cold-start evaluation.
+
+Every numerical step runs in the library's kernels; this module only sequences them.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import tps
+
+
+def make_context(inst, device=0):
+    """Context for one 1D instance (dict with M, m, E0, sigma, n, L); returns (ctx, v0)."""
+    ctx = tps.Context(1, device)
+    ctx.set_masses(inst["M"], inst["m"], 1.0)
+    ctx.set_grid([inst["n"], inst["n"]], [inst["L"], inst["L"]])
+    mu = inst["M"] * inst["m"] / (inst["M"] + inst["m"])
+    v0 = tps.two_body_v0(1, mu, 1.0, inst["E0"], tps.GAUSS, inst["sigma"], inst["n"], inst["L"])
+    ctx.set_pair_potential(tps.GAUSS, v0, inst["sigma"])
+    return ctx, v0
+
+
+def make_dataset(model, instances, k, block=None, nstreams=8, device=0, chunk=256):
+    """Solve every instance (k lowest x-even pairs, cold start, batched `chunk` instances at
+    a time) and project the eigenvectors onto the model's basis.  Returns (X [n*k, 4]
+    float32 torch, T [n*k, px, py] float32 torch, total solve seconds)."""
+    import torch
+    block = block or k
+    Xs, Ts, dt = [], [], 0.0
+    for c0 in range(0, len(instances), chunk):
+        part = instances[c0: c0 + chunk]
+        ctxs, v0s = zip(*[make_context(i, device) for i in part])
+        evecs = [torch.empty(k, c.info()[0], dtype=torch.float64, device="cuda") for c in ctxs]
+        t0 = time.perf_counter()
+        lam, stats, status = tps.solve_batch(list(ctxs), [k] * len(ctxs), tps.X_EVEN, 1e-12,
+                                             block, evecs, nstreams=nstreams)
+        torch.cuda.synchronize()
+        dt += time.perf_counter() - t0
+        if any(s != tps.OK for s in status):
+            raise RuntimeError("a training solve failed")
+        Xs.append(np.concatenate([model.features([i["M"] / i["m"]] * k, [v] * k,
+                                                 [i["sigma"]] * k, list(range(k)))
+                                  for i, v in zip(part, v0s)]))
+        Ts.append(torch.cat([model.project(c, e) for c, e in zip(ctxs, evecs)]))
+        torch.cuda.synchronize()
+        for c in ctxs:
+            c.close()
+        del evecs
+    return torch.from_numpy(np.concatenate(Xs)).cuda(), torch.cat(Ts), dt
+
+
+def train(model, X, T, steps=2000, batch=256, lr=1e-3, lr_final=1e-4, seed=0):
+    """Adam on random mini-batches with a geometric learning-rate decay; returns the loss
+    history (one value per step)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), generator=g).cuda()
+        xb, tb = X.index_select(0, idx).contiguous(), T.index_select(0, idx).contiguous()
+        loss, _ = model.loss_grad(xb, tb)
+        rate = lr * (lr_final / lr) ** (s / max(1, steps - 1))
+        model.adam_step(lr=rate)
+        losses.append(loss)
+    return losses
+
+
+def evaluate(model, instances, k, block=None, tol=1e-12, device=0):
+    """Cold start versus warm start on each instance: outer iterations, H applications
+    (MVMs, the paper's Table 2 count), solve time and the largest relative eigenvalue
+    difference between the two (the tests judge the eigenpairs with the oracle)."""
+    import torch
+    block = block or k
+    rows = []
+    for inst in instances:
+        ctx, v0 = make_context(inst, device)
+        ev = torch.empty(k, ctx.info()[0], dtype=torch.float64, device="cuda")
+        out = {}
+        for name, m in (("cold", None), ("warm", model)):
+            tps.solve_warm(m, ctx, inst["M"] / inst["m"], v0, inst["sigma"], k, tps.X_EVEN, tol,
+                           block, ev)  # warm-up (builds the sector operator and workspaces)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam, st, used = tps.solve_warm(m, ctx, inst["M"] / inst["m"], v0, inst["sigma"], k,
+                                           tps.X_EVEN, tol, block, ev)
+            torch.cuda.synchronize()
+            out[name] = (lam, st.outer_iters, time.perf_counter() - t0, used, st.h_applies)
+        ctx.close()
+        lc, lw = out["cold"][0], out["warm"][0]
+        rows.append({"cold_iters": out["cold"][1], "warm_iters": out["warm"][1],
+                     "cold_s": out["cold"][2], "warm_s": out["warm"][2],
+                     "cold_mvm": out["cold"][4], "warm_mvm": out["warm"][4],
+                     "used_warm": out["warm"][3],
+                     "rel_diff": float(np.max(np.abs(lc - lw) /
+                                              np.maximum(np.abs(lc), abs(lc[0]))))})
+    return rows
+
+
+def main(argv=None):
+    """Train a model on eigenvectors of the sweep-like generator and compare warm and cold
+    starts on unseen instances; prints one JSON line."""
+    import argparse
+    import json
+    import torch
+    from .inputs import warmstart_instances
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--train-instances", type=int, default=2500)
+    ap.add_argument("--k", type=int, default=8, help="eigenvectors per training instance")
+    ap.add_argument("--eval-instances", type=int, default=512)
+    ap.add_argument("--eval-n", type=int, default=256)
+    ap.add_argument("--eval-k", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--px", type=int, default=32)
+    ap.add_argument("--py", type=int, default=32)
+    args = ap.parse_args(argv)
+    model = tps.WarmStart(px=args.px, py=args.py, rank=16, hidden=256, seed=1)
+    train_set = warmstart_instances(args.train_instances, seed=21)
+    t0 = time.perf_counter()
+    X, T, solve_s = make_dataset(model, train_set, k=args.k, nstreams=16)
+    t1 = time.perf_counter()
+    losses = train(model, X, T, steps=args.steps, batch=256, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    test_set = warmstart_instances(args.eval_instances, seed=22, ns=(args.eval_n,))
+    rows = evaluate(model, test_set, k=args.eval_k)
+    mean = lambda key: float(np.mean([r[key] for r in rows]))
+    print(json.dumps({
+        "train": {"instances": len(train_set), "eigenvectors": int(X.shape[0]),
+                  "data_s": t1 - t0, "solve_s": solve_s, "train_s": t2 - t1,
+                  "steps": args.steps, "loss_first": float(np.mean(losses[:20])),
+                  "loss_last": float(np.mean(losses[-20:]))},
+        "eval": {"instances": len(rows), "n": args.eval_n, "k": args.eval_k,
+                 "cold_iters": mean("cold_iters"), "warm_iters": mean("warm_iters"),
+                 "cold_mvm": mean("cold_mvm"), "warm_mvm": mean("warm_mvm"),
+                 "cold_ms": 1e3 * mean("cold_s"), "warm_ms": 1e3 * mean("warm_s"),
+                 "used_warm": sum(r["used_warm"] for r in rows),
+                 "max_rel_diff": max(r["rel_diff"] for r in rows)}}))
+
+
+if __name__ == "__main__":
+    main()

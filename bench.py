@@ -41,9 +41,10 @@ SM_MAX_MHZ = 2070.0
 # digit-pair products of the tensor-core FP64 emulation (9 wave-function digits, 10
 # mode-matrix digits, levels i + j <= 9 kept): each one a BF16 MMA over the full product
 TC_PAIRS = 54
-# DRAM bytes per launch of each kernel from the ncu captures summarised in profiles/
-# (None where no capture of the current kernel exists)
-TRAFFIC_BYTES_PER_LAUNCH = {}
+# DRAM bytes (read + write) per launch of each kernel, mean over the launches captured by
+# ncu (profiles/k_update_k_gram_1d_n512.md, profiles/k_oz_gemm_1d_n512.md); a kernel that
+# changes after its capture is removed from this table
+TRAFFIC_BYTES_PER_LAUNCH = {"k_update": 28.09e6, "k_gram": 14.06e6, "k_oz_gemm": 62.6e6}
 
 
 def measured_peaks():

@@ -209,6 +209,9 @@ typedef struct tps_stats {
   double upd_flops;   /* 2 nrows p q each */
   double upd_bytes;   /* 8 nrows (p + q) each, + 8 nrows q when C is read */
   long long upd_launches;
+  int jacobi_calls;   /* Rayleigh-Ritz eigensolves (one per outer iteration) */
+  int jacobi_sweeps;  /* their cyclic Jacobi sweeps, summed */
+  int jacobi_rounds;  /* rounds that applied at least one rotation, summed */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

@@ -168,7 +168,7 @@ constexpr int JOUT = (JROWS * JMAX + JT - 1) / JT;  // output elements per threa
 
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
 k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
-         int mp) {
+         int mp, int *__restrict__ stat) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   __shared__ double A[2][JROWS][JMAX + 1];
@@ -232,7 +232,9 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
   const double inv_norm = normA > 0.0 ? 1.0 / normA : 0.0;
   int cur = 0;
   long long rnd = 0;
+  int sweeps = 0, rotating_rounds = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
+    ++sweeps;
     const int fl = sweep & 1;
     __syncthreads();
     if (tid == 0) rotated[fl] = 0;
@@ -298,6 +300,7 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
       const int any_rot = round_rot[rnd & 1];
       if (tid == 0) round_rot[(rnd + 1) & 1] = 0;
       if (!any_rot) continue;
+      ++rotating_rounds;
       const int nxt = cur ^ 1;
       for (int e = tid; e < R * mm; e += JT) {
         const int i = e / mm, j = e % mm, gi = r0 + i;
@@ -325,6 +328,11 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
     if (!go) break;
   }
   cluster.sync();  // final A and V complete everywhere
+  if (stat && rank == 0 && tid == 0) {  // sweeps, rounds with rotations, calls
+    atomicAdd(&stat[0], sweeps);
+    atomicAdd(&stat[1], rotating_rounds);
+    atomicAdd(&stat[2], 1);
+  }
   for (int i = tid; i < m; i += JT) diag[i] = Aat(cur, i, i);
   __syncthreads();
   // ascending order by rank (ties by index)
@@ -651,9 +659,9 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 }
 
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s, int mp) {
+                        cudaStream_t s, int mp, int *stat) {
   count_launch();
-  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0);
+  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,

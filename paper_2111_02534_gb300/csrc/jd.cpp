@@ -100,6 +100,7 @@ struct SolverWorkspace {
   double *Mq = nullptr, *Minv = nullptr;        // [(kmax+b)^2]
   double *Rinv = nullptr;                       // [b * b]
   int *keep = nullptr;                          // [b]
+  int *jstat = nullptr;                         // Jacobi sweeps, rotating rounds, calls
   GmresState gm;
   double *h_pinned = nullptr;                   // host readback buffer
   int *hi_pinned = nullptr;
@@ -390,6 +391,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.h = take((long long)b * (steps + 1));
   w->gm.nrm2 = take(b);
   w->keep = reinterpret_cast<int *>(take(bw));
+  w->jstat = reinterpret_cast<int *>(take(2));
   w->gm.done = reinterpret_cast<int *>(take(b));
   w->gm.mvalid = reinterpret_cast<int *>(take(b));
   if ((char *)p > (char *)w->arena + bytes) return set_error(ctx, TPS_ERR_CUDA, "arena overflow");
@@ -536,6 +538,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 4 * sizeof(int), s));
   struct TimingScope {
     explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
     ~TimingScope() { tl_timing = nullptr; }
@@ -631,7 +634,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp);
+    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat);
     warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
@@ -814,6 +817,16 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.h32_ms = w.tm.ms[2];
   stt.h32_flops = w.tm.flops[2];
   stt.h32_launches = w.tm.launches[2];
+  {
+    int js[4] = {0, 0, 0, 0};
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2048, w.jstat, 3 * sizeof(int),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    std::memcpy(js, w.hi_pinned + 2048, 3 * sizeof(int));
+    stt.jacobi_sweeps = js[0];
+    stt.jacobi_rounds = js[1];
+    stt.jacobi_calls = js[2];
+  }
   stt.gram_ms = w.tm.ms[3];
   stt.gram_flops = w.tm.flops[3];
   stt.gram_bytes = w.tm.bytes[3];

@@ -103,9 +103,10 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 // Eigenpairs of the symmetric m x m G (ld ldg): theta ascending, Y column-major (ld ldy).
 // mp > 0: the leading mp x mp block of G is unchanged since the previous call, whose
 // outputs theta[:mp] and Y[:mp, :mp] are still in theta and Y; they seed the solve and are
-// overwritten.
+// overwritten.  stat (device, nullable): adds sweeps, rounds with rotations and 1 to
+// stat[0..2].
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s, int mp = 0);
+                        cudaStream_t s, int mp = 0, int *stat = nullptr);
 // Cholesky G = R^T R of the b x b Gram matrix (ld b); writes Rinv (upper, ld b) and
 // keep[c] = 1 if column c has a pivot >= tol_rel * ref[c] (ref = squared column norms
 // before projection, device, may be null), else 0 (column dropped, Rinv column zero).

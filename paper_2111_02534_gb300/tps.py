@@ -58,7 +58,8 @@ class Stats(C.Structure):
                 ("gram_ms", C.c_double), ("gram_flops", C.c_double), ("gram_bytes", C.c_double),
                 ("gram_launches", C.c_longlong), ("upd_ms", C.c_double),
                 ("upd_flops", C.c_double), ("upd_bytes", C.c_double),
-                ("upd_launches", C.c_longlong),
+                ("upd_launches", C.c_longlong), ("jacobi_calls", C.c_int),
+                ("jacobi_sweeps", C.c_int), ("jacobi_rounds", C.c_int),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

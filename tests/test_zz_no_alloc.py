@@ -34,12 +34,16 @@ def test_noalloc_gram_matches_context_gram_twice():
         B = random_block(q, nrows, seed + 10)
         ref = _gram_with_context(ctx, A, p, B, q, nrows)
         G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
-        st = tps._lib.tps_gram_noalloc(ctypes.c_void_p(dev(A).data_ptr()), nrows, p,
-                                       ctypes.c_void_p(dev(B).data_ptr()), nrows, q, nrows,
+        # keep the device copies referenced until the kernel has read them (a temporary
+        # would return its memory to torch's cache, where the next copy could reuse it)
+        Ad, Bd = dev(A), dev(B)
+        st = tps._lib.tps_gram_noalloc(ctypes.c_void_p(Ad.data_ptr()), nrows, p,
+                                       ctypes.c_void_p(Bd.data_ptr()), nrows, q, nrows,
                                        ctypes.c_void_p(G.data_ptr()), p,
                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert st == tps.OK
         got = host(G)
+        del Ad, Bd
         scale = max(1.0, np.sqrt(nrows)) * max(1.0, np.abs(ref).max())
         assert np.max(np.abs(got - ref)) <= 1e-14 * scale
         assert np.max(np.abs(got.T - A @ B.T)) <= 1e-14 * scale

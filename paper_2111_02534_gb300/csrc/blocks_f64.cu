@@ -168,7 +168,7 @@ constexpr int JOUT = (JROWS * JMAX + JT - 1) / JT;  // output elements per threa
 
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
 k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
-         int mp, int *__restrict__ stat) {
+         int mp, int *__restrict__ stat, double tol_abs, double *Arot) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   __shared__ double A[2][JROWS][JMAX + 1];
@@ -177,6 +177,7 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
   __shared__ int partner[JMAX];
   __shared__ double diag[JMAX];
   __shared__ int perm[JMAX];
+  __shared__ int ipos[JMAX];
   __shared__ double part[JT / 32];
   __shared__ double norm_part;  // this CTA's squared Frobenius norm, read by the others
   __shared__ int rotated[2];    // per sweep parity; CTA 0's flag decides for the cluster
@@ -200,8 +201,9 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
     const int i = e / mm, j = e % mm, gi = r0 + i;
     double v = 0.0;
     if (gi < m && j < m) {
-      if (gi < mp && j < mp) {
-        v = (gi == j) ? theta[gi] : 0.0;
+      if (gi < mp && j < mp) {  // the previous call's rotated matrix (diag(theta) if exact)
+        v = Arot ? 0.5 * (Arot[(long long)j * ldy + gi] + Arot[(long long)gi * ldy + j])
+                 : ((gi == j) ? theta[gi] : 0.0);
       } else if (gi < mp) {  // (Y_prev^T G)[gi][j] = sum_a Y[a][gi] G[a][j]
 #pragma unroll 8
         for (int a = 0; a < mp; ++a) v = fma(Yout[(long long)gi * ldy + a], Gs(a, j), v);
@@ -229,6 +231,9 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
   double nrm2 = 0.0;
   for (int c = 0; c < JCL; ++c) nrm2 += *cluster.map_shared_rank(&norm_part, (unsigned)c);
   const double normA = sqrt(nrm2);
+  // entries below thr are left: the noise floor, or the caller's tolerance when the
+  // eigenvectors are only needed to a given accuracy
+  const double thr = fmax(8.9e-16 * normA, tol_abs);
   const double inv_norm = normA > 0.0 ? 1.0 / normA : 0.0;
   int cur = 0;
   long long rnd = 0;
@@ -262,7 +267,7 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
           // rounding noise that rotations of the largest entries leave behind (4 eps
           // ||A||_F); chasing entries under that floor never terminates.  Squared forms:
           // an FP64 square root or division costs about ten FMAs' latency on this GPU.
-          if (apq * apq > 1e-36 * fabs(app * aqq) && fabs(apq) > 8.9e-16 * normA) {
+          if (apq * apq > 1e-36 * fabs(app * aqq) && fabs(apq) > thr) {
             // t = tan(angle) zeroing a_pq: sign(d) a_pq / (|d| + sqrt(d^2 + a_pq^2)),
             // d = (a_qq - a_pp)/2, in FP32 on normA-scaled values; the rotation below is
             // orthogonal for any t, and a slightly inexact t leaves a_pq reduced by ~1e7
@@ -343,6 +348,16 @@ k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yo
     perm[rk] = i;
   }
   __syncthreads();
+  // the rotated matrix in sorted order: Arot[pos(c)][pos(r)] = A[r][c], pos = perm^-1.
+  // Arot is read (warm start) before the first cluster barrier, so it may be updated here
+  if (Arot) {
+    for (int i = tid; i < m; i += JT) ipos[perm[i]] = i;
+    __syncthreads();
+    for (int e = tid; e < R * m; e += JT) {
+      const int i = e / m, c = e % m, gi = r0 + i;
+      if (gi < m) Arot[(long long)ipos[c] * ldy + ipos[gi]] = A[cur][i][c];
+    }
+  }
   // Y[:, j] = (Q0 V)[:, perm[j]] for this CTA's rows, formed in registers first: with a
   // warm start every CTA reads the previous Y, which is overwritten in place
   double yv[JOUT];
@@ -659,9 +674,9 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 }
 
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s, int mp, int *stat) {
+                        cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot) {
   count_launch();
-  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat);
+  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,

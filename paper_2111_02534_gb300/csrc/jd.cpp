@@ -94,6 +94,7 @@ struct SolverWorkspace {
   double *T2 = nullptr;                                                // [b][N] scratch
   // small
   double *G = nullptr, *Y = nullptr;            // [mmax * mmax]
+  double *Arot = nullptr;                       // [mmax * mmax] Y^T G Y of the last Ritz solve
   double *theta = nullptr, *theta2 = nullptr;   // [mmax]
   double *nrm2 = nullptr, *ref = nullptr;       // [max(b, kmax + b)]
   double *C = nullptr;                          // [(kmax + mmax + b) * b] projection coefficients
@@ -346,7 +347,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   const long long nbig = 2LL * mmax + 2LL * mk2 + 2LL * (kmax + b) + 4LL * b +
                          (long long)(steps + 1) * b + bw;
   const int q = kmax + b;
-  const long long nsmall = 2LL * mmax * mmax + 2LL * mmax + 2LL * std::max(q, mmax) +
+  const long long nsmall = 3LL * mmax * mmax + 2LL * mmax + 2LL * std::max(q, mmax) +
                            2LL * (q + mmax + b) * std::max(b, q) + 2LL * q * q + (long long)bw * bw + bw +
                            /* gmres */ (long long)b * ((steps + 1) * steps + 2 * steps + (steps + 1) +
                                                       3 + steps + (steps + 1)) + 64;
@@ -373,6 +374,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->T2 = take((long long)bw * N);
   w->G = take((long long)mmax * mmax);
   w->Y = take((long long)mmax * mmax);
+  w->Arot = take((long long)mmax * mmax);
   w->theta = take(mmax);
   w->theta2 = take(mmax);
   w->nrm2 = take(std::max(q, mmax));
@@ -608,6 +610,10 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   double prev_res = INFINITY;
   int stall = 0, prev_nlock = -1;
   int warm_mp = 0;  // leading block of G already diagonalised by the last Jacobi call
+  // Ritz vectors are only needed to a fraction of the current residuals: the Jacobi
+  // eigensolve stops at 1e-3 of the smallest unconverged residual of the last iteration
+  // (its exact result Y^T G Y is kept in Arot, so no inexactness accumulates in G)
+  double jac_tol = 0.0;
   int st = TPS_OK;
   for (; outer < max_outer; ++outer) {
     // (1) orthonormalise the new block against the locked vectors and the basis
@@ -634,7 +640,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat);
+    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat, jac_tol, w.Arot);
     warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
@@ -658,6 +664,12 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     }
     if (!std::isfinite(w.h_pinned[0]))
       return set_error(ctx, TPS_ERR_NOT_CONVERGED, "non-finite Ritz value");
+    {
+      double rmin = INFINITY;
+      for (int i = nconv; i < nact; ++i)
+        rmin = std::min(rmin, std::sqrt(std::max(w.h_pinned[64 + i], 0.0)));
+      jac_tol = std::isfinite(rmin) ? 1e-3 * rmin : 0.0;
+    }
     nlock += nconv;
     if (nlock >= k) {
       converged = true;
@@ -693,7 +705,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       std::swap(w.HV, w.HV2);
       launch_copy_small(w.theta + nconv, w.theta2, mk, s);
       std::swap(w.theta, w.theta2);
-      launch_set_diag(w.G, ldG, w.theta, mk, s);
+      launch_copy_block(w.Arot, ldG, nconv, w.G, ldG, mk, s);  // G in the kept Ritz basis
       m = mk;
       warm_mp = 0;  // G's leading block is diagonal by construction
       ++stt.restarts;

@@ -118,6 +118,14 @@ __global__ void k_set_diag(double *G, int ldg, const double *d, int m) {
   G[(long long)j * ldg + i] = (i == j) ? d[i] : 0.0;
 }
 
+// dst[0:mk, 0:mk] = src[off:off+mk, off:off+mk] (column-major, leading dimensions lds, ldd)
+__global__ void k_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mk * mk) return;
+  const int i = e % mk, j = e / mk;
+  dst[(long long)j * ldd + i] = src[(long long)(j + off) * lds + (i + off)];
+}
+
 __global__ void k_copy_small(const double *src, double *dst, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = src[e];
@@ -171,6 +179,11 @@ void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str) {
 void launch_set_diag(double *G, int ldg, const double *d, int m, cudaStream_t str) {
   count_launch();
   k_set_diag<<<nb((long long)m * m), 128, 0, str>>>(G, ldg, d, m);
+}
+void launch_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk,
+                       cudaStream_t str) {
+  count_launch();
+  k_copy_block<<<nb((long long)mk * mk), 128, 0, str>>>(src, lds, off, dst, ldd, mk);
 }
 void launch_copy_small(const double *src, double *dst, int n, cudaStream_t str) {
   count_launch();

@@ -27,6 +27,8 @@ void launch_gmres_givens(int nsys, int s, int j, const double *nrm2, GmresState 
 void launch_gmres_solve(int nsys, int s, GmresState &st, cudaStream_t str);
 void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str);
 void launch_set_diag(double *G, int ldg, const double *d, int m, cudaStream_t str);
+void launch_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk,
+                       cudaStream_t str);
 void launch_copy_small(const double *src, double *dst, int n, cudaStream_t str);
 void launch_sqrt_div(const double *nrm2, double *out, int n, double div, cudaStream_t str);
 void launch_small_gemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,

@@ -104,9 +104,13 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 // mp > 0: the leading mp x mp block of G is unchanged since the previous call, whose
 // outputs theta[:mp] and Y[:mp, :mp] are still in theta and Y; they seed the solve and are
 // overwritten.  stat (device, nullable): adds sweeps, rounds with rotations and 1 to
-// stat[0..2].
+// stat[0..2].  tol_abs: off-diagonal entries below max(4 eps |A|_F, tol_abs) are left.
+// Arot (device, nullable, ld ldy): receives Y^T G Y (theta on its diagonal, the entries
+// left below the threshold off it); with mp > 0 its leading block is read as the
+// previous call's rotated matrix instead of diag(theta).
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s, int mp = 0, int *stat = nullptr);
+                        cudaStream_t s, int mp = 0, int *stat = nullptr, double tol_abs = 0.0,
+                        double *Arot = nullptr);
 // Cholesky G = R^T R of the b x b Gram matrix (ld b); writes Rinv (upper, ld b) and
 // keep[c] = 1 if column c has a pivot >= tol_rel * ref[c] (ref = squared column norms
 // before projection, device, may be null), else 0 (column dropped, Rinv column zero).

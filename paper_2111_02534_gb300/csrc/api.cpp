@@ -311,6 +311,24 @@ int ensure_gram_scratch(tps_ctx *ctx, long long doubles) {
   return TPS_OK;
 }
 
+// A new potential changes only V: the sector operators already built keep their mode
+// matrices, eigenbases and tensor-core digit slices and get the folded V in place.
+int refresh_sector_potentials(tps_ctx *ctx) {
+  const int ny = ctx->n[1];
+  for (int p = TPS_X_EVEN; p <= TPS_X_ODD; ++p) {
+    if (!ctx->sect_ready[p]) continue;
+    DevOperator &op = ctx->sect[p];
+    const int nr = op.n[0], off = p == TPS_X_EVEN ? 0 : 1;
+    std::vector<double> V((size_t)nr * ny);
+    for (int r = 0; r < nr; ++r)
+      for (int j = 0; j < ny; ++j) V[(size_t)r * ny + j] = ctx->V_host[(size_t)(r + off) * ny + j];
+    std::vector<float> Vf(V.begin(), V.end());
+    TPS_CUDA_TRY(ctx, cudaMemcpy(op.V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TPS_CUDA_TRY(ctx, cudaMemcpy(op.Vf, Vf.data(), Vf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return TPS_OK;
+}
+
 int build_sector_operator(tps_ctx *ctx, int parity) {
   if (ctx->sect_ready[parity]) return TPS_OK;
   if (ctx->dim != 1) return set_error(ctx, TPS_ERR_INVALID_ARG, "parity sectors are 1D only");
@@ -460,9 +478,9 @@ int tps_set_potential(tps_ctx *ctx, const double *V, int on_device) {
     TPS_CUDA_TRY(ctx, cudaMemcpy(ctx->full.Vf, vf.data(), vf.size() * sizeof(float),
                                  cudaMemcpyHostToDevice));
   }
-  for (int p = 0; p < 3; ++p) {
-    free_operator(ctx->sect[p]);
-    ctx->sect_ready[p] = false;
+  if (ctx->dim == 1) {
+    st = refresh_sector_potentials(ctx);
+    if (st) return st;
   }
   TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));  // uploads complete (see above)
   ctx->have_V = true;
@@ -476,16 +494,19 @@ int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma) {
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad shape, sigma or v0");
   std::vector<double> V(ctx->full.N);
   if (ctx->dim == 1) {
-    const int nx = ctx->n[0], ny = ctx->n[1];
-    for (int i = 0; i < nx; ++i) {
-      const double x = grid_x(nx, ctx->L[0], i);
-      for (int j = 0; j < ny; ++j) {
-        const double y = grid_x(ny, ctx->L[1], j);
-        V[(size_t)i * ny + j] =
-            -v0 * (shape_f(shape, std::fabs(y - 0.5 * x) / sigma) +
-                   shape_f(shape, std::fabs(y + 0.5 * x) / sigma));
-      }
-    }
+    // evaluated on the device (a host loop over all grid points costs milliseconds), then
+    // kept on the host too for the sector folding
+    cudaSetDevice(ctx->device);
+    launch_pair_potential_1d(ctx->n[0], ctx->n[1], ctx->L[0], ctx->L[1], shape, v0, sigma,
+                             ctx->full.V, ctx->full.Vf, cudaStreamLegacy);
+    TPS_CUDA_TRY(ctx, cudaGetLastError());
+    TPS_CUDA_TRY(ctx, cudaMemcpy(ctx->V_host.data(), ctx->full.V, ctx->full.N * sizeof(double),
+                                 cudaMemcpyDeviceToHost));
+    st = refresh_sector_potentials(ctx);
+    if (st) return st;
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));
+    ctx->have_V = true;
+    return TPS_OK;
   } else {
     const int nx = ctx->n[0], ny = ctx->n[2];
     size_t e = 0;

@@ -496,6 +496,32 @@ __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__res
 }
 
 // ------------------------------ elementwise ----------------------------------
+// Eq. definition_potential on the 1D grid: V[i][j] = -v0 (f(|y_j - x_i/2|/sigma) +
+// f(|y_j + x_i/2|/sigma)), f = exp(-xi^2) (shape 0) or (1 + xi^2)^-3 (shape 1), with
+// x_i = -L_x + i 2L_x/n_x; also the FP32 copy.
+__global__ void k_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,
+                                    double sigma, double *__restrict__ V, float *__restrict__ Vf) {
+  const long long total = (long long)nx * ny;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ny), j = (int)(e % ny);
+    const double x = -Lx + i * (2.0 * Lx / nx), y = -Ly + j * (2.0 * Ly / ny);
+    const double a = fabs(y - 0.5 * x) / sigma, b = fabs(y + 0.5 * x) / sigma;
+    double fa, fb;
+    if (shape == 0) {
+      fa = exp(-a * a);
+      fb = exp(-b * b);
+    } else {
+      const double ta = 1.0 + a * a, tb = 1.0 + b * b;
+      fa = 1.0 / (ta * ta * ta);
+      fb = 1.0 / (tb * tb * tb);
+    }
+    const double v = -v0 * (fa + fb);
+    V[e] = v;
+    Vf[e] = (float)v;
+  }
+}
+
 __global__ void k_axpby_cols(int ncols, long long nrows, double alpha, const double *X,
                              long long ldx, double beta, double *Y, long long ldy) {
   const long long total = (long long)ncols * nrows;
@@ -677,6 +703,13 @@ void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *
                         cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot) {
   count_launch();
   k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
+}
+
+void launch_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,
+                              double sigma, double *V, float *Vf, cudaStream_t s) {
+  count_launch();
+  k_pair_potential_1d<<<grid_for((long long)nx * ny), 256, 0, s>>>(nx, ny, Lx, Ly, shape, v0,
+                                                                   sigma, V, Vf);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,

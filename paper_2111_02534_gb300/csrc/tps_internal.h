@@ -120,6 +120,9 @@ void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, 
 void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s);
 
 // Elementwise helpers.
+// The pair potential of Eq. definition_potential on the full 1D grid (FP64 and FP32 copies).
+void launch_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,
+                              double sigma, double *V, float *Vf, cudaStream_t s);
 void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X, long long ldx,
                        double beta, double *Y, long long ldy, cudaStream_t s);
 // Y[:, c] = X[:, c] * scale[c] (scale device); safe in place.

@@ -252,3 +252,28 @@ def test_full_size_fp64_and_mixed_agree(h_dtype, h64_dtype):
         assert st.h32_launches > 0 and st.h32_flops > 0
     else:
         assert st.h32_launches == 0
+
+
+def test_new_potential_on_a_used_context_matches_a_fresh_context():
+    # changing the potential keeps the context's sector operators (mode matrices,
+    # eigenbases, tensor-core slices) and refreshes only their V
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n64"]
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, w.v0, w.sigma)
+    lam_a, _, _ = _solve(ctx, w.k, tps.X_EVEN, w.block)
+    ctx.set_pair_potential(tps.GAUSS, 1.7 * w.v0, 0.8)
+    lam_b, Xb, _ = _solve(ctx, w.k, tps.X_EVEN, w.block)
+    fresh = make_ctx_1d(w.M, w.m, w.n, w.L, 1.7 * w.v0, 0.8)
+    lam_f, _, _ = _solve(fresh, w.k, tps.X_EVEN, w.block)
+    assert np.max(np.abs(lam_b - lam_f) / np.abs(lam_f)) <= 1e-11
+    assert np.max(np.abs(lam_b - lam_a) / np.abs(lam_a)) > 1e-3
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, 1.7 * w.v0, 0.8)
+    ref, _ = lowest_dense(P, w.k, O_EVEN)
+    assert np.max(np.abs(lam_b - ref) / np.abs(ref)) <= 1e-10
+    # an explicit potential array (host path) on the same context
+    ctx.set_potential(P.V.ravel())
+    lam_c, _, _ = _solve(ctx, w.k, tps.X_EVEN, w.block)
+    assert np.max(np.abs(lam_c - ref) / np.abs(ref)) <= 1e-10
+    ctx.close()
+    fresh.close()

@@ -58,7 +58,7 @@ constexpr int kMaxSlices = 10;
 constexpr int kBM = 128;       // output rows per CTA (TMEM lanes)
 constexpr int kBN = 48;        // output columns per CTA; kLevels * kBN <= 512 TMEM columns
 constexpr int kBK = 64;        // contraction depth per stage (128-byte rows)
-constexpr int kAStages = 4;
+constexpr int kAStages = 6;  // A tiles in flight: each carries ~600 cycles of MMA work
 constexpr int kBStages = 2;
 constexpr int kThreads = 128;
 constexpr uint32_t kATileBytes = kBM * 128;
@@ -367,13 +367,18 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       long long hi[8], lo[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
-      for (int l = 0; l < L; ++l) {
-        uint32_t r[8];
-        tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r);
-        tc::tmem_ld_wait();
+      // all levels of these 8 columns in flight at once, one wait
+      uint32_t r[kLevels][8];
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l)
+        if (l < L) tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r[l]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l) {
+        if (l >= L) break;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const long long d = (long long)__float2int_rn(__uint_as_float(r[q]));
+          const long long d = (long long)__float2int_rn(__uint_as_float(r[l][q]));
           if (l < h)
             hi[q] = hi[q] * 64 + d;
           else

@@ -212,6 +212,9 @@ typedef struct tps_stats {
   int jacobi_calls;   /* Rayleigh-Ritz eigensolves (one per outer iteration) */
   int jacobi_sweeps;  /* their cyclic Jacobi sweeps, summed */
   int jacobi_rounds;  /* rounds that applied at least one rotation, summed */
+  int gs_orthogonalisations; /* block Gram-Schmidt orthogonalisations of new search blocks */
+  int gs_second_passes;      /* of which needed a second pass (a column kept < 1/sqrt 2 of
+                                its norm after the first) */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

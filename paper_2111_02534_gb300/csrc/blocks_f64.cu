@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(GT)
 k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
        const double *__restrict__ B, long long ldb, long long bsb, int q, long long nrows,
        int nchunk, double *__restrict__ partial, unsigned *__restrict__ count,
-       double *__restrict__ G, int ldg, long long bsg) {
+       double *__restrict__ G, int ldg, long long bsg, const int *__restrict__ need) {
+  if (need && *need == 0) return;  // conditional product (decided on the device)
   const int c = blockIdx.x, s = blockIdx.y, pb = blockIdx.z;
   const int qb = (q + 3) / 4;
   const int npb = ((p + 3) / 4) * qb;
@@ -109,7 +110,9 @@ int gram_chunks(long long nrows, int batch, int npb) {
 __global__ void __launch_bounds__(GT)
 k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
          const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha, double beta,
-         double *__restrict__ C, long long ldc, long long bsc, long long nrows) {
+         double *__restrict__ C, long long ldc, long long bsc, long long nrows,
+         const int *__restrict__ need) {
+  if (need && *need == 0) return;  // conditional product (decided on the device)
   const int s = blockIdx.y;
   const int j0 = blockIdx.z * 8;
   __shared__ double Ys[64][8];
@@ -665,7 +668,7 @@ long long gram_scratch_doubles(int p, int q, int batch) {
 
 void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
                  long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
-                 long long bsg, int batch, GramScratch &scr, cudaStream_t s) {
+                 long long bsg, int batch, GramScratch &scr, cudaStream_t s, const int *need) {
   if (p <= 0 || q <= 0 || batch <= 0) return;
   const int npb = ((p + 3) / 4) * ((q + 3) / 4);
   int nchunk = gram_chunks(nrows, batch, npb);
@@ -674,12 +677,12 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
   dim3 grid(nchunk, batch, npb);
   count_launch();
   k_gram<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial,
-                             scr.count, G, ldg, bsg);
+                             scr.count, G, ldg, bsg, need);
 }
 
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
-                   long long bsc, long long nrows, int batch, cudaStream_t s) {
+                   long long bsc, long long nrows, int batch, cudaStream_t s, const int *need) {
   if (q <= 0 || batch <= 0 || nrows <= 0) return;
   if (p <= 0) {  // C = beta * C
     for (int b = 0; b < batch; ++b) {
@@ -695,7 +698,7 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + 7) / 8);
     count_launch();
     k_update<<<grid, GT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha,
-                                 i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows);
+                                 i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows, need);
   }
 }
 
@@ -703,6 +706,24 @@ void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *
                         cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot) {
   count_launch();
   k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
+}
+
+__global__ void k_dgks_flag(const double *__restrict__ before, const double *__restrict__ after,
+                            int ncols, int *__restrict__ need, int *__restrict__ stat) {
+  if (threadIdx.x != 0) return;
+  int n = 0;
+  for (int j = 0; j < ncols; ++j) n |= after[j] < 0.5 * before[j];
+  *need = n;
+  if (stat) {
+    stat[0] += n;
+    stat[1] += 1;
+  }
+}
+
+void launch_dgks_flag(const double *before, const double *after, int ncols, int *need,
+                      int *stat, cudaStream_t s) {
+  count_launch();
+  k_dgks_flag<<<1, 32, 0, s>>>(before, after, ncols, need, stat);
 }
 
 void launch_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,

@@ -8,7 +8,8 @@
 // batched GEMM with no transpose.  Two phases share one accumulator: the 1D H-apply sums
 // K_x P and P K_y^T in registers.
 //
-// Each thread owns a 4x4 register tile; operands go through double-buffered shared
+// Each thread owns an R x R register tile (R = 4; R = 8 for the FP32 variants, which
+// needs a quarter of the shared-memory loads per FMA); operands go through double-buffered shared
 // memory, the next k-slab prefetched into registers while the current one is used.  Warps
 // whose rows all lie beyond M skip the arithmetic (the parity-folded x mode has 2^k + 1
 // rows, so the last row tile is nearly empty).
@@ -65,18 +66,18 @@ inline GemmArgs base_args() {
 
 constexpr int TK = 16;
 
-template <typename Acc, typename TA, typename TB, typename TC, int TM, int TN>
-__global__ void __launch_bounds__((TM / 4) * (TN / 4))
+template <typename Acc, typename TA, typename TB, typename TC, int TM, int TN, int R = 4>
+__global__ void __launch_bounds__((TM / R) * (TN / R))
 k_gemm(const GemmArgs g) {
-  constexpr int NT = (TM / 4) * (TN / 4);
+  constexpr int NT = (TM / R) * (TN / R);
   constexpr int LA = (TM * TK + NT - 1) / NT;
   constexpr int LB = (TK * TN + NT - 1) / NT;
   __shared__ Acc As[2][TK][TM + 1];
   __shared__ Acc Bs[2][TK][TN];
 
   const int tid = threadIdx.x;
-  const int tn = tid % (TN / 4);
-  const int tm = tid / (TN / 4);
+  const int tn = tid % (TN / R);
+  const int tm = tid / (TN / R);
   const long long bid = blockIdx.x;
   const int tiles = g.tiles_m * g.tiles_n;
   const long long z = bid / tiles;
@@ -84,14 +85,14 @@ k_gemm(const GemmArgs g) {
   const int m0 = (t / g.tiles_n) * TM;
   const int n0 = (t % g.tiles_n) * TN;
   // warp-uniform: the first row any thread of this warp owns
-  const int warp_tm0 = ((tid >> 5) << 5) / (TN / 4);
-  const bool live = m0 + warp_tm0 * 4 < g.M;
+  const int warp_tm0 = ((tid >> 5) << 5) / (TN / R);
+  const bool live = m0 + warp_tm0 * R < g.M;
 
-  Acc acc[4][4];
+  Acc acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+    for (int j = 0; j < R; ++j) acc[i][j] = Acc(0);
 
   const int ks0 = (g.K[0] + TK - 1) / TK;
   const int nstage = ks0 + (g.nphase > 1 ? (g.K[1] + TK - 1) / TK : 0);
@@ -146,15 +147,15 @@ k_gemm(const GemmArgs g) {
     if (live) {
 #pragma unroll
       for (int k = 0; k < TK; ++k) {
-        Acc a[4], b[4];
+        Acc a[R], b[R];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[buf][k][tm * 4 + i];
+        for (int i = 0; i < R; ++i) a[i] = As[buf][k][tm * R + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[buf][k][tn * 4 + j];
+        for (int j = 0; j < R; ++j) b[j] = Bs[buf][k][tn * R + j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
     }
     if (s + 1 < nstage) stash(buf ^ 1);
@@ -168,12 +169,12 @@ k_gemm(const GemmArgs g) {
   const Acc *lam2 = static_cast<const Acc *>(g.lam2), *lam3 = static_cast<const Acc *>(g.lam3);
   TC *Cz = static_cast<TC *>(g.C) + z * g.bsc;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + tm * 4 + i;
+  for (int i = 0; i < R; ++i) {
+    const int m = m0 + tm * R + i;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tn * 4 + j;
+    for (int j = 0; j < R; ++j) {
+      const int n = n0 + tn * R + j;
       if (n >= g.Nc) continue;
       Acc c = acc[i][j];
       TC *dst = Cz + (long long)m * g.ldc + n;
@@ -213,20 +214,28 @@ inline void pick_tiles(const GemmArgs &g, int &tm, int &tn) {
     }
 }
 
-template <typename Acc, typename TA, typename TB, typename TC, int TM, int TN>
+template <typename Acc, typename TA, typename TB, typename TC, int TM, int TN, int R = 4>
 void run(GemmArgs g, cudaStream_t s) {
   g.tiles_m = (g.M + TM - 1) / TM;
   g.tiles_n = (g.Nc + TN - 1) / TN;
   const long long blocks = (long long)g.batch * g.tiles_m * g.tiles_n;
   if (blocks <= 0) return;
   count_launch();
-  k_gemm<Acc, TA, TB, TC, TM, TN><<<(unsigned)blocks, (TM / 4) * (TN / 4), 0, s>>>(g);
+  k_gemm<Acc, TA, TB, TC, TM, TN, R><<<(unsigned)blocks, (TM / R) * (TN / R), 0, s>>>(g);
 }
 
+// Tile shapes: tm x tn per CTA with r x r per thread; r = 8 only for FP32 accumulation
+// (an 8 x 8 FP64 tile would not fit the register budget of the FP64 variants' occupancy).
 template <typename Acc, typename TA, typename TB, typename TC>
-void run_tiles(const GemmArgs &g, int tm, int tn, cudaStream_t s) {
+void run_tiles(const GemmArgs &g, int tm, int tn, cudaStream_t s, int r = 4) {
 #define TPS_TILE_CASE(X, Y) \
   if (tm == X && tn == Y) return run<Acc, TA, TB, TC, X, Y>(g, s);
+  if (r == 8 && sizeof(Acc) == 4) {
+    if (tm == 128 && tn == 128) return run<Acc, TA, TB, TC, 128, 128, 8>(g, s);
+    if (tm == 128 && tn == 64) return run<Acc, TA, TB, TC, 128, 64, 8>(g, s);
+    if (tm == 64 && tn == 128) return run<Acc, TA, TB, TC, 64, 128, 8>(g, s);
+    if (tm == 64 && tn == 64) return run<Acc, TA, TB, TC, 64, 64, 8>(g, s);
+  }
   TPS_TILE_CASE(64, 64) TPS_TILE_CASE(64, 48) TPS_TILE_CASE(64, 32)
   TPS_TILE_CASE(48, 64) TPS_TILE_CASE(48, 48) TPS_TILE_CASE(48, 32)
   TPS_TILE_CASE(32, 64) TPS_TILE_CASE(32, 48) TPS_TILE_CASE(32, 32)
@@ -235,8 +244,8 @@ void run_tiles(const GemmArgs &g, int tm, int tn, cudaStream_t s) {
 
 // Tile autotuner.  The k-loop order of k_gemm does not depend on the tile shape, so every
 // candidate computes bitwise-identical results and the choice only changes speed.  The
-// first launch of a GEMM shape (precision, M, Nc, K, batch, phases) times the nine
-// candidates with CUDA events on the caller's stream (each run twice, best kept), caches
+// first launch of a GEMM shape (precision, M, Nc, K, batch, phases) times the nine (FP32:
+// thirteen) candidates with CUDA events on the caller's stream (each run twice, best kept), caches
 // the fastest, and runs it; later launches of that shape use the cache.  Accumulating
 // epilogues (C += ...) cannot be re-run and keep the cost-model choice, as does every
 // launch while tuning is off or the stream is being captured.
@@ -252,9 +261,12 @@ struct TileKeyHash {
     return h;
   }
 };
+struct TileChoice {
+  int tm, tn, r;
+};
 struct TileCache {
   std::mutex mu;
-  std::unordered_map<TileKey, std::pair<int, int>, TileKeyHash> best;
+  std::unordered_map<TileKey, TileChoice, TileKeyHash> best;
 };
 TileCache &tile_cache();
 
@@ -272,35 +284,42 @@ void gemm(GemmArgs g, cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lock(tc.mu);
     auto it = tc.best.find(key);
-    if (it != tc.best.end()) return run_tiles<Acc, TA, TB, TC>(g, it->second.first, it->second.second, s);
+    if (it != tc.best.end())
+      return run_tiles<Acc, TA, TB, TC>(g, it->second.tm, it->second.tn, s, it->second.r);
   }
-  const int cand[3] = {32, 48, 64};
+  // candidates: 4 x 4 register tiles on 32/48/64-wide CTA tiles; for FP32 also 8 x 8
+  // register tiles on 64/128-wide CTA tiles
+  TileChoice cands[13];
+  int nc = 0;
+  for (int a : {32, 48, 64})
+    for (int b : {32, 48, 64}) cands[nc++] = {a, b, 4};
+  if (sizeof(Acc) == 4)
+    for (int a : {64, 128})
+      for (int b : {64, 128}) cands[nc++] = {a, b, 8};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best_ms = 1e30f;
-  int bm = tm, bn = tn;
-  for (int a : cand)
-    for (int b : cand)
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaEventRecord(e0, s);
-        run_tiles<Acc, TA, TB, TC>(g, a, b, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
-          best_ms = ms;
-          bm = a;
-          bn = b;
-        }
+  TileChoice bestc{tm, tn, 4};
+  for (int c = 0; c < nc; ++c)
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      run_tiles<Acc, TA, TB, TC>(g, cands[c].tm, cands[c].tn, s, cands[c].r);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        bestc = cands[c];
       }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lock(tc.mu);
-    tc.best[key] = {bm, bn};
+    tc.best[key] = bestc;
   }
-  run_tiles<Acc, TA, TB, TC>(g, bm, bn, s);
+  run_tiles<Acc, TA, TB, TC>(g, bestc.tm, bestc.tn, s, bestc.r);
 }
 
 // One left mode product: C[z] = A (M x M, shared) * B[z] (M x Nc), rows strided by rs.

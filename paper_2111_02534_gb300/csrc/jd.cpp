@@ -102,6 +102,7 @@ struct SolverWorkspace {
   double *Rinv = nullptr;                       // [b * b]
   int *keep = nullptr;                          // [b]
   int *jstat = nullptr;                         // Jacobi sweeps, rotating rounds, calls
+  int *dgks = nullptr;                          // second-pass flag, passes needed, decisions
   GmresState gm;
   double *h_pinned = nullptr;                   // host readback buffer
   int *hi_pinned = nullptr;
@@ -135,9 +136,10 @@ thread_local PhaseTiming *tl_timing = nullptr;
 // launch_gram / launch_update with CUDA-event timing and algorithmic work counts
 void tgram(const double *A, long long lda, long long bsa, int p, const double *B, long long ldb,
            long long bsb, int q, long long nrows, double *G, int ldg, long long bsg, int batch,
-           GramScratch &scr, cudaStream_t s) {
+           GramScratch &scr, cudaStream_t s, const int *need = nullptr) {
   PhaseTiming *t = tl_timing;
-  const bool live = t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  // conditional launches (need) may do nothing: neither timed nor counted
+  const bool live = !need && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
   if (live) t->launches[3] += 1;
   const bool rec = live && (t->seen[3]++ % PhaseTiming::kSample) == 0;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -146,7 +148,7 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s);
+  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[3].push_back({a, b});
@@ -157,9 +159,10 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
 
 void tupdate(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
              long long bsy, int q, double alpha, double beta, double *C, long long ldc,
-             long long bsc, long long nrows, int batch, cudaStream_t s) {
+             long long bsc, long long nrows, int batch, cudaStream_t s,
+             const int *need = nullptr) {
   PhaseTiming *t = tl_timing;
-  const bool live = t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  const bool live = !need && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
   if (live) t->launches[4] += 1;
   const bool rec = live && (t->seen[4]++ % PhaseTiming::kSample) == 0;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -168,7 +171,7 @@ void tupdate(const double *A, long long lda, long long bsa, int p, const double 
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s);
+  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s, need);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[4].push_back({a, b});
@@ -264,14 +267,22 @@ int orthonormalize(Ctx &c, const double *B1, int nb1, const double *B2, int nb2,
                    int *rank) {
   SolverWorkspace &w = c.w;
   col_norms2(c, T, b, w.ref);
-  for (int pass = 0; pass < 2; ++pass) {
+  // block classical Gram-Schmidt; the second pass runs only where the first lost more
+  // than half of a column's squared norm (the DGKS criterion), decided on the device
+  for (int pass = 0; pass < 2 && nb1 + nb2 > 0; ++pass) {
+    const int *need = nullptr;
+    if (pass == 1) {
+      col_norms2(c, T, b, w.nrm2);
+      launch_dgks_flag(w.ref, w.nrm2, b, w.dgks, w.dgks + 1, c.s);
+      need = w.dgks;
+    }
     if (nb1 > 0) {
-      tgram(B1, c.N, 0, nb1, T, c.N, 0, b, c.N, w.C, nb1, 0, 1, c.ctx->gscr, c.s);
-      tupdate(B1, c.N, 0, nb1, w.C, nb1, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+      tgram(B1, c.N, 0, nb1, T, c.N, 0, b, c.N, w.C, nb1, 0, 1, c.ctx->gscr, c.s, need);
+      tupdate(B1, c.N, 0, nb1, w.C, nb1, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s, need);
     }
     if (nb2 > 0) {
-      tgram(B2, c.N, 0, nb2, T, c.N, 0, b, c.N, w.C, nb2, 0, 1, c.ctx->gscr, c.s);
-      tupdate(B2, c.N, 0, nb2, w.C, nb2, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s);
+      tgram(B2, c.N, 0, nb2, T, c.N, 0, b, c.N, w.C, nb2, 0, 1, c.ctx->gscr, c.s, need);
+      tupdate(B2, c.N, 0, nb2, w.C, nb2, 0, b, -1.0, 1.0, T, c.N, 0, c.N, 1, c.s, need);
     }
   }
   // Cholesky QR twice; the first pass drops numerically dependent columns
@@ -394,6 +405,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.nrm2 = take(b);
   w->keep = reinterpret_cast<int *>(take(bw));
   w->jstat = reinterpret_cast<int *>(take(2));
+  w->dgks = reinterpret_cast<int *>(take(2));
   w->gm.done = reinterpret_cast<int *>(take(b));
   w->gm.mvalid = reinterpret_cast<int *>(take(b));
   if ((char *)p > (char *)w->arena + bytes) return set_error(ctx, TPS_ERR_CUDA, "arena overflow");
@@ -541,6 +553,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 4 * sizeof(int), s));
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
   struct TimingScope {
     explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
     ~TimingScope() { tl_timing = nullptr; }
@@ -830,11 +843,16 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.h32_flops = w.tm.flops[2];
   stt.h32_launches = w.tm.launches[2];
   {
-    int js[4] = {0, 0, 0, 0};
+    int js[4] = {0, 0, 0, 0}, gs[4] = {0, 0, 0, 0};
     TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2048, w.jstat, 3 * sizeof(int),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2056, w.dgks, 3 * sizeof(int),
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     std::memcpy(js, w.hi_pinned + 2048, 3 * sizeof(int));
+    std::memcpy(gs, w.hi_pinned + 2056, 3 * sizeof(int));
+    stt.gs_second_passes = gs[1];
+    stt.gs_orthogonalisations = gs[2];
     stt.jacobi_sweeps = js[0];
     stt.jacobi_rounds = js[1];
     stt.jacobi_calls = js[2];

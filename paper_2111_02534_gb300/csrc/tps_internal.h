@@ -90,14 +90,23 @@ struct GramScratch {
   unsigned *count = nullptr;  // per-block tickets of the one-launch Gram, zero between calls
   long long ncount = 0;
 };
-// G_s = A_s^T B_s (p x q, column-major ldg) for s < batch.
+// G_s = A_s^T B_s (p x q, column-major ldg) for s < batch.  need (device, nullable): the
+// product is skipped when *need == 0 (a decision taken by an earlier kernel).
 void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
                  long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
-                 long long bsg, int batch, GramScratch &scr, cudaStream_t s);
-// C_s = beta*C_s + alpha * A_s Y_s (Y column-major p x q, ldy, batch stride bsy).
+                 long long bsg, int batch, GramScratch &scr, cudaStream_t s,
+                 const int *need = nullptr);
+// C_s = beta*C_s + alpha * A_s Y_s (Y column-major p x q, ldy, batch stride bsy); need as
+// for launch_gram.
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
-                   long long bsc, long long nrows, int batch, cudaStream_t s);
+                   long long bsc, long long nrows, int batch, cudaStream_t s,
+                   const int *need = nullptr);
+// *need = 1 if any column lost more than half its squared norm: after[j] < 0.5 before[j]
+// (the DGKS criterion for a second Gram-Schmidt pass); also counts the decision in
+// stat[0] (passes needed) and stat[1] (decisions), stat nullable.
+void launch_dgks_flag(const double *before, const double *after, int ncols, int *need,
+                      int *stat, cudaStream_t s);
 
 // Small dense kernels (one CTA or one cluster each).
 // Eigenpairs of the symmetric m x m G (ld ldg): theta ascending, Y column-major (ld ldy).

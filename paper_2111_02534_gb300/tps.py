@@ -60,6 +60,7 @@ class Stats(C.Structure):
                 ("upd_flops", C.c_double), ("upd_bytes", C.c_double),
                 ("upd_launches", C.c_longlong), ("jacobi_calls", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("jacobi_rounds", C.c_int),
+                ("gs_orthogonalisations", C.c_int), ("gs_second_passes", C.c_int),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

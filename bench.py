@@ -217,6 +217,38 @@ def run_sweep(tps, torch, nstreams):
                         "n in {128,192,256,384}, L=20, 4 x-even pairs each, block 4"}
 
 
+def run_apply_2d(tps, torch, nvec=8, reps=5):
+    """H-apply throughput on the 2D workload (n = 48 per Cartesian component, 5.3 M
+    unknowns, 8 vectors): FP64 and FP32 mode products, algorithmic 2N(4n)+3N flops per
+    vector, CUDA events on the current stream."""
+    from paper_2111_02534_gb300.inputs import WORKLOADS, random_normal_block
+    w = WORKLOADS["2d_n48"]
+    ctx = tps.Context(2, torch.cuda.current_device())
+    ctx.set_masses(w.M, w.m, w.hbar)
+    ctx.set_grid(list(w.n), list(w.L))
+    ctx.set_pair_potential(tps.GAUSS, w.v0, w.sigma)
+    N = ctx.info()[0]
+    x = torch.from_numpy(random_normal_block(nvec, N, 5)).cuda()
+    y = torch.empty_like(x)
+    flops = nvec * (2.0 * N * sum(w.n) + 3.0 * N)
+    out = {"workload": "2d_n48: M/m = 20, n = 48^4 (5,308,416 unknowns), 8 vectors",
+           "nvec": nvec}
+    for name, dt in (("fp64", tps.F64), ("fp32", tps.F32)):
+        ctx.apply_h(x, y, 0.0, dtype=dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.apply_h(x, y, 0.0, dtype=dt)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name + "_ms"] = ms
+        out[name + "_tflops"] = flops / (ms / 1000.0) / 1e12
+    ctx.close()
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -363,6 +395,7 @@ def run_ours(args):
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = run_sweep(tps, torch, args.sweep_streams)
+    apply_2d = run_apply_2d(tps, torch) if rank == 0 and not args.no_sweep else None
 
     # per-kernel rates from the solver's own CUDA-event timers over the timed solves; the
     # kernel family with the largest share of the step is the roofline
@@ -462,6 +495,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if sweep is not None:
             line["sweep"] = sweep
+        if apply_2d is not None:
+            line["h_apply_2d"] = apply_2d
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

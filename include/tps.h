@@ -75,6 +75,12 @@ const char *tps_status_string(int status);
  * context gave up a bounded wait since the last call (TPS_ERR_TIMEOUT; its outputs are
  * then invalid) -- each such wait ends after about one second instead of hanging. */
 int tps_device_status(tps_ctx *ctx);
+/* Self-test of that failure path: a one-warp kernel waits on a barrier that nothing
+ * signals, gives up after `seconds` (0 < seconds <= 2) exactly as the tensor-core kernels'
+ * waits do, and records it; a second kernel then checks that the device still takes work.
+ * Returns TPS_ERR_TIMEOUT when both happened (the expected outcome), TPS_ERR_CUDA
+ * otherwise.  Synchronous; allocates and frees 8 bytes. */
+int tps_selftest_wait_timeout(int device, double seconds);
 
 /* ---- problem definition ------------------------------------------------- */
 

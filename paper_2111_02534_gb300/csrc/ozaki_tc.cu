@@ -618,6 +618,22 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
   return cudaSuccess;
 }
 
+// ------------------------------ failure-path self-test ------------------------------
+namespace {
+// Waits on an mbarrier that nothing arrives on, with the given limit: the bounded-wait
+// path of the tensor-core kernels, taken on purpose.
+__global__ void k_selftest_wait(long long limit, int *flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  tc::fence_barrier_init();
+  tc::mbar_wait_for(&bar, 0, flag, 7, limit);
+}
+__global__ void k_selftest_touch(int *flag) {
+  if (threadIdx.x == 0) flag[1] = 1;
+}
+}  // namespace
+
 // Reads (synchronously) and clears the operator's timed-out-wait flag.
 int tc_operator_status(const DevOperator &op) {
   if (!op.tc) return 0;
@@ -630,3 +646,27 @@ int tc_operator_status(const DevOperator &op) {
 }
 
 }  // namespace tps
+
+extern "C" int tps_selftest_wait_timeout(int device, double seconds) {
+  if (!(seconds > 0.0) || seconds > 2.0) return TPS_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return TPS_ERR_CUDA;
+  int *flag = nullptr;
+  if (cudaMalloc(&flag, 2 * sizeof(int)) != cudaSuccess) return TPS_ERR_NOMEM;
+  int h[2] = {0, 0};
+  bool ok = cudaMemset(flag, 0, 2 * sizeof(int)) == cudaSuccess;
+  if (ok) {
+    // SM clock cycles of the limit at the device's maximum clock (kHz attribute)
+    int khz = 2000000;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+    tps::count_launch();
+    tps::k_selftest_wait<<<1, 32>>>((long long)(seconds * khz * 1e3), flag);
+    // the device must still take work after the timed-out wait
+    tps::count_launch();
+    tps::k_selftest_touch<<<1, 32>>>(flag);
+    ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(h, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  cudaFree(flag);
+  if (!ok || h[1] != 1) return TPS_ERR_CUDA;
+  return h[0] == 7 ? TPS_ERR_TIMEOUT : TPS_ERR_CUDA;
+}

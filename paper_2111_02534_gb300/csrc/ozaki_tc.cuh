@@ -51,19 +51,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Wait for the phase of the given parity to complete; false (and *err = code) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+// Wait for the phase of the given parity to complete; false (and *err = code) when it has
+// not completed after limit SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, int *err, int code,
+                                              long long limit) {
   const uint32_t a = smem_addr(bar);
   if (mbar_try_wait(a, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     for (int i = 0; i < 256; ++i)
       if (mbar_try_wait(a, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       if (err) atomicExch(err, code);
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+  return mbar_wait_for(bar, parity, err, code, kWaitCycles);
 }
 
 // ------------------------------------ TMA -------------------------------------

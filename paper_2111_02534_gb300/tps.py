@@ -77,6 +77,7 @@ _sig = {
     "tps_last_error": (C.c_char_p, [_vp]),
     "tps_status_string": (C.c_char_p, [C.c_int]),
     "tps_device_status": (C.c_int, [_vp]),
+    "tps_selftest_wait_timeout": (C.c_int, [C.c_int, C.c_double]),
     "tps_set_masses": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "tps_set_alpha": (C.c_int, [_vp, C.c_double]),
     "tps_set_grid": (C.c_int, [_vp, _ip, _dp]),

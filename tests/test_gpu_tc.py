@@ -120,3 +120,22 @@ def test_solve_with_tc_products_full_size():
     ref = np.array(gold["evals"])
     assert np.max(np.abs(lam - ref) / np.maximum(np.abs(ref), abs(ref[0]))) <= 1e-10
     ctx.close()
+
+
+def test_bounded_wait_reports_timeout_and_the_device_stays_usable():
+    # the tensor-core kernels' waits give up after a bounded time and report it instead
+    # of hanging; the self-test takes that path on purpose (a barrier nothing signals)
+    require_gpu()
+    tps = _tps()
+    assert tps._lib.tps_selftest_wait_timeout(0, 0.2) == tps.ERR_TIMEOUT
+    assert tps._lib.tps_selftest_wait_timeout(0, 0.0) == tps.ERR_INVALID_ARG
+    # afterwards the library's kernels run and agree as before
+    ctx = make_ctx_1d(20.0, 1.0, (64, 64), (20.0, 20.0), 1.0, 1.0)
+    N, hn = ctx.info()
+    psi = dev(random_normal_block(2, N, 4))
+    a, b = torch.empty_like(psi), torch.empty_like(psi)
+    ctx.apply_h(psi, a, 0.0, dtype=tps.F64)
+    ctx.apply_h(psi, b, 0.0, dtype=tps.F64_TC)
+    ctx.device_status()
+    assert float(((a - b).norm(dim=1) / (hn * psi.norm(dim=1))).max()) <= 1e-14
+    ctx.close()

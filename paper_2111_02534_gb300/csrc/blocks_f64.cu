@@ -708,6 +708,47 @@ void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *
   k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
 }
 
+// out[c] = sum_r A[c][r]^2 for ncols columns (ld lda): one pass, one FMA per element.
+// Block (chunk, c) sums its rows into partial[c][chunk]; the last block of a column (ticket
+// after a fence) adds the chunks in order and re-arms the ticket.
+__global__ void __launch_bounds__(GT)
+k_col_norms2(const double *__restrict__ A, long long lda, long long nrows, int nchunk,
+             double *__restrict__ partial, unsigned *__restrict__ count, double *__restrict__ out) {
+  const int chunk = blockIdx.x, c = blockIdx.y;
+  const long long rows_per = (nrows + nchunk - 1) / nchunk;
+  const long long r0 = (long long)chunk * rows_per;
+  const long long r1 = r0 + rows_per < nrows ? r0 + rows_per : nrows;
+  const double *a = A + (long long)c * lda;
+  double s0 = 0.0, s1 = 0.0;
+  long long r = r0 + threadIdx.x;
+  for (; r + GT < r1; r += 2 * GT) {
+    const double x = a[r], y = a[r + GT];
+    s0 = fma(x, x, s0);
+    s1 = fma(y, y, s1);
+  }
+  if (r < r1) s0 = fma(a[r], a[r], s0);
+  double v = s0 + s1;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __shared__ double red[GT / 32];
+  __shared__ unsigned ticket;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < GT / 32; ++w) t += red[w];
+    partial[(long long)c * nchunk + chunk] = t;
+    __threadfence();
+    ticket = atomicAdd(&count[c], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0 || ticket != (unsigned)(nchunk - 1)) return;
+  __threadfence();
+  double t = 0.0;
+  for (int k = 0; k < nchunk; ++k) t += __ldcg(partial + (long long)c * nchunk + k);
+  out[c] = t;
+  count[c] = 0u;
+}
+
 __global__ void k_dgks_flag(const double *__restrict__ before, const double *__restrict__ after,
                             int ncols, int *__restrict__ need, int *__restrict__ stat) {
   if (threadIdx.x != 0) return;
@@ -718,6 +759,19 @@ __global__ void k_dgks_flag(const double *__restrict__ before, const double *__r
     stat[0] += n;
     stat[1] += 1;
   }
+}
+
+void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
+                       GramScratch &scr, cudaStream_t s) {
+  if (ncols <= 0) return;
+  long long nchunk = (2LL * 152 + ncols - 1) / ncols;
+  const long long maxc = (nrows + 2047) / 2048;
+  if (nchunk > maxc) nchunk = maxc;
+  if (nchunk > scr.capacity / ncols) nchunk = scr.capacity / ncols;
+  if (nchunk < 1) nchunk = 1;
+  count_launch();
+  k_col_norms2<<<dim3((unsigned)nchunk, ncols), GT, 0, s>>>(A, lda, nrows, (int)nchunk,
+                                                           scr.partial, scr.count, out);
 }
 
 void launch_dgks_flag(const double *before, const double *after, int ncols, int *need,

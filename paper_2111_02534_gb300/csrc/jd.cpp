@@ -258,7 +258,7 @@ void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double sh
 
 // diag(A^T A) for ncols columns -> out[ncols] (device)
 void col_norms2(Ctx &c, const double *A, int ncols, double *out) {
-  tgram(A, c.N, c.N, 1, A, c.N, c.N, 1, c.N, out, 1, 1, ncols, c.ctx->gscr, c.s);
+  launch_col_norms2(A, c.N, ncols, c.N, out, c.ctx->gscr, c.s);
 }
 
 // T (b cols) <- orthonormal basis of span(T) minus span(B1, B2); B1, B2 orthonormal blocks

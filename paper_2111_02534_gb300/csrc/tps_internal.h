@@ -102,6 +102,9 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
                    long long bsc, long long nrows, int batch, cudaStream_t s,
                    const int *need = nullptr);
+// out[c] = squared 2-norm of column c (ld lda, nrows rows), c < ncols; uses scr.
+void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
+                       GramScratch &scr, cudaStream_t s);
 // *need = 1 if any column lost more than half its squared norm: after[j] < 0.5 before[j]
 // (the DGKS criterion for a second Gram-Schmidt pass); also counts the decision in
 // stat[0] (passes needed) and stat[1] (decisions), stat nullable.

@@ -61,6 +61,13 @@ enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2 };  /* arithmetic of apply calls
  * splitting into six-bit digit slices per operand row (9 for the wave function, 10 for the
  * mode matrices; Ozaki scheme), exact FP32 accumulation per digit level, FP64
  * recombination; 1D H-apply only. */
+/* Rayleigh-Ritz eigensolver (Sec. 4.1, the projected problem G y = theta y, m <= 64):
+ * TPS_RR_MIXED: FP32 eigenvectors (tridiagonalisation, bisection, inverse iteration), then FP64
+ *   iterative refinement of the eigenvectors
+ *   (Ogita-Aishima, with close eigenvalues rotated as groups) to the same accuracy as
+ *   TPS_RR_JACOBI64, which the same launch runs instead if the refinement stalls;
+ * TPS_RR_JACOBI64: cyclic Jacobi in FP64. */
+enum { TPS_RR_MIXED = 0, TPS_RR_JACOBI64 = 1 };
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -183,6 +190,9 @@ typedef struct tps_solver_opts {
   int h64_dtype;      /* how every FP64 H-apply of the solver runs (refinement phase, FP64-only
                          mode, final Rayleigh quotients): TPS_F64_TC (default: tensor-core
                          emulation, 1D; 2D solves use the FMA pipe) or TPS_F64 (FMA pipe) */
+  int rr_method;      /* Rayleigh-Ritz eigensolver: TPS_RR_MIXED (default) or TPS_RR_JACOBI64 */
+  int rr_refine_max;  /* TPS_RR_MIXED: FP64 refinement iterations before the FP64 Jacobi
+                         takes over (0: 12) */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -215,12 +225,18 @@ typedef struct tps_stats {
   double upd_flops;   /* 2 nrows p q each */
   double upd_bytes;   /* 8 nrows (p + q) each, + 8 nrows q when C is read */
   long long upd_launches;
-  int jacobi_calls;   /* Rayleigh-Ritz eigensolves (one per outer iteration) */
+  int jacobi_calls;   /* Rayleigh-Ritz solves by the FP64 cyclic Jacobi (TPS_RR_JACOBI64, or
+                         a TPS_RR_MIXED fallback) */
   int jacobi_sweeps;  /* their cyclic Jacobi sweeps, summed */
   int jacobi_rounds;  /* rounds that applied at least one rotation, summed */
   int gs_orthogonalisations; /* block Gram-Schmidt orthogonalisations of new search blocks */
   int gs_second_passes;      /* of which needed a second pass (a column kept < 1/sqrt 2 of
                                 its norm after the first) */
+  int rr_mixed_calls;        /* Rayleigh-Ritz solves by TPS_RR_MIXED */
+  int rr_fp32_solves;        /* their FP32 eigensolves (starting vectors and group rotations) */
+  int rr_refine_iters;       /* their FP64 refinement iterations */
+  int rr_groups_rotated;     /* groups of close eigenvalues rotated inside the refinement */
+  int rr_fallbacks;          /* solves the FP64 Jacobi finished (refinement not converged) */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 
@@ -280,9 +296,10 @@ int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, co
 int tps_orthonormalize(tps_ctx *ctx, const double *Q_dev, long long ldq, int nq, double *T_dev,
                        long long ldt, int b, long long nrows, int *rank_host, cudaStream_t stream);
 
-/* Eigen-decomposition of a symmetric m x m matrix (m <= 64) on the device by cyclic
- * Jacobi (Rayleigh-Ritz of Sec. 4.1).  theta_dev: m eigenvalues ascending; Y_dev:
- * eigenvectors, column-major m x m with leading dimension ldy. */
+/* Eigen-decomposition of a symmetric m x m matrix (m <= 64) on the device (Rayleigh-Ritz
+ * of Sec. 4.1) by TPS_RR_MIXED.  theta_dev: m eigenvalues ascending; Y_dev: eigenvectors,
+ * column-major m x m with leading dimension ldy.  Off-diagonals of Y^T G Y are left below
+ * 8.9e-16 ||G||_F and Y^T Y - I below 4 m 2^-53. */
 int tps_small_eigh(tps_ctx *ctx, const double *G_dev, int m, int ldg, double *theta_dev,
                    double *Y_dev, int ldy, cudaStream_t stream);
 

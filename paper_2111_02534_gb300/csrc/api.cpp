@@ -749,7 +749,8 @@ int tps_small_eigh(tps_ctx *ctx, const double *G_dev, int m, int ldg, double *th
   if (!ctx) return TPS_ERR_INVALID_ARG;
   if (m < 1 || m > 64 || ldg < m || ldy < m || !G_dev || !theta_dev || !Y_dev)
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad small_eigh arguments");
-  launch_jacobi_eigh(G_dev, m, ldg, theta_dev, Y_dev, ldy, stream);
+  launch_rr_eigh(G_dev, m, ldg, theta_dev, Y_dev, ldy, stream, 0, nullptr, 0.0, nullptr,
+                 TPS_RR_MIXED);
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;
 }

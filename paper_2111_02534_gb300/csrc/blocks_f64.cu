@@ -1,15 +1,11 @@
 // FP64 block kernels for the Jacobi-Davidson steps of Sec. 4.1: tall-skinny Gram
 // matrices and block updates (orthogonalisation, Rayleigh-Ritz projection, Ritz
-// vectors, restarts, Arnoldi), the small dense eigen/Cholesky/Givens work on one
-// CTA, and elementwise helpers.  Everything stays on the device; the host only
+// vectors, restarts, Arnoldi), the small dense Cholesky/Givens work on one CTA, and
+// elementwise helpers (the small eigensolver is in rr_eigh.cu).  Everything stays on the device; the host only
 // reads a few scalars per outer iteration to steer the loop.
-#include <cooperative_groups.h>
-
 #include <cstring>
 
 #include "tps_internal.h"
-
-namespace cg = cooperative_groups;
 
 namespace tps {
 namespace {
@@ -139,261 +135,6 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
     double *dst = Cs + (long long)(j0 + j) * ldc + r;
     *dst = (beta == 0.0) ? acc[j] : fma(beta, *dst, acc[j]);
   }
-}
-
-// ------------------------------ Jacobi eigh ----------------------------------
-// Cyclic Jacobi with round-robin (tournament) ordering: each round rotates mm/2
-// disjoint pairs at once (Golub & Van Loan, symmetric Schur decomposition and the
-// parallel ordering of the cyclic Jacobi method); A' = J^T A J is formed element by
-// element from the two pairs an element's row and column belong to, V' = V J likewise.
-//
-// GB300 executes FP64 at a small fraction of the FP32 rate, and a round's update is
-// O(m^2) FP64 work, so the matrix is spread over a thread-block cluster: CTA r owns a
-// slab of rows of A and V and reads the partner rows it needs from the other CTAs'
-// shared memory.  Every CTA computes the (identical) rotation parameters of a round
-// itself, so one cluster barrier per round is the only cross-CTA synchronisation, and
-// the exit decision of each sweep is CTA 0's, read by all.
-constexpr int JMAX = 64;
-constexpr int JCL = 8;                 // CTAs per cluster
-constexpr int JROWS = JMAX / JCL;      // rows per CTA at most
-constexpr int JT = 256;
-
-// Warm start (mp > 0): the leading mp x mp block of G is the projection onto a basis
-// whose Ritz pairs (Y[:mp, :mp], theta[:mp]) the previous call returned, and only the
-// trailing columns are new.  The kernel then diagonalises A0 = Q0^T G Q0 with
-// Q0 = diag(Y_prev, I): its leading block is diag(theta_prev) (exactly, up to the
-// rounding the previous call left below its threshold), and the coupling block
-// Y_prev^T G_12 holds the previous Ritz vectors' residuals against the new columns, so
-// far fewer sweeps are needed than from the identity.  The result is Q0 V.  theta and
-// Y are read before the first cluster barrier / before the final write, so they may be
-// updated in place.
-constexpr int JOUT = (JROWS * JMAX + JT - 1) / JT;  // output elements per thread
-
-__global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
-k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
-         int mp, int *__restrict__ stat, double tol_abs, double *Arot) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  __shared__ double A[2][JROWS][JMAX + 1];
-  __shared__ double Vv[2][JROWS][JMAX + 1];
-  __shared__ double rc[JMAX], rs[JMAX];
-  __shared__ int partner[JMAX];
-  __shared__ double diag[JMAX];
-  __shared__ int perm[JMAX];
-  __shared__ int ipos[JMAX];
-  __shared__ double part[JT / 32];
-  __shared__ double norm_part;  // this CTA's squared Frobenius norm, read by the others
-  __shared__ int rotated[2];    // per sweep parity; CTA 0's flag decides for the cluster
-  __shared__ int act[JMAX];     // index rotates in this round
-  __shared__ int round_rot[2];  // any pair rotates in this round (by running round parity)
-  const int tid = threadIdx.x;
-  const int mm = (m + 1) & ~1;          // even number of players (m odd: one dummy)
-  const int R = (mm + JCL - 1) / JCL;   // rows per CTA
-  const int r0 = rank * R;
-  // element (row, col) of A in buffer buf, wherever its row lives
-  auto Aat = [&](int buf, int row, int col) -> double {
-    const double *p = cluster.map_shared_rank(&A[buf][row % R][col], (unsigned)(row / R));
-    return *p;
-  };
-  // symmetric part of G
-  auto Gs = [&](int r, int c) -> double {
-    return 0.5 * (G[(long long)c * ldg + r] + G[(long long)r * ldg + c]);
-  };
-  double f = 0.0;
-  for (int e = tid; e < R * mm; e += JT) {
-    const int i = e / mm, j = e % mm, gi = r0 + i;
-    double v = 0.0;
-    if (gi < m && j < m) {
-      if (gi < mp && j < mp) {  // the previous call's rotated matrix (diag(theta) if exact)
-        v = Arot ? 0.5 * (Arot[(long long)j * ldy + gi] + Arot[(long long)gi * ldy + j])
-                 : ((gi == j) ? theta[gi] : 0.0);
-      } else if (gi < mp) {  // (Y_prev^T G)[gi][j] = sum_a Y[a][gi] G[a][j]
-#pragma unroll 8
-        for (int a = 0; a < mp; ++a) v = fma(Yout[(long long)gi * ldy + a], Gs(a, j), v);
-      } else if (j < mp) {   // (G Y_prev)[gi][j], the same terms in the same order
-#pragma unroll 8
-        for (int a = 0; a < mp; ++a) v = fma(Yout[(long long)j * ldy + a], Gs(gi, a), v);
-      } else {
-        v = Gs(gi, j);
-      }
-    }
-    A[0][i][j] = v;
-    Vv[0][i][j] = (gi == j) ? 1.0 : 0.0;
-    f += v * v;
-  }
-  for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-  if ((tid & 31) == 0) part[tid >> 5] = f;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < JT / 32; ++w) t += part[w];
-    norm_part = t;
-    round_rot[0] = round_rot[1] = 0;
-  }
-  cluster.sync();
-  double nrm2 = 0.0;
-  for (int c = 0; c < JCL; ++c) nrm2 += *cluster.map_shared_rank(&norm_part, (unsigned)c);
-  const double normA = sqrt(nrm2);
-  // entries below thr are left: the noise floor, or the caller's tolerance when the
-  // eigenvectors are only needed to a given accuracy
-  const double thr = fmax(8.9e-16 * normA, tol_abs);
-  const double inv_norm = normA > 0.0 ? 1.0 / normA : 0.0;
-  int cur = 0;
-  long long rnd = 0;
-  int sweeps = 0, rotating_rounds = 0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    ++sweeps;
-    const int fl = sweep & 1;
-    __syncthreads();
-    if (tid == 0) rotated[fl] = 0;
-    __syncthreads();
-    for (int r = 0; r < mm - 1; ++r, ++rnd) {
-      cluster.sync();  // A[cur] complete in every CTA
-      // pairs of this round (circle method): (mm-1, r), ((r+k) mod (mm-1), (r-k) mod (mm-1));
-      // all pairs in one warp: FP64 work is paid per warp instruction
-      if (tid < mm / 2) {
-        const int k = tid;
-        int pi, qi;
-        if (k == 0) {
-          pi = mm - 1;
-          qi = r;
-        } else {
-          pi = (r + k) % (mm - 1);
-          qi = (r - k + (mm - 1)) % (mm - 1);
-        }
-        const int p = pi < qi ? pi : qi, q = pi < qi ? qi : pi;
-        double c = 1.0, sn = 0.0;
-        if (q < m) {
-          // the three loads go out together (one DSMEM round trip)
-          const double apq = Aat(cur, p, q), app = Aat(cur, p, p), aqq = Aat(cur, q, q);
-          // rotate unless a_pq is negligible relative to its diagonal pair or below the
-          // rounding noise that rotations of the largest entries leave behind (4 eps
-          // ||A||_F); chasing entries under that floor never terminates.  Squared forms:
-          // an FP64 square root or division costs about ten FMAs' latency on this GPU.
-          if (apq * apq > 1e-36 * fabs(app * aqq) && fabs(apq) > thr) {
-            // t = tan(angle) zeroing a_pq: sign(d) a_pq / (|d| + sqrt(d^2 + a_pq^2)),
-            // d = (a_qq - a_pp)/2, in FP32 on normA-scaled values; the rotation below is
-            // orthogonal for any t, and a slightly inexact t leaves a_pq reduced by ~1e7
-            const float df = (float)(0.5 * (aqq - app) * inv_norm);
-            const float af = (float)(apq * inv_norm);
-            const float tf = (df >= 0.f ? af : -af) / (fabsf(df) + sqrtf(df * df + af * af));
-            const double t = (double)tf;
-            // c = (1 + t^2)^(-1/2): FP32 estimate and two FP64 Newton steps (orthogonal to
-            // FP64 rounding), s = t c
-            const double u = 1.0 + t * t;
-            double cc = (double)rsqrtf((float)u);
-            cc = cc * (1.5 - 0.5 * u * cc * cc);
-            cc = cc * (1.5 - 0.5 * u * cc * cc);
-            c = cc;
-            sn = t * cc;
-            rotated[fl] = 1;
-            round_rot[rnd & 1] = 1;
-          }
-        }
-        act[p] = act[q] = (sn != 0.0);
-        // column p of J = c e_p - s e_q ; column q of J = s e_p + c e_q
-        partner[p] = q;
-        partner[q] = p;
-        rc[p] = c;
-        rs[p] = -sn;
-        rc[q] = c;
-        rs[q] = sn;
-      }
-      __syncthreads();
-      // a round without rotations changes nothing: keep the buffers.  Every CTA computed
-      // the same parameters, so all of them take the same branch (and the barrier count
-      // per round does not depend on it either way).  The other parity's flag is reset
-      // here: its last readers passed the barrier above, its next writers come after the
-      // next cluster barrier.
-      const int any_rot = round_rot[rnd & 1];
-      if (tid == 0) round_rot[(rnd + 1) & 1] = 0;
-      if (!any_rot) continue;
-      ++rotating_rounds;
-      const int nxt = cur ^ 1;
-      for (int e = tid; e < R * mm; e += JT) {
-        const int i = e / mm, j = e % mm, gi = r0 + i;
-        if (gi >= mm) continue;
-        if (!act[gi] && !act[j]) {  // both rotations are the identity here
-          A[nxt][i][j] = A[cur][i][j];
-          Vv[nxt][i][j] = Vv[cur][i][j];
-          continue;
-        }
-        const int pi = partner[gi], pj = partner[j];
-        const double ci = rc[gi], si = rs[gi], cj = rc[j], sj = rs[j];
-        // A'[i][j] = sum_{a in {i,pi}, b in {j,pj}} J[a][i] J[b][j] A[a][b]
-        const double v = ci * (cj * A[cur][i][j] + sj * A[cur][i][pj]) +
-                         si * (cj * Aat(cur, pi, j) + sj * Aat(cur, pi, pj));
-        A[nxt][i][j] = v;
-        Vv[nxt][i][j] = cj * Vv[cur][i][j] + sj * Vv[cur][i][pj];
-      }
-      cur = nxt;
-    }
-    // every CTA takes CTA 0's decision, so all of them run the same number of barriers;
-    // CTA 0 resets the other parity's flag next sweep, so this read cannot race with it
-    __syncthreads();
-    cluster.sync();
-    const int go = *cluster.map_shared_rank(&rotated[fl], 0u);
-    if (!go) break;
-  }
-  cluster.sync();  // final A and V complete everywhere
-  if (stat && rank == 0 && tid == 0) {  // sweeps, rounds with rotations, calls
-    atomicAdd(&stat[0], sweeps);
-    atomicAdd(&stat[1], rotating_rounds);
-    atomicAdd(&stat[2], 1);
-  }
-  for (int i = tid; i < m; i += JT) diag[i] = Aat(cur, i, i);
-  __syncthreads();
-  // ascending order by rank (ties by index)
-  for (int i = tid; i < m; i += JT) {
-    int rk = 0;
-    const double di = diag[i];
-    for (int j = 0; j < m; ++j) rk += (diag[j] < di) || (diag[j] == di && j < i);
-    perm[rk] = i;
-  }
-  __syncthreads();
-  // the rotated matrix in sorted order: Arot[pos(c)][pos(r)] = A[r][c], pos = perm^-1.
-  // Arot is read (warm start) before the first cluster barrier, so it may be updated here
-  if (Arot) {
-    for (int i = tid; i < m; i += JT) ipos[perm[i]] = i;
-    __syncthreads();
-    for (int e = tid; e < R * m; e += JT) {
-      const int i = e / m, c = e % m, gi = r0 + i;
-      if (gi < m) Arot[(long long)ipos[c] * ldy + ipos[gi]] = A[cur][i][c];
-    }
-  }
-  // Y[:, j] = (Q0 V)[:, perm[j]] for this CTA's rows, formed in registers first: with a
-  // warm start every CTA reads the previous Y, which is overwritten in place
-  double yv[JOUT];
-#pragma unroll
-  for (int t = 0; t < JOUT; ++t) {
-    const int e = tid + t * JT;
-    double v = 0.0;
-    if (e < R * m) {
-      const int i = e / m, j = e % m, gi = r0 + i;
-      const int pj = perm[j];
-      if (gi < mp) {  // sum_a Y_prev[gi][a] V[a][pj]; row a of V lives in CTA a / R
-#pragma unroll 8
-        for (int a = 0; a < mp; ++a)
-          v = fma(Yout[(long long)a * ldy + gi],
-                  *cluster.map_shared_rank(&Vv[cur][a % R][pj], (unsigned)(a / R)), v);
-      } else if (gi < m) {
-        v = Vv[cur][i][pj];
-      }
-    }
-    yv[t] = v;
-  }
-  cluster.sync();  // every CTA is done reading the previous Y
-#pragma unroll
-  for (int t = 0; t < JOUT; ++t) {
-    const int e = tid + t * JT;
-    if (e < R * m) {
-      const int i = e / m, j = e % m, gi = r0 + i;
-      if (gi < m) Yout[(long long)j * ldy + gi] = yv[t];
-    }
-  }
-  if (rank == 0)
-    for (int j = tid; j < m; j += JT) theta[j] = diag[perm[j]];
-  cluster.sync();  // keep this CTA's shared memory alive until the others are done
 }
 
 // ------------------------------ Cholesky QR ----------------------------------
@@ -700,12 +441,6 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     k_update<<<grid, GT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha,
                                  i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows, need);
   }
-}
-
-void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
-                        cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot) {
-  count_launch();
-  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
 }
 
 // out[c] = sum_r A[c][r]^2 for ncols columns (ld lda): one pass, one FMA per element.

@@ -404,7 +404,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.h = take((long long)b * (steps + 1));
   w->gm.nrm2 = take(b);
   w->keep = reinterpret_cast<int *>(take(bw));
-  w->jstat = reinterpret_cast<int *>(take(2));
+  w->jstat = reinterpret_cast<int *>(take(4));  // 8 counters
   w->dgks = reinterpret_cast<int *>(take(2));
   w->gm.done = reinterpret_cast<int *>(take(b));
   w->gm.mvalid = reinterpret_cast<int *>(take(b));
@@ -552,7 +552,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(opts.timing != 0);
-  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 4 * sizeof(int), s));
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 8 * sizeof(int), s));
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
   struct TimingScope {
     explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
@@ -653,7 +653,8 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_jacobi_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat, jac_tol, w.Arot);
+    launch_rr_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat, jac_tol, w.Arot,
+                   opts.rr_method, opts.rr_refine_max);
     warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
@@ -843,19 +844,24 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.h32_flops = w.tm.flops[2];
   stt.h32_launches = w.tm.launches[2];
   {
-    int js[4] = {0, 0, 0, 0}, gs[4] = {0, 0, 0, 0};
-    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2048, w.jstat, 3 * sizeof(int),
+    int js[8] = {0, 0, 0, 0, 0, 0, 0, 0}, gs[4] = {0, 0, 0, 0};
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2048, w.jstat, 8 * sizeof(int),
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.hi_pinned + 2056, w.dgks, 3 * sizeof(int),
                                       cudaMemcpyDeviceToHost, s));
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    std::memcpy(js, w.hi_pinned + 2048, 3 * sizeof(int));
+    std::memcpy(js, w.hi_pinned + 2048, 8 * sizeof(int));
     std::memcpy(gs, w.hi_pinned + 2056, 3 * sizeof(int));
     stt.gs_second_passes = gs[1];
     stt.gs_orthogonalisations = gs[2];
     stt.jacobi_sweeps = js[0];
     stt.jacobi_rounds = js[1];
     stt.jacobi_calls = js[2];
+    stt.rr_mixed_calls = js[3];
+    stt.rr_fp32_solves = js[4];
+    stt.rr_refine_iters = js[5];
+    stt.rr_groups_rotated = js[6];
+    stt.rr_fallbacks = js[7];
   }
   stt.gram_ms = w.tm.ms[3];
   stt.gram_flops = w.tm.flops[3];

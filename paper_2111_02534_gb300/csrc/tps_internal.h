@@ -120,9 +120,19 @@ void launch_dgks_flag(const double *before, const double *after, int ncols, int 
 // Arot (device, nullable, ld ldy): receives Y^T G Y (theta on its diagonal, the entries
 // left below the threshold off it); with mp > 0 its leading block is read as the
 // previous call's rotated matrix instead of diag(theta).
+// This entry runs the FP64 cyclic Jacobi method.
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
                         cudaStream_t s, int mp = 0, int *stat = nullptr, double tol_abs = 0.0,
                         double *Arot = nullptr);
+// The same contract by `method` (TPS_RR_MIXED: FP32 Jacobi + FP64 refinement, with the
+// FP64 Jacobi inside the same launch when the refinement does not converge;
+// TPS_RR_JACOBI64: FP64 Jacobi).  stat (nullable) needs 8 ints: [0..2] as above for the
+// FP64 Jacobi, [3] mixed calls, [4] FP32 eigensolves, [5] refinement iterations, [6] groups of
+// close eigenvalues rotated, [7] calls that fell back to the FP64 Jacobi.  refine_max:
+// refinement iterations before the fallback (<= 0: 12).
+void launch_rr_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
+                    cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot, int method,
+                    int refine_max = 0);
 // Cholesky G = R^T R of the b x b Gram matrix (ld b); writes Rinv (upper, ld b) and
 // keep[c] = 1 if column c has a pivot >= tol_rel * ref[c] (ref = squared column norms
 // before projection, device, may be null), else 0 (column dropped, Rinv column zero).

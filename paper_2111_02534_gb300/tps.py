@@ -35,6 +35,7 @@ ANY, X_EVEN, X_ODD = 0, 1, 2
 F64 = 0
 F32 = 1
 F64_TC = 2
+RR_MIXED, RR_JACOBI64 = 0, 1   # Rayleigh-Ritz eigensolver (solver option rr_method)
 
 
 class SolverOpts(C.Structure):
@@ -44,7 +45,8 @@ class SolverOpts(C.Structure):
                 ("guard", C.c_int), ("smooth_start", C.c_int), ("prec_dtype", C.c_int),
                 ("h_dtype", C.c_int), ("switch_tol", C.c_double), ("refine_block", C.c_int),
                 ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int),
-                ("h64_dtype", C.c_int)]
+                ("h64_dtype", C.c_int), ("rr_method", C.c_int),
+                ("rr_refine_max", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -61,6 +63,9 @@ class Stats(C.Structure):
                 ("upd_launches", C.c_longlong), ("jacobi_calls", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("jacobi_rounds", C.c_int),
                 ("gs_orthogonalisations", C.c_int), ("gs_second_passes", C.c_int),
+                ("rr_mixed_calls", C.c_int), ("rr_fp32_solves", C.c_int),
+                ("rr_refine_iters", C.c_int), ("rr_groups_rotated", C.c_int),
+                ("rr_fallbacks", C.c_int),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

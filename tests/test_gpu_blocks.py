@@ -50,19 +50,35 @@ def test_block_update(ctx, nrows, p, q, beta):
     assert np.max(np.abs(host(Cd) - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("m,kind", [(1, "rand"), (7, "rand"), (32, "rand"), (64, "rand"),
-                                    (40, "cluster"), (33, "graded")])
+@pytest.mark.parametrize("m,kind", [(1, "rand"), (2, "rand"), (7, "rand"), (32, "rand"),
+                                    (64, "rand"), (40, "cluster"), (33, "graded"),
+                                    (64, "graded"), (16, "jdlike"), (24, "jdlike"),
+                                    (32, "jdlike"), (32, "degenerate"), (20, "equal"),
+                                    (9, "zero"), (48, "tiny_gaps")])
 def test_small_eigh(ctx, m, kind):
+    # the default eigensolver (FP32 Jacobi + FP64 refinement): random spectra, tight
+    # clusters, graded magnitudes, the spectra of Jacobi-Davidson projections (a few close
+    # low Ritz values under a wide spread), exactly repeated and all-equal eigenvalues
     rng = np.random.default_rng(m)
     if kind == "rand":
         A = rng.standard_normal((m, m))
         A = A + A.T
+    elif kind == "zero":
+        A = np.zeros((m, m))
     else:
         Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
         if kind == "cluster":
             d = np.repeat(np.array([-3.0, -1e-3, 0.0, 1e-12, 2.0]), m // 5 + 1)[:m] + 1e-14 * rng.standard_normal(m)
-        else:
+        elif kind == "graded":
             d = np.logspace(-12, 3, m) * np.where(np.arange(m) % 2, -1, 1)
+        elif kind == "jdlike":
+            d = np.concatenate([np.sort(rng.uniform(-0.02, 0.0, 8)), 10 ** rng.uniform(-1, 2.5, m - 8)])
+        elif kind == "degenerate":
+            d = np.concatenate([np.full(6, -0.01), np.full(4, -0.0099999), 10 ** rng.uniform(-1, 2.5, m - 10)])
+        elif kind == "equal":
+            d = np.full(m, 2.5)
+        else:  # eigenvalues 1e-9 apart around 1, and a wide spread
+            d = np.concatenate([1.0 + 1e-9 * np.arange(m // 2), 10 ** rng.uniform(-2, 2, m - m // 2)])
         A = (Q * d) @ Q.T
         A = 0.5 * (A + A.T)
     th = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -71,6 +87,7 @@ def test_small_eigh(ctx, m, kind):
     w, Yh = host(th), host(Y).T          # Y is column-major
     ref = np.linalg.eigvalsh(A)
     nrm = np.linalg.norm(A, 2)
+    nrm = max(nrm, 1e-300)
     assert np.all(np.diff(w) >= 0)
     assert np.max(np.abs(w - ref)) <= 1e-14 * nrm * m
     assert np.max(np.abs(Yh.T @ Yh - np.eye(m))) <= 1e-13 * m

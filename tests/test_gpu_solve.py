@@ -277,3 +277,35 @@ def test_new_potential_on_a_used_context_matches_a_fresh_context():
     assert np.max(np.abs(lam_c - ref) / np.abs(ref)) <= 1e-10
     ctx.close()
     fresh.close()
+
+
+@pytest.mark.parametrize("rr_method,refine_max", [(0, 0), (1, 0), (0, 1)])
+def test_rayleigh_ritz_methods_agree_full_size(rr_method, refine_max):
+    # the Rayleigh-Ritz eigensolver by FP32 Jacobi + FP64 refinement (default), by FP64
+    # cyclic Jacobi, and with the refinement cut to one iteration so that most solves fall
+    # back to the FP64 Jacobi inside the same launch: the same eigenpairs on the 1d_n512
+    # workload, every pair certified by the oracle's residual
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
+    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, rr_method=rr_method,
+                        rr_refine_max=refine_max)
+    ref = np.array(gold["evals"])
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, gold["v0"], w.sigma)
+    res = _check_vectors(P, lam, X, parity_sign=1.0)
+    weyl, kt = certify(lam, res, ref)
+    assert np.all(kt <= 1e-12 * np.abs(lam))
+    if rr_method == tps.RR_JACOBI64:
+        assert st.rr_mixed_calls == 0 and st.jacobi_calls == st.outer_iters
+    else:
+        assert st.rr_mixed_calls == st.outer_iters and st.rr_fp32_solves >= st.rr_mixed_calls
+        if refine_max == 1:
+            assert st.rr_fallbacks > 0 and st.jacobi_calls == st.rr_fallbacks
+        else:
+            assert st.rr_fallbacks == 0 and st.jacobi_calls == 0
+            assert st.rr_refine_iters >= st.rr_mixed_calls
+    ctx.close()

@@ -4,6 +4,7 @@
 // elementwise helpers (the small eigensolver is in rr_eigh.cu).  Everything stays on the device; the host only
 // reads a few scalars per outer iteration to steer the loop.
 #include <cstring>
+#include <utility>
 
 #include "tps_internal.h"
 
@@ -13,59 +14,99 @@ namespace {
 constexpr int GT = 256;  // threads of the Gram / update kernels
 
 // -------------------------------- Gram ---------------------------------------
-// G_s = A_s^T B_s in one launch.  CTA (c, s, pb) sums the 4x4 block pb over the rows of
-// chunk c into partial[s][pb][c][16]; the last CTA of a block to finish (ticket counter,
+// G_s = A_s^T B_s in one launch.  CTA (c, s, pb) sums the BP x BQ block pb over the rows of
+// chunk c into partial[s][pb][c][BP BQ]; the last CTA of a block to finish (ticket counter,
 // after a memory fence) adds the chunks in chunk order -- the same order every call, so
-// the result is deterministic -- writes the block into G and re-arms the counter.
+// the result is deterministic -- writes the block into G and re-arms the counter.  The
+// register tile fits the shape (16 x 1, 8 x 2, 4 x 4 and smaller), so narrow products do
+// not pay for FMAs on padding; trans = 1 stores the transposed block (the launcher swaps
+// the operands when p < q).
+//
+// Warp reduction of V = BP BQ values by recursive halving: at offset o each lane keeps
+// half of its values and adds the other half of its partner's, so a lane spends V - 1 +
+// (5 - log2 V) FP64 adds instead of 5 V -- FP64 instructions are the scarce resource on
+// GB300.  Afterwards lane l holds the sum of value index sum_k bit(l, 4-k) V / 2^(k+1).
+template <int V>
+__device__ __forceinline__ void warp_halving_sum(double (&v)[V]) {
+  const int lane = threadIdx.x & 31;
+  int n = V;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (n > 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < V / 2; ++i) {
+        if (i < n / 2) {
+          const double send = up ? v[i] : v[i + n / 2];
+          const double keep = up ? v[i + n / 2] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      n >>= 1;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ int halving_index(int lane) {
+  int idx = 0, w = V / 2;
+#pragma unroll
+  for (int o = 16; o > 0 && w > 0; o >>= 1, w >>= 1) idx += (lane & o) ? w : 0;
+  return idx;
+}
+
+template <int V>
+__device__ __forceinline__ bool halving_writer(int lane) {  // one lane per value index
+  int used = 0;
+#pragma unroll
+  for (int w = V / 2; w > 0; w >>= 1) ++used;  // offsets 16 .. 2^(5-used) carry the index
+  return (lane & ((1 << (5 - used)) - 1)) == 0;
+}
+
+template <int BP, int BQ>
 __global__ void __launch_bounds__(GT)
 k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
        const double *__restrict__ B, long long ldb, long long bsb, int q, long long nrows,
        int nchunk, double *__restrict__ partial, unsigned *__restrict__ count,
-       double *__restrict__ G, int ldg, long long bsg, const int *__restrict__ need) {
+       double *__restrict__ G, int ldg, long long bsg, int trans, const int *__restrict__ need) {
+  constexpr int V = BP * BQ;
   if (need && *need == 0) return;  // conditional product (decided on the device)
   const int c = blockIdx.x, s = blockIdx.y, pb = blockIdx.z;
-  const int qb = (q + 3) / 4;
-  const int npb = ((p + 3) / 4) * qb;
-  const int i0 = (pb / qb) * 4, j0 = (pb % qb) * 4;
+  const int qb = (q + BQ - 1) / BQ;
+  const int npb = ((p + BP - 1) / BP) * qb;
+  const int i0 = (pb / qb) * BP, j0 = (pb % qb) * BQ;
   const double *As = A + s * bsa;
   const double *Bs = B + s * bsb;
   const long long rows_per = (nrows + nchunk - 1) / nchunk;
   const long long r0 = (long long)c * rows_per;
   const long long r1 = r0 + rows_per < nrows ? r0 + rows_per : nrows;
-  double acc[4][4];
+  double acc[V];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k = 0; k < V; ++k) acc[k] = 0.0;
   for (long long r = r0 + threadIdx.x; r < r1; r += GT) {
-    double a[4], b[4];
+    double a[BP], b[BQ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = (i0 + i < p) ? As[(long long)(i0 + i) * lda + r] : 0.0;
+    for (int i = 0; i < BP; ++i) a[i] = (i0 + i < p) ? As[(long long)(i0 + i) * lda + r] : 0.0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = (j0 + j < q) ? Bs[(long long)(j0 + j) * ldb + r] : 0.0;
+    for (int j = 0; j < BQ; ++j) b[j] = (j0 + j < q) ? Bs[(long long)(j0 + j) * ldb + r] : 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < BP; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      for (int j = 0; j < BQ; ++j) acc[i * BQ + j] = fma(a[i], b[j], acc[i * BQ + j]);
   }
-  __shared__ double red[GT / 32][16];
+  warp_halving_sum<V>(acc);
+  __shared__ double red[GT / 32][V];
   __shared__ unsigned ticket;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double v = acc[i][j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][i * 4 + j] = v;
-    }
+  if (halving_writer<V>(lane)) red[warp][halving_index<V>(lane)] = acc[0];
   __syncthreads();
   const long long blk = (long long)s * npb + pb;
-  if (threadIdx.x < 16) {
+  if (threadIdx.x < V) {
     double v = 0.0;
     for (int w = 0; w < GT / 32; ++w) v += red[w][threadIdx.x];
-    partial[(blk * nchunk + c) * 16 + threadIdx.x] = v;
+    partial[(blk * nchunk + c) * V + threadIdx.x] = v;
     __threadfence();  // this chunk's sums are visible before the ticket is taken
   }
   __syncthreads();
@@ -73,21 +114,26 @@ k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
   __syncthreads();
   if (ticket != (unsigned)(nchunk - 1)) return;
   // last CTA of the block: every other chunk's partial sums are in memory
-  if (threadIdx.x < 16) {
+  if (threadIdx.x < V) {
     __threadfence();
-    const double *src = partial + blk * nchunk * 16 + threadIdx.x;
+    const double *src = partial + blk * nchunk * V + threadIdx.x;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     int cc = 0;
     for (; cc + 4 <= nchunk; cc += 4) {
-      v0 += __ldcg(src + (long long)(cc + 0) * 16);
-      v1 += __ldcg(src + (long long)(cc + 1) * 16);
-      v2 += __ldcg(src + (long long)(cc + 2) * 16);
-      v3 += __ldcg(src + (long long)(cc + 3) * 16);
+      v0 += __ldcg(src + (long long)(cc + 0) * V);
+      v1 += __ldcg(src + (long long)(cc + 1) * V);
+      v2 += __ldcg(src + (long long)(cc + 2) * V);
+      v3 += __ldcg(src + (long long)(cc + 3) * V);
     }
-    for (; cc < nchunk; ++cc) v0 += __ldcg(src + (long long)cc * 16);
+    for (; cc < nchunk; ++cc) v0 += __ldcg(src + (long long)cc * V);
     const double v = (v0 + v1) + (v2 + v3);
-    const int i = i0 + threadIdx.x / 4, j = j0 + threadIdx.x % 4;
-    if (i < p && j < q) G[s * bsg + (long long)j * ldg + i] = v;
+    const int i = i0 + threadIdx.x / BQ, j = j0 + threadIdx.x % BQ;
+    if (i < p && j < q) {
+      if (trans)
+        G[s * bsg + (long long)i * ldg + j] = v;
+      else
+        G[s * bsg + (long long)j * ldg + i] = v;
+    }
   }
   if (threadIdx.x == 0) count[blk] = 0u;  // re-armed for the next call on this stream
 }
@@ -102,7 +148,9 @@ int gram_chunks(long long nrows, int batch, int npb) {
 }
 
 // ------------------------------- update --------------------------------------
-// C_s[:, j0:j0+8] = beta*C_s + alpha * A_s Y_s[:, j0:j0+8]
+// C_s[:, j0:j0+BQ] = beta*C_s + alpha * A_s Y_s[:, j0:j0+BQ]; BQ fits q (1, 2, 4 or 8), so
+// narrow updates do not pay for FMAs on padding columns.
+template <int BQ>
 __global__ void __launch_bounds__(GT)
 k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
          const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha, double beta,
@@ -110,27 +158,27 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
          const int *__restrict__ need) {
   if (need && *need == 0) return;  // conditional product (decided on the device)
   const int s = blockIdx.y;
-  const int j0 = blockIdx.z * 8;
-  __shared__ double Ys[64][8];
-  for (int e = threadIdx.x; e < p * 8; e += GT) {
-    const int i = e / 8, j = e % 8;
+  const int j0 = blockIdx.z * BQ;
+  __shared__ double Ys[64][BQ];
+  for (int e = threadIdx.x; e < p * BQ; e += GT) {
+    const int i = e / BQ, j = e % BQ;
     Ys[i][j] = (j0 + j < q) ? alpha * Y[s * bsy + (long long)(j0 + j) * ldy + i] : 0.0;
   }
   __syncthreads();
   const long long r = blockIdx.x * (long long)GT + threadIdx.x;
   if (r >= nrows) return;
   const double *As = A + s * bsa;
-  double acc[8];
+  double acc[BQ];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+  for (int j = 0; j < BQ; ++j) acc[j] = 0.0;
   for (int i = 0; i < p; ++i) {
     const double a = As[(long long)i * lda + r];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);
+    for (int j = 0; j < BQ; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);
   }
   double *Cs = C + s * bsc;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < BQ; ++j) {
     if (j0 + j >= q) break;
     double *dst = Cs + (long long)(j0 + j) * ldc + r;
     *dst = (beta == 0.0) ? acc[j] : fma(beta, *dst, acc[j]);
@@ -411,14 +459,42 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
                  long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
                  long long bsg, int batch, GramScratch &scr, cudaStream_t s, const int *need) {
   if (p <= 0 || q <= 0 || batch <= 0) return;
-  const int npb = ((p + 3) / 4) * ((q + 3) / 4);
+  int trans = 0;
+  if (p < q) {  // G^T = B^T A: the wider operand along the register tile's long side
+    std::swap(A, B);
+    std::swap(lda, ldb);
+    std::swap(bsa, bsb);
+    std::swap(p, q);
+    trans = 1;
+  }
+  auto pow2 = [](int x, int lo, int hi) {
+    int v = lo;
+    while (v < x && v < hi) v <<= 1;
+    return v;
+  };
+  const int BQ = q == 1 ? 1 : (q == 2 ? 2 : 4);
+  const int BP = BQ == 1 ? pow2(p, 1, 16) : (BQ == 2 ? pow2(p, 2, 8) : 4);
+  const int npb = ((p + BP - 1) / BP) * ((q + BQ - 1) / BQ);
+  const int V = BP * BQ;
   int nchunk = gram_chunks(nrows, batch, npb);
-  const long long cap = scr.capacity / ((long long)batch * npb * 16);
+  // partial sums fit the scratch; sized with 16 values per block at least, so that
+  // batch * npb also stays below the ticket count (one per 16 doubles of capacity)
+  const long long cap = scr.capacity / ((long long)batch * npb * (V > 16 ? V : 16));
   if (nchunk > cap) nchunk = (int)(cap > 0 ? cap : 1);
   dim3 grid(nchunk, batch, npb);
   count_launch();
-  k_gram<<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial,
-                             scr.count, G, ldg, bsg, need);
+#define TPS_GRAM(bp, bq)                                                                        \
+  k_gram<bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial, \
+                                     scr.count, G, ldg, bsg, trans, need)
+  if (BQ == 4)
+    TPS_GRAM(4, 4);
+  else if (BQ == 2)
+    BP == 2 ? TPS_GRAM(2, 2) : (BP == 4 ? TPS_GRAM(4, 2) : TPS_GRAM(8, 2));
+  else
+    BP == 1 ? TPS_GRAM(1, 1)
+            : (BP == 2 ? TPS_GRAM(2, 1)
+                       : (BP == 4 ? TPS_GRAM(4, 1) : (BP == 8 ? TPS_GRAM(8, 1) : TPS_GRAM(16, 1))));
+#undef TPS_GRAM
 }
 
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
@@ -433,13 +509,22 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     }
     return;
   }
+  const int BQ = q >= 8 ? 8 : (q >= 4 ? 4 : (q >= 2 ? 2 : 1));
   // p is processed in slabs of 64 rows of Y; the first slab applies beta
   for (int i0 = 0; i0 < p; i0 += 64) {
     const int pp = p - i0 < 64 ? p - i0 : 64;
-    dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + 7) / 8);
+    dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + BQ - 1) / BQ);
+    const double bt = i0 == 0 ? beta : 1.0;
+    const double *Ai = A + (long long)i0 * lda;
     count_launch();
-    k_update<<<grid, GT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha,
-                                 i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows, need);
+    if (BQ == 8)
+      k_update<8><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
+    else if (BQ == 4)
+      k_update<4><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
+    else if (BQ == 2)
+      k_update<2><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
+    else
+      k_update<1><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
   }
 }
 

@@ -20,7 +20,12 @@ def ctx():
 
 
 @pytest.mark.parametrize("nrows,p,q", [(131584, 24, 8), (1000003, 5, 1), (4097, 64, 64),
-                                       (257, 1, 1), (0, 3, 2)])
+                                       (257, 1, 1), (0, 3, 2),
+                                       # every register tile: 16x1, 8x1, 4x1, 2x1, 8x2, 4x2,
+                                       # 2x2, operands swapped (p < q), ragged 4x4
+                                       (50001, 13, 1), (30011, 7, 1), (20011, 3, 1),
+                                       (9999, 2, 1), (70001, 7, 2), (4099, 3, 2), (777, 2, 2),
+                                       (65537, 1, 5), (12345, 2, 11), (131584, 10, 8)])
 def test_gram(ctx, nrows, p, q):
     A = random_block(p, nrows, 1)
     B = random_block(q, nrows, 2)
@@ -33,7 +38,10 @@ def test_gram(ctx, nrows, p, q):
 
 
 @pytest.mark.parametrize("nrows,p,q,beta", [(131584, 24, 8, 0.0), (100003, 70, 3, 1.0),
-                                            (513, 1, 17, -0.5), (1000, 0, 4, 2.0)])
+                                            (513, 1, 17, -0.5), (1000, 0, 4, 2.0),
+                                            # column tiles 1, 2, 4 (ragged), 8, 8 + 1
+                                            (40001, 11, 1, 1.0), (3001, 5, 2, 0.0),
+                                            (131584, 32, 5, -1.0), (20003, 9, 9, 0.5)])
 def test_block_update(ctx, nrows, p, q, beta):
     A = random_block(max(p, 1), nrows, 3)[:p]
     Y = np.random.default_rng(4).standard_normal((p, q))

@@ -56,11 +56,15 @@ typedef enum tps_status {
 
 enum { TPS_GAUSS = 0, TPS_LORENTZ3 = 1 };          /* f_G = exp(-xi^2), f_L = (1+xi^2)^-3 */
 enum { TPS_ANY = 0, TPS_X_EVEN = 1, TPS_X_ODD = 2 }; /* heavy-exchange sector (Sec. 5.1) */
-enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2 };  /* arithmetic of apply calls (data stay FP64) */
+enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2, TPS_TF32_TC = 3 };  /* arithmetic of apply calls
+                                                                       (data stay FP64) */
 /* TPS_F64_TC: FP64-accurate mode products emulated on the BF16 tensor cores by error-free
  * splitting into six-bit digit slices per operand row (9 for the wave function, 10 for the
  * mode matrices; Ozaki scheme), exact FP32 accumulation per digit level, FP64
- * recombination; 1D H-apply only. */
+ * recombination; 1D H-apply only.
+ * TPS_TF32_TC: the preconditioner's four mode products on the tensor cores with TF32 inputs
+ * (10 explicit mantissa bits) and FP32 accumulation, ~2.5e-3 relative to the exact
+ * (T - sigma)^-1 r; 1D preconditioner only. */
 /* Rayleigh-Ritz eigensolver (Sec. 4.1, the projected problem G y = theta y, m <= 64):
  * TPS_RR_MIXED: FP32 eigenvectors (tridiagonalisation, bisection, inverse iteration), then FP64
  *   iterative refinement of the eigenvectors
@@ -176,8 +180,9 @@ typedef struct tps_solver_opts {
                          absent from the early search space is not skipped (default 2) */
   int smooth_start;   /* applications of the kinetic preconditioner (shift -1e-3 ||H||_est) to
                          the random part of the start block, a low-pass filter (default 2) */
-  int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_F32 (default)
-                         or TPS_F64 */
+  int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_TF32_TC
+                         (default; tensor cores, 1D -- 2D solves use TPS_F32), TPS_F32 or
+                         TPS_F64 */
   int h_dtype;        /* TPS_F64 (default): FP64 H products throughout (on the tensor cores,
                          see h64_dtype); TPS_F32: mixed precision -- a first phase runs the H
                          mode products in FP32 until every pair's residual is below

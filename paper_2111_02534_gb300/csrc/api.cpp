@@ -272,6 +272,8 @@ void free_operator(DevOperator &op) {
     op.lam_h[k].clear();
   }
   free_tc_operator(op.tc);
+  free_tf_operator(op.tf);
+  op.tf = nullptr;
   op.tc = nullptr;
   cudaFree(op.V);
   cudaFree(op.Vf);
@@ -685,8 +687,8 @@ int tps_device_status(tps_ctx *ctx) {
   if (!ctx) return TPS_ERR_INVALID_ARG;
   TPS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   TPS_CUDA_TRY(ctx, cudaDeviceSynchronize());
-  int flag = tc_operator_status(ctx->full);
-  for (int p = 0; p < 3; ++p) flag |= tc_operator_status(ctx->sect[p]);
+  int flag = tc_operator_status(ctx->full) | tf_operator_status(ctx->full);
+  for (int p = 0; p < 3; ++p) flag |= tc_operator_status(ctx->sect[p]) | tf_operator_status(ctx->sect[p]);
   if (flag < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
   if (flag) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   return TPS_OK;
@@ -696,9 +698,15 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
                    int dtype, cudaStream_t stream) {
   int st = check_ready(ctx);
   if (st) return st;
-  if ((dtype != TPS_F64 && dtype != TPS_F32) || nvec < 0 || (nvec > 0 && (!r_dev || !out_dev)) ||
-      !std::isfinite(theta))
+  if ((dtype != TPS_F64 && dtype != TPS_F32 && dtype != TPS_TF32_TC) || nvec < 0 ||
+      (nvec > 0 && (!r_dev || !out_dev)) || !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_prec arguments");
+  if (dtype == TPS_TF32_TC) {
+    if (ctx->full.nmodes != 2)
+      return set_error(ctx, TPS_ERR_INVALID_ARG, "the TF32 tensor-core preconditioner is 1D only");
+    st = ensure_tf_operator(ctx->full);
+    if (st) return set_error(ctx, st, "building the TF32 preconditioner operator failed");
+  }
   const char *a = (const char *)r_dev, *b = (const char *)out_dev;
   const size_t bytes = (size_t)nvec * ctx->full.N * sizeof(double);
   if (nvec > 0 && a < b + bytes && b < a + bytes)
@@ -712,10 +720,14 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
     const int nv = (int)std::min<long long>(cap, nvec - v0);
     const double *rin = (const double *)r_dev + (long long)v0 * ctx->full.N;
     double *o = (double *)out_dev + (long long)v0 * ctx->full.N;
-    if (dtype == TPS_F32)
+    if (dtype == TPS_TF32_TC) {
+      st = launch_apply_prec_tf32(ctx->full, rin, o, nv, theta, ctx->ws, stream);
+      if (st) return set_error(ctx, st, "TF32 preconditioner launch failed");
+    } else if (dtype == TPS_F32) {
       launch_apply_prec_f32(ctx->full, rin, o, nv, theta, ctx->ws, stream);
-    else
+    } else {
       launch_apply_prec(ctx->full, rin, o, nv, theta, ctx->ws, stream);
+    }
   }
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;

@@ -244,7 +244,9 @@ void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double sh
     b = t.get();
     cudaEventRecord(a, c.s);
   }
-  if (c.w.prec_dtype == TPS_F32)
+  if (c.w.prec_dtype == TPS_TF32_TC)
+    launch_apply_prec_tf32(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
+  else if (c.w.prec_dtype == TPS_F32)
     launch_apply_prec_f32(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
   else
     launch_apply_prec(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
@@ -558,7 +560,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
     ~TimingScope() { tl_timing = nullptr; }
   } timing_scope(&w.tm);
-  w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64 : TPS_F32;
+  // the TF32 tensor-core preconditioner exists for the 1D operator; 2D solves use FP32
+  w.prec_dtype = opts.prec_dtype == TPS_F64
+                     ? TPS_F64
+                     : ((opts.prec_dtype == TPS_TF32_TC && op.nmodes == 2) ? TPS_TF32_TC : TPS_F32);
+  if (w.prec_dtype == TPS_TF32_TC) {
+    const int st_tf = ensure_tf_operator(op);  // allocation errors here, not mid-solve
+    if (st_tf) return set_error(ctx, st_tf, "building the TF32 preconditioner operator failed");
+  }
   // the tensor-core FP64 H-apply exists for the 1D operator; 2D solves use the FMA pipe
   w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && op.nmodes == 2) ? TPS_F64_TC : TPS_F64;
   if (w.h64_dtype == TPS_F64_TC)
@@ -898,7 +907,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->seed = 12345;
   o->guard = 2;
   o->smooth_start = 2;
-  o->prec_dtype = TPS_F32;
+  o->prec_dtype = TPS_TF32_TC;  // 1D; 2D solves use TPS_F32
   o->h_dtype = TPS_F64;
   o->switch_tol = 1e-6;
   o->refine_block = 0;

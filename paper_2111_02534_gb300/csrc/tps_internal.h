@@ -50,6 +50,8 @@ struct DevOperator {
   bool owns = true;
   // tensor-core (BF16 digit slice) form of the mode matrices, built on first use
   mutable struct TcOperator *tc = nullptr;
+  // padded FP32 eigenbases for the TF32 tensor-core preconditioner, built on first use
+  mutable struct TfOperator *tf = nullptr;
 };
 
 // Workspace for one operator application (preconditioner intermediates).
@@ -80,6 +82,16 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
                               const double *theta_dev, double theta, cudaStream_t s);
 cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s);
 void free_tc_operator(struct TcOperator *t);
+// TF32 tensor-core preconditioner (1D): out[v] = (T - sigma)^-1 r[v] with the four mode
+// products in TF32 (FP64 r and out; the FP32 intermediates use the workspace, which must
+// hold tf_prec_workspace_floats / 2 doubles).  ensure_tf_operator builds op.tf (padded
+// eigenbases, synchronous); the launcher returns TPS_ERR_INVALID_ARG without it.
+void free_tf_operator(struct TfOperator *t);
+int ensure_tf_operator(const DevOperator &op);
+long long tf_prec_workspace_floats(const DevOperator &op, int nvec);
+int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, int nvec,
+                           double sigma, ApplyWorkspace &ws, cudaStream_t s);
+int tf_operator_status(const DevOperator &op);
 // Synchronously reads and clears the timed-out-wait flag of op's tensor-core kernels.
 int tc_operator_status(const DevOperator &op);
 

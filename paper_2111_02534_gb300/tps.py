@@ -35,6 +35,7 @@ ANY, X_EVEN, X_ODD = 0, 1, 2
 F64 = 0
 F32 = 1
 F64_TC = 2
+TF32_TC = 3     # preconditioner on the tensor cores in TF32 (1D)
 RR_MIXED, RR_JACOBI64 = 0, 1   # Rayleigh-Ritz eigensolver (solver option rr_method)
 
 

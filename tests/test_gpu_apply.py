@@ -244,3 +244,67 @@ def test_apply_h_fp32(dim, n):
     tol = 8 * np.sqrt(max(n)) * np.finfo(np.float32).eps
     assert err.max() <= tol, (err.max(), tol)
     assert err.max() > 1e-13          # it really ran in FP32
+
+
+# The TF32 tensor-core preconditioner (TPS_TF32_TC): four mode products with inputs
+# truncated to 10 explicit mantissa bits (relative error <= 2^-10 per operand) and FP32
+# accumulation; each product's result is then off by at most ~2 * 2^-10 relative in norm
+# for the orthogonal eigenbases, four of them 8e-3; an emulation of the truncation gives
+# 2.5e-3.  The bar is 1e-2 relative norm-wise.
+TF32_TOL = 1e-2
+
+
+@pytest.mark.parametrize("n,nvec,theta", [((64, 64), 3, -0.5), ((100, 70), 2, -1.3),
+                                          ((12, 8), 4, -0.05), ((130, 200), 1, -2.0),
+                                          ((66, 34), 9, -0.3)])
+def test_apply_prec_1d_tf32(n, nvec, theta):
+    # padded rows (70, 130, 34, 66 are not multiples of 4 floats), K below one 32-wide
+    # tile (n = 8, 12), M and N ragged against the 128 x 64 tiles
+    require_gpu()
+    tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
+    L = (20.0, 15.0)
+    P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+    ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    r = random_block(nvec, P.N, seed=nvec + 11)
+    out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, theta, dtype=tps.TF32_TC)
+    ctx.device_status()
+    got = host(out)
+    ref = apply_sylvester(P, r, theta)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TF32_TOL, err.max()
+    # the same call twice gives the same bits (a fixed operator for GMRES)
+    out2 = torch.empty_like(out)
+    ctx.apply_prec(dev(r), out2, theta, dtype=tps.TF32_TC)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    ctx.close()
+
+
+def test_apply_prec_1d_tf32_full_size():
+    require_gpu()
+    tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
+    w = WORKLOADS["1d_n512"]
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, 0.05, w.sigma)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, 0.05, w.sigma)
+    r = random_block(8, P.N, seed=5)
+    out = torch.empty(8, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, -1e-3, dtype=tps.TF32_TC)
+    ctx.device_status()
+    got = host(out)
+    ref = apply_sylvester(P, r[:2], -1e-3)
+    err = np.linalg.norm(got[:2] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TF32_TOL, err.max()
+    ctx.close()
+
+
+def test_apply_prec_tf32_rejects_2d():
+    require_gpu()
+    tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
+    ctx = make_ctx_2d(20.0, 1.0, (8, 8, 8, 8), (5.0,) * 4, 1.0, 1.0)
+    N = ctx.info()[0]
+    x = torch.ones(1, N, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(tps.TpsError):
+        ctx.apply_prec(x, y, -0.5, dtype=tps.TF32_TC)
+    ctx.close()

@@ -309,3 +309,25 @@ def test_rayleigh_ritz_methods_agree_full_size(rr_method, refine_max):
             assert st.rr_fallbacks == 0 and st.jacobi_calls == 0
             assert st.rr_refine_iters >= st.rr_mixed_calls
     ctx.close()
+
+
+def test_tf32_preconditioner_solve_full_size():
+    # the solver with the TF32 tensor-core preconditioner: the same certified eigenpairs on
+    # the 1d_n512 workload, with about as many H applications as the FP32 preconditioner
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
+    lam32, _, st32 = _solve(ctx, w.k, tps.X_EVEN, w.block, prec_dtype=tps.F32)
+    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, prec_dtype=tps.TF32_TC)
+    ctx.device_status()
+    ref = np.array(gold["evals"])
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, gold["v0"], w.sigma)
+    res = _check_vectors(P, lam, X, parity_sign=1.0)
+    weyl, kt = certify(lam, res, ref)
+    assert np.all(kt <= 1e-12 * np.abs(lam))
+    assert st.h_applies <= 1.25 * st32.h_applies, (st.h_applies, st32.h_applies)
+    ctx.close()

@@ -198,6 +198,10 @@ typedef struct tps_solver_opts {
   int rr_method;      /* Rayleigh-Ritz eigensolver: TPS_RR_MIXED (default) or TPS_RR_JACOBI64 */
   int rr_refine_max;  /* TPS_RR_MIXED: FP64 refinement iterations before the FP64 Jacobi
                          takes over (0: 12) */
+  int correction_dtype; /* arithmetic of the Gram and update products inside the correction
+                         solve (projectors, GMRES Arnoldi), which is solved to inner_tol and
+                         whose result is orthonormalised in FP64 before it enters the basis:
+                         TPS_F32 (default) or TPS_F64 */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -219,7 +223,8 @@ typedef struct tps_stats {
   double h32_ms;      /* with opts.timing: device time of the FP32 H applications */
   double h32_flops;   /* algorithmic flops of the FP32 H applications */
   long long h32_launches;
-  /* Gram products A^T B and block updates C = bC + a A Y (a6, a7), with opts.timing.  To
+  /* FP64 Gram products A^T B and block updates C = bC + a A Y (a6, a7), with opts.timing
+   * (the correction solve's FP32-arithmetic products are not included).  To
    * keep the timing overhead low every 4th launch is timed: *_ms, *_flops and *_bytes
    * cover the timed launches (so flops / ms is their rate), *_launches counts all. */
   double gram_ms;     /* device time of the timed Gram launches */

@@ -20,14 +20,15 @@ constexpr int GT = 256;  // threads of the Gram / update kernels
 // the result is deterministic -- writes the block into G and re-arms the counter.  The
 // register tile fits the shape (16 x 1, 8 x 2, 4 x 4 and smaller), so narrow products do
 // not pay for FMAs on padding; trans = 1 stores the transposed block (the launcher swaps
-// the operands when p < q).
+// the operands when p < q).  T = float: FP32 products and partial sums on the FP64 data
+// (the low-precision variant; the chunk sums are added in FP64).
 //
 // Warp reduction of V = BP BQ values by recursive halving: at offset o each lane keeps
 // half of its values and adds the other half of its partner's, so a lane spends V - 1 +
 // (5 - log2 V) FP64 adds instead of 5 V -- FP64 instructions are the scarce resource on
 // GB300.  Afterwards lane l holds the sum of value index sum_k bit(l, 4-k) V / 2^(k+1).
-template <int V>
-__device__ __forceinline__ void warp_halving_sum(double (&v)[V]) {
+template <int V, typename T>
+__device__ __forceinline__ void warp_halving_sum(T (&v)[V]) {
   const int lane = threadIdx.x & 31;
   int n = V;
 #pragma unroll
@@ -37,8 +38,8 @@ __device__ __forceinline__ void warp_halving_sum(double (&v)[V]) {
 #pragma unroll
       for (int i = 0; i < V / 2; ++i) {
         if (i < n / 2) {
-          const double send = up ? v[i] : v[i + n / 2];
-          const double keep = up ? v[i + n / 2] : v[i];
+          const T send = up ? v[i] : v[i + n / 2];
+          const T keep = up ? v[i + n / 2] : v[i];
           v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
       }
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool halving_writer(int lane) {  // one lane per valu
   return (lane & ((1 << (5 - used)) - 1)) == 0;
 }
 
-template <int BP, int BQ>
+template <typename T, int BP, int BQ>
 __global__ void __launch_bounds__(GT)
 k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
        const double *__restrict__ B, long long ldb, long long bsb, int q, long long nrows,
@@ -82,31 +83,31 @@ k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
   const long long rows_per = (nrows + nchunk - 1) / nchunk;
   const long long r0 = (long long)c * rows_per;
   const long long r1 = r0 + rows_per < nrows ? r0 + rows_per : nrows;
-  double acc[V];
+  T acc[V];
 #pragma unroll
-  for (int k = 0; k < V; ++k) acc[k] = 0.0;
+  for (int k = 0; k < V; ++k) acc[k] = T(0);
   for (long long r = r0 + threadIdx.x; r < r1; r += GT) {
-    double a[BP], b[BQ];
+    T a[BP], b[BQ];
 #pragma unroll
-    for (int i = 0; i < BP; ++i) a[i] = (i0 + i < p) ? As[(long long)(i0 + i) * lda + r] : 0.0;
+    for (int i = 0; i < BP; ++i) a[i] = (i0 + i < p) ? (T)As[(long long)(i0 + i) * lda + r] : T(0);
 #pragma unroll
-    for (int j = 0; j < BQ; ++j) b[j] = (j0 + j < q) ? Bs[(long long)(j0 + j) * ldb + r] : 0.0;
+    for (int j = 0; j < BQ; ++j) b[j] = (j0 + j < q) ? (T)Bs[(long long)(j0 + j) * ldb + r] : T(0);
 #pragma unroll
     for (int i = 0; i < BP; ++i)
 #pragma unroll
       for (int j = 0; j < BQ; ++j) acc[i * BQ + j] = fma(a[i], b[j], acc[i * BQ + j]);
   }
   warp_halving_sum<V>(acc);
-  __shared__ double red[GT / 32][V];
+  __shared__ T red[GT / 32][V];
   __shared__ unsigned ticket;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (halving_writer<V>(lane)) red[warp][halving_index<V>(lane)] = acc[0];
   __syncthreads();
   const long long blk = (long long)s * npb + pb;
   if (threadIdx.x < V) {
-    double v = 0.0;
+    T v = T(0);
     for (int w = 0; w < GT / 32; ++w) v += red[w][threadIdx.x];
-    partial[(blk * nchunk + c) * V + threadIdx.x] = v;
+    partial[(blk * nchunk + c) * V + threadIdx.x] = (double)v;
     __threadfence();  // this chunk's sums are visible before the ticket is taken
   }
   __syncthreads();
@@ -149,8 +150,9 @@ int gram_chunks(long long nrows, int batch, int npb) {
 
 // ------------------------------- update --------------------------------------
 // C_s[:, j0:j0+BQ] = beta*C_s + alpha * A_s Y_s[:, j0:j0+BQ]; BQ fits q (1, 2, 4 or 8), so
-// narrow updates do not pay for FMAs on padding columns.
-template <int BQ>
+// narrow updates do not pay for FMAs on padding columns.  T = float: FP32 products and
+// sums on the FP64 data (the low-precision variant), the beta combination in FP64.
+template <typename T, int BQ>
 __global__ void __launch_bounds__(GT)
 k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
          const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha, double beta,
@@ -159,20 +161,20 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
   if (need && *need == 0) return;  // conditional product (decided on the device)
   const int s = blockIdx.y;
   const int j0 = blockIdx.z * BQ;
-  __shared__ double Ys[64][BQ];
+  __shared__ T Ys[64][BQ];
   for (int e = threadIdx.x; e < p * BQ; e += GT) {
     const int i = e / BQ, j = e % BQ;
-    Ys[i][j] = (j0 + j < q) ? alpha * Y[s * bsy + (long long)(j0 + j) * ldy + i] : 0.0;
+    Ys[i][j] = (j0 + j < q) ? (T)(alpha * Y[s * bsy + (long long)(j0 + j) * ldy + i]) : T(0);
   }
   __syncthreads();
   const long long r = blockIdx.x * (long long)GT + threadIdx.x;
   if (r >= nrows) return;
   const double *As = A + s * bsa;
-  double acc[BQ];
+  T acc[BQ];
 #pragma unroll
-  for (int j = 0; j < BQ; ++j) acc[j] = 0.0;
+  for (int j = 0; j < BQ; ++j) acc[j] = T(0);
   for (int i = 0; i < p; ++i) {
-    const double a = As[(long long)i * lda + r];
+    const T a = (T)As[(long long)i * lda + r];
 #pragma unroll
     for (int j = 0; j < BQ; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);
   }
@@ -181,7 +183,7 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
   for (int j = 0; j < BQ; ++j) {
     if (j0 + j >= q) break;
     double *dst = Cs + (long long)(j0 + j) * ldc + r;
-    *dst = (beta == 0.0) ? acc[j] : fma(beta, *dst, acc[j]);
+    *dst = (beta == 0.0) ? (double)acc[j] : fma(beta, *dst, (double)acc[j]);
   }
 }
 
@@ -457,7 +459,8 @@ long long gram_scratch_doubles(int p, int q, int batch) {
 
 void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
                  long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
-                 long long bsg, int batch, GramScratch &scr, cudaStream_t s, const int *need) {
+                 long long bsg, int batch, GramScratch &scr, cudaStream_t s, const int *need,
+                 bool low) {
   if (p <= 0 || q <= 0 || batch <= 0) return;
   int trans = 0;
   if (p < q) {  // G^T = B^T A: the wider operand along the register tile's long side
@@ -483,9 +486,13 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
   if (nchunk > cap) nchunk = (int)(cap > 0 ? cap : 1);
   dim3 grid(nchunk, batch, npb);
   count_launch();
-#define TPS_GRAM(bp, bq)                                                                        \
-  k_gram<bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, scr.partial, \
-                                     scr.count, G, ldg, bsg, trans, need)
+#define TPS_GRAM(bp, bq)                                                                      \
+  (low ? k_gram<float, bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk,  \
+                                                   scr.partial, scr.count, G, ldg, bsg, trans,     \
+                                                   need)                                           \
+       : k_gram<double, bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, \
+                                                    scr.partial, scr.count, G, ldg, bsg, trans,    \
+                                                    need))
   if (BQ == 4)
     TPS_GRAM(4, 4);
   else if (BQ == 2)
@@ -499,7 +506,8 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
 
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
-                   long long bsc, long long nrows, int batch, cudaStream_t s, const int *need) {
+                   long long bsc, long long nrows, int batch, cudaStream_t s, const int *need,
+                   bool low) {
   if (q <= 0 || batch <= 0 || nrows <= 0) return;
   if (p <= 0) {  // C = beta * C
     for (int b = 0; b < batch; ++b) {
@@ -517,14 +525,14 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     const double bt = i0 == 0 ? beta : 1.0;
     const double *Ai = A + (long long)i0 * lda;
     count_launch();
-    if (BQ == 8)
-      k_update<8><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
-    else if (BQ == 4)
-      k_update<4><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
-    else if (BQ == 2)
-      k_update<2><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
+#define TPS_UPD(T, bq)                                                                       \
+  k_update<T, bq><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, \
+                                      bsc, nrows, need)
+    if (low)
+      BQ == 8 ? TPS_UPD(float, 8) : (BQ == 4 ? TPS_UPD(float, 4) : (BQ == 2 ? TPS_UPD(float, 2) : TPS_UPD(float, 1)));
     else
-      k_update<1><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, bsc, nrows, need);
+      BQ == 8 ? TPS_UPD(double, 8) : (BQ == 4 ? TPS_UPD(double, 4) : (BQ == 2 ? TPS_UPD(double, 2) : TPS_UPD(double, 1)));
+#undef TPS_UPD
   }
 }
 

@@ -81,6 +81,7 @@ struct PhaseTiming {
 struct SolverWorkspace {
   PhaseTiming tm;
   int prec_dtype = TPS_F64;  // arithmetic of the preconditioner applications
+  bool corr_low = false;     // FP32-arithmetic Gram/update products in the correction solve
   int h64_dtype = TPS_F64;   // FP64 H-applies on the FMA pipe or the tensor cores
   long long N = 0;
   int mmax = 0, b = 0, kmax = 0, steps = 0;
@@ -134,12 +135,14 @@ void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
 thread_local PhaseTiming *tl_timing = nullptr;
 
 // launch_gram / launch_update with CUDA-event timing and algorithmic work counts
+// low: FP32-arithmetic products (the correction equation's); like conditional launches
+// (need, which may do nothing) they are neither timed nor counted in the FP64 Gram and
+// update statistics
 void tgram(const double *A, long long lda, long long bsa, int p, const double *B, long long ldb,
            long long bsb, int q, long long nrows, double *G, int ldg, long long bsg, int batch,
-           GramScratch &scr, cudaStream_t s, const int *need = nullptr) {
+           GramScratch &scr, cudaStream_t s, const int *need = nullptr, bool low = false) {
   PhaseTiming *t = tl_timing;
-  // conditional launches (need) may do nothing: neither timed nor counted
-  const bool live = !need && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  const bool live = !need && !low && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
   if (live) t->launches[3] += 1;
   const bool rec = live && (t->seen[3]++ % PhaseTiming::kSample) == 0;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -148,7 +151,7 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need);
+  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need, low);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[3].push_back({a, b});
@@ -160,9 +163,9 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
 void tupdate(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
              long long bsy, int q, double alpha, double beta, double *C, long long ldc,
              long long bsc, long long nrows, int batch, cudaStream_t s,
-             const int *need = nullptr) {
+             const int *need = nullptr, bool low = false) {
   PhaseTiming *t = tl_timing;
-  const bool live = !need && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
+  const bool live = !need && !low && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
   if (live) t->launches[4] += 1;
   const bool rec = live && (t->seen[4]++ % PhaseTiming::kSample) == 0;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -171,7 +174,8 @@ void tupdate(const double *A, long long lda, long long bsa, int p, const double 
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s, need);
+  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s, need,
+                low);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[4].push_back({a, b});
@@ -322,17 +326,21 @@ void kt_inverse(Ctx &c, const double *Qt, int nq, const double *KQt, int use_pre
   if (use_prec) {
     apply_prec_timed(c, Yin, Out, nsys, shift);
     if (nq > 0) {
-      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
+      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s, nullptr,
+            w.corr_low);
       // C2 = Minv * C, stored after C
       double *C2 = w.C + (long long)nq * nsys;
       launch_small_gemm(nq, nsys, nq, 1.0, w.Minv, nq, w.C, nq, 0.0, C2, nq, c.s);
-      tupdate(KQt, c.N, 0, nq, C2, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+      tupdate(KQt, c.N, 0, nq, C2, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s, nullptr,
+              w.corr_low);
     }
   } else {
     if (Out != Yin) launch_axpby_cols(nsys, c.N, 1.0, Yin, c.N, 0.0, Out, c.N, c.s);
     for (int pass = 0; pass < 2 && nq > 0; ++pass) {
-      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s);
-      tupdate(Qt, c.N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s);
+      tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s, nullptr,
+            w.corr_low);
+      tupdate(Qt, c.N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, Out, c.N, 0, c.N, 1, c.s, nullptr,
+              w.corr_low);
     }
   }
 }
@@ -457,7 +465,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                        nq - nq_cached, shift);
       *prec_applies += nq - nq_cached;
     }
-    tgram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s);
+    tgram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s, nullptr, w.corr_low);
     launch_spd_inverse(w.Mq, nq, w.Minv, s);
   }
   const int sst = steps;
@@ -480,8 +488,8 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     // right projector of Eq. jdcor, applied explicitly: rounding in the Q directions
     // would otherwise grow by 1/h_{j+1,j} per Arnoldi step
     if (nq > 0) {
-      tgram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s);
-      tupdate(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s);
+      tgram(Qt, N, 0, nq, zj, N, 0, nsys, N, w.C, nq, 0, 1, ctx->gscr, s, nullptr, w.corr_low);
+      tupdate(Qt, N, 0, nq, w.C, nq, 0, nsys, -1.0, 1.0, zj, N, 0, N, 1, s, nullptr, w.corr_low);
     }
     apply_h_timed(c, zj, w.W, nsys, theta, low);
     *h_applies += nsys;
@@ -490,9 +498,9 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     // Arnoldi, classical Gram-Schmidt twice, per system: h = Z_i^T p_i ; p_i -= Z_i h
     for (int pass = 0; pass < 2; ++pass) {
       tgram(Z, (long long)nsys * N, N, j + 1, w.P, N, N, 1, N, w.gm.h, sst + 1, sst + 1, nsys,
-                  ctx->gscr, s);
+            ctx->gscr, s, nullptr, w.corr_low);
       tupdate(Z, (long long)nsys * N, N, j + 1, w.gm.h, sst + 1, sst + 1, 1, -1.0, 1.0, w.P, N,
-                    N, N, nsys, s);
+              N, N, nsys, s, nullptr, w.corr_low);
       launch_hess_add(nsys, sst, j, w.gm.h, sst + 1, w.gm, s);
     }
     col_norms2(c, w.P, nsys, w.gm.nrm2);
@@ -500,7 +508,8 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     launch_scale_cols(nsys, N, w.P, N, w.gm.scale, 0, Z + (long long)(j + 1) * nsys * N, N, s);
   }
   launch_gmres_solve(nsys, sst, w.gm, s);
-  tupdate(Z, (long long)nsys * N, N, sst, w.gm.y, sst, sst, 1, 1.0, 0.0, T, N, N, N, nsys, s);
+  tupdate(Z, (long long)nsys * N, N, sst, w.gm.y, sst, sst, 1, 1.0, 0.0, T, N, N, N, nsys, s,
+          nullptr, w.corr_low);
   TPS_CUDA_TRY(ctx, cudaGetLastError());
   return TPS_OK;
 }
@@ -564,6 +573,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   w.prec_dtype = opts.prec_dtype == TPS_F64
                      ? TPS_F64
                      : ((opts.prec_dtype == TPS_TF32_TC && op.nmodes == 2) ? TPS_TF32_TC : TPS_F32);
+  w.corr_low = opts.correction_dtype != TPS_F64;
   if (w.prec_dtype == TPS_TF32_TC) {
     const int st_tf = ensure_tf_operator(op);  // allocation errors here, not mid-solve
     if (st_tf) return set_error(ctx, st_tf, "building the TF32 preconditioner operator failed");
@@ -908,6 +918,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->guard = 2;
   o->smooth_start = 2;
   o->prec_dtype = TPS_TF32_TC;  // 1D; 2D solves use TPS_F32
+  o->correction_dtype = TPS_F32;
   o->h_dtype = TPS_F64;
   o->switch_tol = 1e-6;
   o->refine_block = 0;
@@ -965,6 +976,7 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
   int ha = 0, pa = 0;
   ctx->sw->tm.reset(false);
   ctx->sw->prec_dtype = TPS_F64;
+  ctx->sw->corr_low = false;
   st = correction_impl(ctx, ctx->full, Qt_dev, nq, nullptr, 0, R_dev, theta_dev, nsys, steps,
                        use_prec, shift, 0.0, T_dev, &ha, &pa, stream, false, false);
   if (st) return st;

@@ -104,16 +104,18 @@ struct GramScratch {
 };
 // G_s = A_s^T B_s (p x q, column-major ldg) for s < batch.  need (device, nullable): the
 // product is skipped when *need == 0 (a decision taken by an earlier kernel).
+// low: FP32 products and sums on the FP64 data (~1e-7 relative), for the correction
+// equation, which is solved to 1e-3 and whose result is re-orthogonalised in FP64.
 void launch_gram(const double *A, long long lda, long long bsa, int p, const double *B,
                  long long ldb, long long bsb, int q, long long nrows, double *G, int ldg,
                  long long bsg, int batch, GramScratch &scr, cudaStream_t s,
-                 const int *need = nullptr);
+                 const int *need = nullptr, bool low = false);
 // C_s = beta*C_s + alpha * A_s Y_s (Y column-major p x q, ldy, batch stride bsy); need as
 // for launch_gram.
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
                    long long bsc, long long nrows, int batch, cudaStream_t s,
-                   const int *need = nullptr);
+                   const int *need = nullptr, bool low = false);
 // out[c] = squared 2-norm of column c (ld lda, nrows rows), c < ncols; uses scr.
 void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
                        GramScratch &scr, cudaStream_t s);

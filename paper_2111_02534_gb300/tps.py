@@ -47,7 +47,8 @@ class SolverOpts(C.Structure):
                 ("h_dtype", C.c_int), ("switch_tol", C.c_double), ("refine_block", C.c_int),
                 ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int),
                 ("h64_dtype", C.c_int), ("rr_method", C.c_int),
-                ("rr_refine_max", C.c_int)]
+                ("rr_refine_max", C.c_int),
+                ("correction_dtype", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -331,3 +331,26 @@ def test_tf32_preconditioner_solve_full_size():
     assert np.all(kt <= 1e-12 * np.abs(lam))
     assert st.h_applies <= 1.25 * st32.h_applies, (st.h_applies, st32.h_applies)
     ctx.close()
+
+
+def test_correction_products_fp32_and_fp64_agree_full_size():
+    # the correction solve's Gram/update products in FP32 arithmetic (default) or FP64: the
+    # same certified eigenpairs on the 1d_n512 workload and about as many H applications
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, gold["v0"], w.sigma)
+    ref = np.array(gold["evals"])
+    applies = {}
+    for cd in (tps.F32, tps.F64):
+        lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, correction_dtype=cd)
+        assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+        res = _check_vectors(P, lam, X, parity_sign=1.0)
+        weyl, kt = certify(lam, res, ref)
+        assert np.all(kt <= 1e-12 * np.abs(lam))
+        applies[cd] = st.h_applies
+    assert applies[tps.F32] <= 1.25 * applies[tps.F64], applies
+    ctx.close()

@@ -730,10 +730,24 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     if (nconv > 0 || m + bp > mmaxp) {
       const int avail = m - nconv;
       const int mk = (m + bp > mmaxp) ? std::min(avail, mminp) : avail;
-      tupdate(w.V, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.V2, N, 0,
-                    N, 1, s);
-      tupdate(w.HV, N, 0, m, w.Y + (long long)nconv * ldG, ldG, 0, mk, 1.0, 0.0, w.HV2, N,
-                    0, N, 1, s);
+      // Ritz vectors nconv .. nact-1 are already in X and HX (columns nconv .. of the
+      // block formed for the residuals, by the same products in the same order): copy
+      // them, and form only the remaining kept columns
+      const int ov = std::max(0, std::min(nact - nconv, mk));
+      if (ov > 0) {
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.V2, X + (long long)nconv * N,
+                                          (size_t)ov * N * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.HV2, w.HX + (long long)nconv * N,
+                                          (size_t)ov * N * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+      }
+      if (mk > ov) {
+        tupdate(w.V, N, 0, m, w.Y + (long long)(nconv + ov) * ldG, ldG, 0, mk - ov, 1.0, 0.0,
+                w.V2 + (long long)ov * N, N, 0, N, 1, s);
+        tupdate(w.HV, N, 0, m, w.Y + (long long)(nconv + ov) * ldG, ldG, 0, mk - ov, 1.0, 0.0,
+                w.HV2 + (long long)ov * N, N, 0, N, 1, s);
+      }
       std::swap(w.V, w.V2);
       std::swap(w.HV, w.HV2);
       launch_copy_small(w.theta + nconv, w.theta2, mk, s);

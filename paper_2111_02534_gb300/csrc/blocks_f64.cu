@@ -188,40 +188,64 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
 }
 
 // ------------------------------ Cholesky QR ----------------------------------
+// 1/sqrt(d) for a normal d > 0 to FP64 accuracy without the FP64 square root and divide
+// (each ~0.33 us of dependent latency on GB300): d = ds 4^h with ds in [1, 4), an FP32
+// estimate of 1/sqrt(ds) and two FP64 Newton steps y <- y (3 - ds y^2) / 2 (2^-23 -> 2^-45
+// -> rounding), then scaled by 2^-h.
+__device__ __forceinline__ double rsqrt64(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+  const int h = e >> 1;  // floor(e / 2)
+  const double ds = __longlong_as_double(bits - ((long long)(2 * h) << 52));
+  double y = (double)rsqrtf((float)ds);
+  y = y * (1.5 - 0.5 * ds * y * y);
+  y = y * (1.5 - 0.5 * ds * y * y);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));
+}
+
+// Cholesky G = R^T R (R upper) of the b x b Gram matrix (b <= 32, one warp), dropping
+// columns whose pivot falls below tol_rel^2 ref[j]; then Rinv by back substitution, a
+// column per lane.  Pivots use rsqrt64 and every division is a multiplication by it.
 __global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__restrict__ ref,
                            double tol_rel, double *__restrict__ Rinv, int *__restrict__ keep) {
   __shared__ double R[32][33];
+  __shared__ double inv[32];
   __shared__ int kp[32];
   const int tid = threadIdx.x;
   for (int e = tid; e < b * b; e += blockDim.x) {
     const int i = e % b, j = e / b;
-    R[i][j] = G[(long long)j * b + i];
+    R[i][j] = (i <= j) ? G[(long long)j * b + i] : 0.0;
   }
-  __syncthreads();
-  if (tid == 0) {
-    // right-looking Cholesky G = R^T R (R upper), dropping dependent columns
-    for (int j = 0; j < b; ++j) {
+  __syncwarp();
+  for (int j = 0; j < b; ++j) {
+    if (tid == 0) {
       double d = R[j][j];
       for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
       const double rj = ref ? ref[j] : G[(long long)j * b + j];
-      if (!(d > tol_rel * tol_rel * rj) || !(d > 0.0)) {
-        kp[j] = 0;
-        for (int i = j; i < b; ++i) R[j][i] = 0.0;
-        continue;
-      }
-      kp[j] = 1;
-      const double rjj = sqrt(d);
-      R[j][j] = rjj;
-      for (int i = j + 1; i < b; ++i) {
-        double v = R[j][i];
-        for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
-        R[j][i] = v / rjj;
+      const int ok = (d > tol_rel * tol_rel * rj) && (d > 0.0) && (d > 1e-300);
+      kp[j] = ok;
+      if (ok) {
+        const double y = rsqrt64(d);
+        inv[j] = y;
+        R[j][j] = d * y;
+      } else {
+        inv[j] = 0.0;
+        R[j][j] = 0.0;
       }
     }
-    for (int i = 0; i < b; ++i)
-      for (int j = 0; j < i; ++j) R[i][j] = 0.0;
+    __syncwarp();
+    const int i = tid;
+    if (i > j && i < b) {
+      if (kp[j]) {
+        double v = R[j][i];
+        for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
+        R[j][i] = v * inv[j];
+      } else {
+        R[j][i] = 0.0;  // the dropped column's row of R is zero
+      }
+    }
+    __syncwarp();
   }
-  __syncthreads();
   // Rinv column c by back substitution (dropped rows/columns are zero)
   if (tid < b) {
     const int c = tid;
@@ -235,7 +259,7 @@ __global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__
         }
         double v = (i == c) ? 1.0 : 0.0;
         for (int k = i + 1; k <= c; ++k) v -= R[i][k] * x[k];
-        x[i] = v / R[i][i];
+        x[i] = v * inv[i];
       }
     }
     for (int i = 0; i < b; ++i) Rinv[(long long)c * b + i] = x[i];
@@ -244,12 +268,14 @@ __global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__
 }
 
 // --------------------------- SPD inverse (small) ------------------------------
-// Minv = M^-1 by Cholesky M = L L^T in place in Minv (lower), then L^-1, then L^-T L^-1.
+// Minv = M^-1 by Cholesky M = L L^T in place in Minv (lower), then L^-1, then L^-T L^-1;
+// reciprocal pivots by rsqrt64, no FP64 division.
 __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__restrict__ W) {
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ double sm[];
   double *Lm = sm;           // q x q, column-major
   double *Li = sm + q * q;   // q x q
+  double *dinv = Li + q * q; // 1 / L[j][j]
   for (int e = tid; e < q * q; e += nt) {
     const int i = e % q, j = e / q;
     Lm[e] = 0.5 * (M[(long long)j * q + i] + M[(long long)i * q + j]);
@@ -260,13 +286,15 @@ __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__res
     if (tid == 0) {
       double d = Lm[j * q + j];
       for (int k = 0; k < j; ++k) d -= Lm[k * q + j] * Lm[k * q + j];
-      Lm[j * q + j] = sqrt(d > 0.0 ? d : 1e-300);
+      const double y = rsqrt64(d > 1e-300 ? d : 1e-300);
+      dinv[j] = y;
+      Lm[j * q + j] = (d > 1e-300 ? d : 1e-300) * y;
     }
     __syncthreads();
     for (int i = j + 1 + tid; i < q; i += nt) {
       double v = Lm[j * q + i];
       for (int k = 0; k < j; ++k) v -= Lm[k * q + i] * Lm[k * q + j];
-      Lm[j * q + i] = v / Lm[j * q + j];
+      Lm[j * q + i] = v * dinv[j];
     }
     __syncthreads();
   }
@@ -275,7 +303,7 @@ __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__res
     for (int i = c; i < q; ++i) {
       double v = (i == c) ? 1.0 : 0.0;
       for (int k = c; k < i; ++k) v -= Lm[k * q + i] * Li[c * q + k];
-      Li[c * q + i] = v / Lm[i * q + i];
+      Li[c * q + i] = v * dinv[i];
     }
   }
   __syncthreads();
@@ -409,22 +437,35 @@ __global__ void k_sector_expand(int parity, int nx, int ny, int ncols, const dou
 // sign fix: one CTA per column, argmax |x| (lowest index on ties), flip if negative.
 // |x| is compared through its bit pattern (sign cleared): for IEEE doubles that order is
 // the numeric one, and integer compares avoid the slow FP64 pipe.
-__global__ void k_fix_sign(long long nrows, double *X) {
-  const long long c = blockIdx.x;
-  double *x = X + c * nrows;
+// Sign convention for returned eigenvectors: the entry of largest magnitude (the first
+// such index on ties) is made positive.  Chunk c of column j records its largest |x| (bit
+// pattern), the index, and that entry's sign in part[j][c]; k_sign_apply combines the
+// chunks of a column in chunk order and negates its slice of the column if needed (the
+// signs travel with the partials, so no block reads an entry another may be negating).
+__global__ void k_sign_partial(long long nrows, const double *__restrict__ X, int nchunk,
+                               unsigned long long *__restrict__ part) {
+  const int c = blockIdx.x, j = blockIdx.y;
+  const double *x = X + (long long)j * nrows;
+  const long long per = (nrows + nchunk - 1) / nchunk;
+  const long long r0 = (long long)c * per, r1 = r0 + per < nrows ? r0 + per : nrows;
   unsigned long long best = 0;
-  long long bi = 0;
-  for (long long r = threadIdx.x; r < nrows; r += blockDim.x) {
-    const unsigned long long a = (unsigned long long)__double_as_longlong(x[r]) & 0x7fffffffffffffffULL;
+  long long bi = r0 < nrows ? r0 : 0;
+  int neg = 0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x[r]);
+    const unsigned long long a = u & 0x7fffffffffffffffULL;
     if (a > best) {
       best = a;
       bi = r;
+      neg = (int)(u >> 63);
     }
   }
   __shared__ unsigned long long sb[256];
   __shared__ long long si[256];
+  __shared__ int sn[256];
   sb[threadIdx.x] = best;
   si[threadIdx.x] = bi;
+  sn[threadIdx.x] = neg;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
@@ -433,14 +474,42 @@ __global__ void k_fix_sign(long long nrows, double *X) {
       if (a > sb[threadIdx.x] || (a == sb[threadIdx.x] && ai < si[threadIdx.x])) {
         sb[threadIdx.x] = a;
         si[threadIdx.x] = ai;
+        sn[threadIdx.x] = sn[threadIdx.x + o];
       }
     }
     __syncthreads();
   }
-  const bool neg = __double_as_longlong(x[si[0]]) < 0;
+  if (threadIdx.x == 0) {
+    unsigned long long *pp = part + ((long long)j * nchunk + c) * 2;
+    pp[0] = sb[0];
+    pp[1] = ((unsigned long long)si[0] << 1) | (unsigned long long)sn[0];
+  }
+}
+
+__global__ void k_sign_apply(long long nrows, double *__restrict__ X, int nchunk,
+                             const unsigned long long *__restrict__ part) {
+  const int j = blockIdx.y;
+  __shared__ int neg;
+  if (threadIdx.x == 0) {
+    unsigned long long best = 0, tag = 0;
+    bool have = false;
+    for (int c = 0; c < nchunk; ++c) {  // chunk order = index order: ties keep the first
+      const unsigned long long a = part[((long long)j * nchunk + c) * 2];
+      const unsigned long long t = part[((long long)j * nchunk + c) * 2 + 1];
+      if (!have || a > best) {
+        best = a;
+        tag = t;
+        have = true;
+      }
+    }
+    neg = (int)(tag & 1ull);
+  }
   __syncthreads();
-  if (neg)
-    for (long long r = threadIdx.x; r < nrows; r += blockDim.x) x[r] = -x[r];
+  if (!neg) return;
+  double *x = X + (long long)j * nrows;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows;
+       r += (long long)gridDim.x * blockDim.x)
+    x[r] = -x[r];
 }
 
 unsigned grid_for(long long total, int threads = 256) {
@@ -622,11 +691,11 @@ void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, 
 }
 
 void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)q * q * sizeof(double);
+  const size_t smem = (2 * (size_t)q * q + q) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_spd_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * 96 * 96 * (int)sizeof(double));
+                         (2 * 96 * 96 + 96) * (int)sizeof(double));
     attr = true;
   }
   count_launch();
@@ -671,10 +740,20 @@ void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *r
                                                                        full);
 }
 
-void launch_fix_sign(int ncols, long long nrows, double *X, cudaStream_t s) {
-  if (ncols <= 0) return;
+void launch_fix_sign(int ncols, long long nrows, double *X, GramScratch &scr, cudaStream_t s) {
+  if (ncols <= 0 || nrows <= 0) return;
+  long long nchunk = (4LL * 152 + ncols - 1) / ncols;
+  const long long maxc = (nrows + 4095) / 4096;
+  if (nchunk > maxc) nchunk = maxc;
+  if (nchunk > scr.capacity / (2LL * ncols)) nchunk = scr.capacity / (2LL * ncols);
+  if (nchunk < 1) nchunk = 1;
+  unsigned long long *part = reinterpret_cast<unsigned long long *>(scr.partial);
   count_launch();
-  k_fix_sign<<<ncols, 256, 0, s>>>(nrows, X);
+  k_sign_partial<<<dim3((unsigned)nchunk, ncols), 256, 0, s>>>(nrows, X, (int)nchunk, part);
+  long long blocks = (nrows + 255) / 256;
+  if (blocks > 152LL * 4 / ncols + 1) blocks = 152LL * 4 / ncols + 1;
+  count_launch();
+  k_sign_apply<<<dim3((unsigned)blocks, ncols), 256, 0, s>>>(nrows, X, (int)nchunk, part);
 }
 
 }  // namespace tps

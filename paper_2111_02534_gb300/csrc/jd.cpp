@@ -861,7 +861,7 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       evals_host[i] = lam[order[i]];
       if (i < 64) stt.resid[i] = resid[order[i]];
     }
-    launch_fix_sign(nret, ctx->full.N, evecs_dev, s);
+    launch_fix_sign(nret, ctx->full.N, evecs_dev, ctx->gscr, s);
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     TPS_CUDA_TRY(ctx, cudaGetLastError());
   }

@@ -173,7 +173,7 @@ void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double 
 void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
                           double *full, cudaStream_t s);
 // flip the sign of each column so that its entry of largest magnitude is positive.
-void launch_fix_sign(int ncols, long long nrows, double *X, cudaStream_t s);
+void launch_fix_sign(int ncols, long long nrows, double *X, GramScratch &scr, cudaStream_t s);
 
 // ------------------------------- context ------------------------------------
 struct SolverWorkspace;

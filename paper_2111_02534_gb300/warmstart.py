@@ -1,5 +1,6 @@
 """Learned warm start: data generation from the solver's own eigenvectors, training on the
-GPU (tps_ws_loss_grad / tps_ws_adam_step), and warm- versus cold-start evaluation.
+GPU (tps_ws_loss_grad / tps_ws_adam_step), and its evaluation against a cold start and the
+non-learned homotopy start (the previous point of a decreasing-E0 sweep).
 
 Every numerical step runs in the library's kernels; this module only sequences them.
 """
@@ -69,10 +70,37 @@ def train(model, X, T, steps=2000, batch=256, lr=1e-3, lr_final=1e-4, seed=0):
     return losses
 
 
-def evaluate(model, instances, k, block=None, tol=1e-12, device=0):
-    """Cold start versus warm start on each instance: outer iterations, H applications
-    (MVMs, the paper's Table 2 count), solve time and the largest relative eigenvalue
-    difference between the two (the tests judge the eigenpairs with the oracle)."""
+HOMOTOPY_STEP = 1.25  # E0 ratio between neighbouring points of a decreasing-E0 sweep
+
+
+def homotopy_solve(ctx, inst, k, block, tol, ev, step=HOMOTOPY_STEP, timed=True):
+    """The non-learned baseline (Sec. 6, homotopy over E0): solve the neighbouring point of
+    a sweep that decreases E0 -- the same M/m, sigma and grid, E0 larger by `step`, v0 tuned
+    to it -- and start the instance's solve from its k eigenvectors.  The neighbour's solve
+    is the previous step of the sweep and is not timed.  Returns (eigenvalues, Stats,
+    seconds of the instance's solve); the context's potential is the instance's after."""
+    import torch
+    mu = inst["M"] * inst["m"] / (inst["M"] + inst["m"])
+    v_prev = tps.two_body_v0(1, mu, 1.0, inst["E0"] * step, tps.GAUSS, inst["sigma"], inst["n"],
+                             inst["L"])
+    v_inst = tps.two_body_v0(1, mu, 1.0, inst["E0"], tps.GAUSS, inst["sigma"], inst["n"],
+                             inst["L"])
+    prev = torch.empty_like(ev)
+    ctx.set_pair_potential(tps.GAUSS, v_prev, inst["sigma"])
+    ctx.solve(k, tps.X_EVEN, tol, block, prev)
+    ctx.set_pair_potential(tps.GAUSS, v_inst, inst["sigma"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, st = ctx.solve(k, tps.X_EVEN, tol, block, ev, x0=prev)
+    torch.cuda.synchronize()
+    return lam, st, time.perf_counter() - t0
+
+
+def evaluate(model, instances, k, block=None, tol=1e-12, device=0, homotopy=True):
+    """Cold start, learned warm start and (homotopy=True) the homotopy start on each
+    instance: outer iterations, H applications (MVMs, the paper's Table 2 count), solve
+    time and the largest relative eigenvalue difference to the cold solve (the tests judge
+    the eigenpairs with the oracle)."""
     import torch
     block = block or k
     rows = []
@@ -89,14 +117,20 @@ def evaluate(model, instances, k, block=None, tol=1e-12, device=0):
                                            tps.X_EVEN, tol, block, ev)
             torch.cuda.synchronize()
             out[name] = (lam, st.outer_iters, time.perf_counter() - t0, used, st.h_applies)
-        ctx.close()
         lc, lw = out["cold"][0], out["warm"][0]
-        rows.append({"cold_iters": out["cold"][1], "warm_iters": out["warm"][1],
-                     "cold_s": out["cold"][2], "warm_s": out["warm"][2],
-                     "cold_mvm": out["cold"][4], "warm_mvm": out["warm"][4],
-                     "used_warm": out["warm"][3],
-                     "rel_diff": float(np.max(np.abs(lc - lw) /
-                                              np.maximum(np.abs(lc), abs(lc[0]))))})
+        scale = np.maximum(np.abs(lc), abs(lc[0]))
+        row = {"cold_iters": out["cold"][1], "warm_iters": out["warm"][1],
+               "cold_s": out["cold"][2], "warm_s": out["warm"][2],
+               "cold_mvm": out["cold"][4], "warm_mvm": out["warm"][4],
+               "used_warm": out["warm"][3],
+               "rel_diff": float(np.max(np.abs(lc - lw) / scale))}
+        if homotopy:
+            lh, sth, th = homotopy_solve(ctx, inst, k, block, tol, ev)
+            row.update({"homotopy_iters": sth.outer_iters, "homotopy_mvm": sth.h_applies,
+                        "homotopy_s": th,
+                        "homotopy_rel_diff": float(np.max(np.abs(lc - lh) / scale))})
+        ctx.close()
+        rows.append(row)
     return rows
 
 
@@ -135,10 +169,15 @@ def main(argv=None):
                   "loss_last": float(np.mean(losses[-20:]))},
         "eval": {"instances": len(rows), "n": args.eval_n, "k": args.eval_k,
                  "cold_iters": mean("cold_iters"), "warm_iters": mean("warm_iters"),
+                 "homotopy_iters": mean("homotopy_iters"),
                  "cold_mvm": mean("cold_mvm"), "warm_mvm": mean("warm_mvm"),
+                 "homotopy_mvm": mean("homotopy_mvm"),
                  "cold_ms": 1e3 * mean("cold_s"), "warm_ms": 1e3 * mean("warm_s"),
+                 "homotopy_ms": 1e3 * mean("homotopy_s"),
+                 "homotopy_step": HOMOTOPY_STEP,
                  "used_warm": sum(r["used_warm"] for r in rows),
-                 "max_rel_diff": max(r["rel_diff"] for r in rows)}}))
+                 "max_rel_diff": max(r["rel_diff"] for r in rows),
+                 "homotopy_max_rel_diff": max(r["homotopy_rel_diff"] for r in rows)}}))
 
 
 if __name__ == "__main__":

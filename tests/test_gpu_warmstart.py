@@ -161,3 +161,31 @@ def test_trained_network_beats_cold_start():
     assert residual_norms(P, host(ev), lam).max() <= 1e-11 * P.norm_estimate()
     ctx.close()
     model.close()
+
+
+def test_homotopy_start_saves_h_applications():
+    # the non-learned baseline: the previous point of a decreasing-E0 sweep (E0 x 1.25,
+    # same M/m, sigma and grid) starts the instance's solve; fewer H applications than a
+    # cold start, eigenvalues equal to the cold ones to 1e-10, the oracle's residual as judge
+    require_gpu()
+    from paper_2111_02534_gb300 import tps, warmstart
+    from paper_2111_02534_gb300.inputs import warmstart_instances
+    kw = dict(ratio=(10.0, 30.0), E0=(1e-2, 1e-1), sigmas=(1.0,), L=20.0)
+    insts = warmstart_instances(6, seed=97, ns=(96,), **kw)
+    cold, hom = [], []
+    for inst in insts:
+        ctx, v0 = warmstart.make_context(inst)
+        N = ctx.info()[0]
+        ev = torch.empty(4, N, dtype=torch.float64, device="cuda")
+        lc, stc = ctx.solve(4, tps.X_EVEN, 1e-12, 4, ev)
+        lh, sth, _ = warmstart.homotopy_solve(ctx, inst, 4, 4, 1e-12, ev)
+        assert sth.n_converged == 4
+        assert np.max(np.abs(lc - lh) / np.maximum(np.abs(lc), abs(lc[0]))) <= 1e-10
+        cold.append(stc.h_applies)
+        hom.append(sth.h_applies)
+        P = problem_1d(inst["M"], 1.0, 1.0, (inst["n"], inst["n"]), (inst["L"], inst["L"]), v0,
+                       inst["sigma"])
+        assert residual_norms(P, host(ev), lh).max() <= 1e-11 * P.norm_estimate()
+        ctx.close()
+    print("homotopy MVMs", np.mean(hom), "cold", np.mean(cold))
+    assert np.mean(hom) < 0.9 * np.mean(cold), (hom, cold)

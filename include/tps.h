@@ -359,7 +359,11 @@ int tps_gram_noalloc(const double *A_dev, long long lda, int p, const double *B_
  * rank (px + py).  Loss per sample against a target T (px x py, from tps_ws_project):
  *     L = 1 - <P, T>^2 / (|P|^2 |T|^2),  P = C^T D,
  * invariant under the arbitrary sign and scale of an eigenvector; the mean over the batch
- * is minimised.  1D only. */
+ * is minimised.  In 2D the same matrix form holds with x and y the Jacobi vectors: psi
+ * (layout [x1][x2][y1][y2]) is read as an (n_x1 n_x2) x (n_y1 n_y2) matrix and
+ *     phi_a(x) = F_a1(x1) F_a2(x2),  a = a1 q_x + a2,  px = q_x^2,
+ * F the real Fourier modes of one Cartesian component (a1, a2 < q_x), chi_b likewise with
+ * py = q_y^2; a 2D model needs px and py perfect squares. */
 typedef struct tps_ws tps_ws;
 
 /* Create a model on `device` with He-initialised weights (counter-based generator from
@@ -390,7 +394,8 @@ int tps_ws_loss_grad(tps_ws *ws, const float *X_dev, const float *T_dev, int B,
 int tps_ws_adam_step(tps_ws *ws, float lr, float beta1, float beta2, float eps,
                      cudaStream_t stream);
 /* Training targets: T[v] = Phi^T psi_v Chi (px x py, FP32) of k eigenvectors evecs[k][N]
- * (device, FP64, the context's full 1D grid).  Needs 2 px <= n_x and py < n_y. */
+ * (device, FP64, the context's full grid).  Needs 2 px <= n_x and py < n_y in 1D;
+ * q_x < n_x1, n_x2 and q_y < n_y1, n_y2 in 2D (TPS_ERR_INVALID_ARG otherwise). */
 int tps_ws_project(tps_ws *ws, tps_ctx *ctx, const double *evecs_dev, int k, float *T_dev,
                    cudaStream_t stream);
 /* Predicted states on the context's full grid: x0[k][N] (device FP64) for features

@@ -14,7 +14,11 @@ homotopy restart of Sec. 5.2 and the low-rank outlook of Sec. 6):
   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps);
 * grid maps: Phi[x][a] = cos(a pi x / L) sampled at x_j = -L + 2Lj/n and scaled to unit
   norm over the grid, Chi[y][b] the real Fourier modes 1, cos, sin, cos 2, sin 2, ... likewise;
-  targets T = Phi^T psi Chi, predictions psi = Phi P Chi^T.
+  targets T = Phi^T psi Chi, predictions psi = Phi P Chi^T;
+* 2D grid maps (psi laid out [x1][x2][y1][y2]): the same matrix form with psi a
+  (n_x1 n_x2) x (n_y1 n_y2) matrix, Phi[(x1,x2)][(a1,a2)] = F_a1(x1) F_a2(x2) over the first
+  q_x real Fourier modes F of each Cartesian component (px = q_x^2, a = a1 q_x + a2) and
+  Chi likewise over y (py = q_y^2): products of unit-norm columns, so unit norm again.
 
 Backpropagation is written out by hand (chain rule through each layer); tests pin it
 to central finite differences of the forward pass.
@@ -157,3 +161,40 @@ def assemble(o, rank, px, py, nx, ny):
     P = np.einsum("sra,srb->sab", C, D)
     Phi, Chi = mode_matrix(0, nx, px), mode_matrix(1, ny, py)
     return np.einsum("xa,sab,yb->sxy", Phi, P, Chi).reshape(len(o), nx * ny)
+
+
+def mode_matrix_2d(n1: int, n2: int, q: int) -> np.ndarray:
+    """(n1 n2) x q^2 samples of the product modes F_a1(x1) F_a2(x2) (real Fourier modes of
+    each Cartesian component), row x1 n2 + x2, column a1 q + a2."""
+    F1, F2 = mode_matrix(1, n1, q), mode_matrix(1, n2, q)
+    out = np.empty((n1 * n2, q * q))
+    for x1 in range(n1):
+        for x2 in range(n2):
+            for a1 in range(q):
+                for a2 in range(q):
+                    out[x1 * n2 + x2, a1 * q + a2] = F1[x1, a1] * F2[x2, a2]
+    return out
+
+
+def _side(p: int) -> int:
+    q = int(round(np.sqrt(p)))
+    if q * q != p:
+        raise ValueError("2D grid maps need px and py to be perfect squares")
+    return q
+
+
+def project_2d(psi, n, px, py):
+    """Targets T[v] = Phi^T psi_v Chi for 2D psi [k, n0 n1 n2 n3]."""
+    Phi = mode_matrix_2d(n[0], n[1], _side(px))
+    Chi = mode_matrix_2d(n[2], n[3], _side(py))
+    P = np.asarray(psi, dtype=np.float64).reshape(-1, n[0] * n[1], n[2] * n[3])
+    return np.einsum("xa,vxy,yb->vab", Phi, P, Chi)
+
+
+def assemble_2d(o, rank, px, py, n):
+    """2D grid functions psi[v] = Phi (C^T D) Chi^T from network outputs o [k, R(px+py)]."""
+    C, D = split_output(np.asarray(o, dtype=np.float64), rank, px, py)
+    P = np.einsum("sra,srb->sab", C, D)
+    Phi = mode_matrix_2d(n[0], n[1], _side(px))
+    Chi = mode_matrix_2d(n[2], n[3], _side(py))
+    return np.einsum("xa,sab,yb->sxy", Phi, P, Chi).reshape(len(o), -1)

@@ -284,6 +284,20 @@ __global__ void k_mode_matrix(int kind, int n, int na, double *__restrict__ M) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) M[(long long)j * na + a] *= inv;
 }
 
+// 2D product modes: K[(i1 n2 + i2)][(a1 q + a2)] = F1[i1][a1] F2[i2][a2] from two unit-norm
+// 1D mode matrices (n1 x q, n2 x q), so every column has unit norm again
+__global__ void k_mode_kron(const double *__restrict__ F1, int n1, const double *__restrict__ F2,
+                            int n2, int q, double *__restrict__ K) {
+  const long long qq = (long long)q * q, total = (long long)n1 * n2 * qq;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / qq;
+    const int col = (int)(e % qq);
+    const int i1 = (int)(row / n2), i2 = (int)(row % n2), a1 = col / q, a2 = col % q;
+    K[e] = F1[(long long)i1 * q + a1] * F2[(long long)i2 * q + a2];
+  }
+}
+
 // U[v][x][b] = sum_y psi[v][x][y] Chi[y][b]  (first mode product of the projection)
 __global__ void k_project_y(const double *__restrict__ psi, long long N, int nx, int ny,
                             const double *__restrict__ Chi, int py, double *__restrict__ U,
@@ -464,12 +478,70 @@ void forward(tps_ws *ws, int B, bool bf16, cudaStream_t s) {
   }
 }
 
-// unit-norm mode matrices of a 1D grid: Phi (nx x px, x-even cosines), Chi (ny x py)
-void mode_matrices(tps_ws *ws, int nx, int ny, double *Phi, double *Chi, cudaStream_t s) {
+int isqrt_exact(int p) {
+  int q = 0;
+  while ((q + 1) * (q + 1) <= p) ++q;
+  return q * q == p ? q : -1;
+}
+
+// The grid maps of a context as one matrix product psi ~ Phi P Chi^T: psi viewed as an
+// nx x ny matrix (1D: n_x x n_y; 2D: (n_x1 n_x2) x (n_y1 n_y2)), Phi nx x px, Chi ny x py.
+struct GridMaps {
+  int dim = 1, nx = 0, ny = 0, qx = 0, qy = 0;
+  long long len = 0;  // doubles of scratch the maps take (Phi, Chi and 2D 1D-factors)
+};
+
+int grid_maps(tps_ws *ws, const tps_ctx *ctx, GridMaps *g) {
+  if (!ctx->have_grid) return ws_error(ws, TPS_ERR_INVALID_ARG, "grid not set");
+  g->dim = ctx->dim;
+  if (ctx->dim == 1) {
+    g->nx = ctx->n[0];
+    g->ny = ctx->n[1];
+    if (2 * ws->px > g->nx || ws->py >= g->ny)
+      return ws_error(ws, TPS_ERR_INVALID_ARG, "grid too coarse for the model's modes");
+    g->len = (long long)g->nx * ws->px + (long long)g->ny * ws->py;
+    return TPS_OK;
+  }
+  g->qx = isqrt_exact(ws->px);
+  g->qy = isqrt_exact(ws->py);
+  if (g->qx < 1 || g->qy < 1)
+    return ws_error(ws, TPS_ERR_INVALID_ARG, "2D grid maps need px and py perfect squares");
+  for (int k = 0; k < 4; ++k)
+    if ((k < 2 ? g->qx : g->qy) >= ctx->n[k])
+      return ws_error(ws, TPS_ERR_INVALID_ARG, "grid too coarse for the model's modes");
+  g->nx = ctx->n[0] * ctx->n[1];
+  g->ny = ctx->n[2] * ctx->n[3];
+  long long f = 0;
+  for (int k = 0; k < 4; ++k) f += (long long)ctx->n[k] * (k < 2 ? g->qx : g->qy);
+  g->len = (long long)g->nx * ws->px + (long long)g->ny * ws->py + f;
+  return TPS_OK;
+}
+
+// unit-norm mode matrices: 1D Phi (x-even cosines) and Chi (real Fourier modes); 2D the
+// products of the real Fourier modes of the two Cartesian components of x (and of y)
+void mode_matrices(tps_ws *ws, const tps_ctx *ctx, const GridMaps &g, double *Phi, double *Chi,
+                   cudaStream_t s) {
+  if (g.dim == 1) {
+    tps::count_launch();
+    tps::mlp::k_mode_matrix<<<ws->px, 256, 0, s>>>(0, g.nx, ws->px, Phi);
+    tps::count_launch();
+    tps::mlp::k_mode_matrix<<<ws->py, 256, 0, s>>>(1, g.ny, ws->py, Chi);
+    return;
+  }
+  double *F = Chi + (long long)g.ny * ws->py, *Fk[4];
+  for (int k = 0; k < 4; ++k) {
+    const int q = k < 2 ? g.qx : g.qy;
+    Fk[k] = F;
+    tps::count_launch();
+    tps::mlp::k_mode_matrix<<<q, 256, 0, s>>>(1, ctx->n[k], q, F);
+    F += (long long)ctx->n[k] * q;
+  }
   tps::count_launch();
-  tps::mlp::k_mode_matrix<<<ws->px, 256, 0, s>>>(0, nx, ws->px, Phi);
+  tps::mlp::k_mode_kron<<<grid_1d((long long)g.nx * ws->px), 256, 0, s>>>(
+      Fk[0], ctx->n[0], Fk[1], ctx->n[1], g.qx, Phi);
   tps::count_launch();
-  tps::mlp::k_mode_matrix<<<ws->py, 256, 0, s>>>(1, ny, ws->py, Chi);
+  tps::mlp::k_mode_kron<<<grid_1d((long long)g.ny * ws->py), 256, 0, s>>>(
+      Fk[2], ctx->n[2], Fk[3], ctx->n[3], g.qy, Chi);
 }
 
 }  // namespace
@@ -682,17 +754,16 @@ int tps_ws_adam_step(tps_ws *ws, float lr, float beta1, float beta2, float eps,
 int tps_ws_project(tps_ws *ws, tps_ctx *ctx, const double *evecs_dev, int k, float *T_dev,
                    cudaStream_t stream) {
   if (!ws || !ctx || k < 0 || (k > 0 && (!evecs_dev || !T_dev))) return TPS_ERR_INVALID_ARG;
-  if (ctx->dim != 1 || !ctx->have_grid) return ws_error(ws, TPS_ERR_INVALID_ARG, "1D grid needed");
-  const int nx = ctx->n[0], ny = ctx->n[1];
-  if (2 * ws->px > nx || ws->py >= ny)
-    return ws_error(ws, TPS_ERR_INVALID_ARG, "grid too coarse for the model's modes");
+  GridMaps g;
+  int st = grid_maps(ws, ctx, &g);
+  if (st) return st;
+  const int nx = g.nx, ny = g.ny;
   if (k == 0) return TPS_OK;
   WS_CUDA_TRY(ws, cudaSetDevice(ws->device));
-  const long long need = (long long)nx * ws->px + (long long)ny * ws->py + (long long)k * nx * ws->py;
-  int st = ensure_scratch(ws, need);
+  st = ensure_scratch(ws, g.len + (long long)k * nx * ws->py);
   if (st) return st;
-  double *Phi = ws->scratch, *Chi = Phi + (long long)nx * ws->px, *U = Chi + (long long)ny * ws->py;
-  mode_matrices(ws, nx, ny, Phi, Chi, stream);
+  double *Phi = ws->scratch, *Chi = Phi + (long long)nx * ws->px, *U = ws->scratch + g.len;
+  mode_matrices(ws, ctx, g, Phi, Chi, stream);
   tps::count_launch();
   tps::mlp::k_project_y<<<grid_1d((long long)k * nx * ws->py), 256, 0, stream>>>(
       evecs_dev, (long long)nx * ny, nx, ny, Chi, ws->py, U, k);
@@ -706,16 +777,15 @@ int tps_ws_project(tps_ws *ws, tps_ctx *ctx, const double *evecs_dev, int k, flo
 int tps_ws_predict(tps_ws *ws, tps_ctx *ctx, const float *X_dev, int k, double *x0_dev,
                    cudaStream_t stream) {
   if (!ws || !ctx || k < 0 || (k > 0 && (!X_dev || !x0_dev))) return TPS_ERR_INVALID_ARG;
-  if (ctx->dim != 1 || !ctx->have_grid) return ws_error(ws, TPS_ERR_INVALID_ARG, "1D grid needed");
-  const int nx = ctx->n[0], ny = ctx->n[1];
-  if (2 * ws->px > nx || ws->py >= ny)
-    return ws_error(ws, TPS_ERR_INVALID_ARG, "grid too coarse for the model's modes");
+  GridMaps g;
+  int st = grid_maps(ws, ctx, &g);
+  if (st) return st;
+  const int nx = g.nx, ny = g.ny;
   if (k == 0) return TPS_OK;
   WS_CUDA_TRY(ws, cudaSetDevice(ws->device));
-  int st = ensure_batch(ws, k);
+  st = ensure_batch(ws, k);
   if (st) return st;
-  const long long need = (long long)nx * ws->px + (long long)ny * ws->py + (long long)k * ws->px * ny;
-  st = ensure_scratch(ws, need);
+  st = ensure_scratch(ws, g.len + (long long)k * ws->px * ny);
   if (st) return st;
   if (!ws->wb_valid) {
     tps::count_launch();
@@ -725,8 +795,8 @@ int tps_ws_predict(tps_ws *ws, tps_ctx *ctx, const float *X_dev, int k, double *
   WS_CUDA_TRY(ws, cudaMemcpyAsync(ws->A[0], X_dev, sizeof(float) * 4 * k,
                                   cudaMemcpyDeviceToDevice, stream));
   forward(ws, k, true, stream);
-  double *Phi = ws->scratch, *Chi = Phi + (long long)nx * ws->px, *Q = Chi + (long long)ny * ws->py;
-  mode_matrices(ws, nx, ny, Phi, Chi, stream);
+  double *Phi = ws->scratch, *Chi = Phi + (long long)nx * ws->px, *Q = ws->scratch + g.len;
+  mode_matrices(ws, ctx, g, Phi, Chi, stream);
   tps::count_launch();
   tps::mlp::k_assemble_y<<<grid_1d((long long)k * ws->px * ny), 256, 0, stream>>>(
       ws->A[kLayers], ws->R, ws->px, ws->py, Chi, ny, Q, k);
@@ -746,7 +816,7 @@ int tps_ws_solve(tps_ws *ws, tps_ctx *ctx, double mass_ratio, double v0, double 
   if (!ws)  // no model: the cold-started solver
     return tps_solve(ctx, k, parity, tol, block, nullptr, 0, opts, evals_host, evecs_dev, stats,
                      stream);
-  if (ctx->dim != 1 || !ctx->have_grid) return ws_error(ws, TPS_ERR_INVALID_ARG, "1D grid needed");
+  if (!ctx->have_grid) return ws_error(ws, TPS_ERR_INVALID_ARG, "grid not set");
   // the whole first block the solver accepts: k wanted pairs plus its guard pairs
   tps_solver_opts o;
   if (opts)
@@ -761,7 +831,8 @@ int tps_ws_solve(tps_ws *ws, tps_ctx *ctx, double mass_ratio, double v0, double 
   int st = tps_ws_features(nw, mr.data(), vv.data(), sg.data(), idx.data(), X.data());
   if (st) return ws_error(ws, st, "bad problem parameters");
   WS_CUDA_TRY(ws, cudaSetDevice(ws->device));
-  const long long N = (long long)ctx->n[0] * ctx->n[1];
+  long long N = 1;
+  for (int d = 0; d < 2 * ctx->dim; ++d) N *= ctx->n[d];
   if (!ws->feat) WS_CUDA_TRY(ws, cudaMalloc(&ws->feat, sizeof(float) * 4 * 64));
   if (ws->x0_len < (long long)nw * N) {
     cudaFree(ws->x0);

@@ -92,10 +92,11 @@ def sweep_instances(count: int = 256, seed: int = 3):
 
 
 def warmstart_instances(count: int, seed: int, ratio=(1.0, 40.0), E0=(1e-4, 1.0),
-                        sigmas=(0.5, 1.0, 2.0), ns=(128, 192, 256, 384), L: float = 20.0):
-    """Parameters of 1D instances for the learned warm start (same fields as
-    sweep_instances): M/m uniform in `ratio`, E0 log-uniform in `E0`, sigma and n drawn
-    from the given sets."""
+                        sigmas=(0.5, 1.0, 2.0), ns=(128, 192, 256, 384), L: float = 20.0,
+                        dim: int = 1):
+    """Parameters of instances for the learned warm start (same fields as sweep_instances,
+    plus dim): M/m uniform in `ratio`, E0 log-uniform in `E0`, sigma and n drawn from the
+    given sets; n points and half-width L on every Cartesian component."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(count):
@@ -103,5 +104,5 @@ def warmstart_instances(count: int, seed: int, ratio=(1.0, 40.0), E0=(1e-4, 1.0)
         e = float(np.exp(rng.uniform(np.log(E0[0]), np.log(E0[1]))))
         s = float(rng.choice(list(sigmas)))
         n = int(rng.choice(list(ns)))
-        out.append(dict(M=float(r), m=1.0, E0=e, sigma=s, n=n, L=L))
+        out.append(dict(M=float(r), m=1.0, E0=e, sigma=s, n=n, L=L, dim=dim))
     return out

@@ -115,6 +115,74 @@ def test_project_and_predict_match_oracle(n):
     m.close()
 
 
+def test_project_and_predict_2d_match_oracle():
+    # 2D grid maps: psi [x1][x2][y1][y2] as an (n_x^2) x (n_y^2) matrix, product modes
+    require_gpu()
+    from gpu_common import make_ctx_2d
+    from paper_2111_02534_gb300 import tps
+    n = (8, 8, 10, 10)
+    m = _model(px=9, py=16)
+    ctx = make_ctx_2d(20.0, 1.0, n, (6.0,) * 4, 1.0, 1.0)
+    N = ctx.info()[0]
+    rng = np.random.Generator(np.random.PCG64(8))
+    psi = rng.normal(size=(3, N))
+    T = host(m.project(ctx, dev(psi)))
+    assert np.allclose(T, mlp.project_2d(psi, n, m.px, m.py), rtol=0,
+                       atol=1e-6 * np.abs(T).max())
+    X = rng.normal(size=(5, 4)).astype(np.float32)
+    got = host(m.predict(ctx, _f32(X)))
+    dims = mlp.layer_dims(m.px, m.py, m.rank, m.hidden)
+    o, _ = mlp.forward(_bf16(m.get_params(), dims).astype(np.float64), dims, X.astype(np.float64))
+    ref = mlp.assemble_2d(o, m.rank, m.px, m.py, n)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.abs(ref).max()
+    m.close()
+    # px not a perfect square, or more modes than grid points: rejected
+    bad = _model(px=8, py=16)
+    with pytest.raises(tps.TpsError):
+        bad.project(ctx, dev(psi))
+    bad.close()
+    big = _model(px=81, py=16)
+    with pytest.raises(tps.TpsError):
+        big.predict(ctx, _f32(X))
+    big.close()
+    ctx.close()
+
+
+def test_trained_network_2d_beats_cold_start():
+    # 2D: train on solver eigenvectors of instances on a 12^4 grid (degenerate pairs made
+    # canonical), start unseen instances on a finer 16^4 grid from the prediction
+    require_gpu()
+    from paper_2111_02534_gb300 import tps, warmstart
+    from paper_2111_02534_gb300.inputs import warmstart_instances
+    from oracle.hamiltonian import problem_2d
+    kw = dict(warmstart.TWO_D)
+    train_set = warmstart_instances(80, seed=12, ns=(12,), **kw)
+    model = tps.WarmStart(px=25, py=25, rank=16, hidden=256, seed=1)
+    X, T, _ = warmstart.make_dataset(model, train_set, k=6, chunk=40)
+    losses = warmstart.train(model, X, T, steps=600, batch=256, lr=2e-3, lr_final=2e-4)
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:20])
+    test_set = warmstart_instances(4, seed=13, ns=(16,), **kw)
+    rows = warmstart.evaluate(model, test_set, k=4)
+    cold = np.mean([r["cold_mvm"] for r in rows])
+    warm = np.mean([r["warm_mvm"] for r in rows])
+    hom = np.mean([r["homotopy_mvm"] for r in rows])
+    print("2D MVMs cold", cold, "warm", warm, "homotopy", hom,
+          "loss", np.mean(losses[:20]), np.mean(losses[-20:]))
+    assert all(r["used_warm"] for r in rows)
+    assert max(r["rel_diff"] for r in rows) <= 1e-10
+    assert max(r["homotopy_rel_diff"] for r in rows) <= 1e-10
+    assert warm < cold and hom < cold, (warm, hom, cold)   # measured 298.5, 248.8, 329.5
+    inst = test_set[0]
+    ctx, v0 = warmstart.make_context(inst)
+    ev = torch.empty(4, ctx.info()[0], dtype=torch.float64, device="cuda")
+    lam, st, used = tps.solve_warm(model, ctx, inst["M"], v0, inst["sigma"], 4, tps.ANY,
+                                   1e-12, 4, ev)
+    P = problem_2d(inst["M"], 1.0, 1.0, (inst["n"],) * 4, (inst["L"],) * 4, v0, inst["sigma"])
+    assert used and residual_norms(P, host(ev), lam).max() <= 1e-11 * P.norm_estimate()
+    ctx.close()
+    model.close()
+
+
 def test_trained_network_beats_cold_start():
     # train on eigenvectors the solver produced for 120 instances, then start unseen
     # instances (also on a finer grid) from the prediction

@@ -115,3 +115,41 @@ def test_project_and_assemble_round_trip():
 def test_features_are_the_stated_map():
     X = mlp.features(40.0, math.e ** 5, 2.0, 8)
     assert np.allclose(X, [[1.0, 1.0, 1.0, 1.0]], atol=1e-15)
+
+
+def test_mode_matrix_2d_is_the_product_basis():
+    # pinned to the modes written out from their formulas (not through mode_matrix):
+    # F_0 = 1, F_1 = cos(t), F_2 = sin(t), F_3 = cos(2t), ... with t = pi x / L, x_j = -L + 2Lj/n
+    n1, n2, q = 12, 10, 4
+    def raw(a, n):
+        t = 2.0 * np.pi * np.arange(n) / n - np.pi
+        f = (a + 1) // 2
+        return np.ones(n) if a == 0 else (np.cos(f * t) if a % 2 else np.sin(f * t))
+    M = mlp.mode_matrix_2d(n1, n2, q)
+    assert M.shape == (n1 * n2, q * q)
+    assert np.allclose(M.T @ M, np.eye(q * q), atol=1e-13)
+    for a1, a2 in ((0, 0), (1, 2), (3, 0), (2, 3)):
+        g = np.outer(raw(a1, n1), raw(a2, n2)).ravel()
+        assert np.allclose(M[:, a1 * q + a2], g / np.linalg.norm(g), atol=1e-14)
+
+
+def test_project_and_assemble_2d():
+    n, px, py, rank = (8, 6, 10, 6), 9, 16, 3
+    C = RNG.normal(size=(2, rank, px))
+    D = RNG.normal(size=(2, rank, py))
+    o = np.concatenate([C.reshape(2, -1), D.reshape(2, -1)], axis=1)
+    psi = mlp.assemble_2d(o, rank, px, py, n)
+    assert psi.shape == (2, int(np.prod(n)))
+    assert np.allclose(mlp.project_2d(psi, n, px, py), np.einsum("sra,srb->sab", C, D),
+                       atol=1e-12)
+    # a separable product cos(x1) sin(x2) * cos(2 y1) projects onto exactly one coefficient,
+    # at (a1 q + a2, b1 q + b2) = (1*3 + 2, 3*4 + 0), with the product of the grid norms
+    t = [2.0 * np.pi * np.arange(k) / k - np.pi for k in n]
+    f = np.einsum("i,j,k,l->ijkl", np.cos(t[0]), np.sin(t[1]), np.cos(2 * t[2]),
+                  np.ones(n[3]))
+    T = mlp.project_2d(f.ravel()[None], n, px, py)[0]
+    E = np.zeros((px, py))
+    E[5, 12] = np.sqrt(n[0] / 2 * n[1] / 2 * n[2] / 2 * n[3])
+    assert np.allclose(T, E, atol=1e-12)
+    with pytest.raises(ValueError):
+        mlp.project_2d(psi, n, 8, py)

@@ -59,7 +59,7 @@ constexpr int kBM = 128;       // output rows per CTA (TMEM lanes)
 constexpr int kBN = 48;        // output columns per CTA; kLevels * kBN <= 512 TMEM columns
 constexpr int kBK = 64;        // contraction depth per stage (128-byte rows)
 constexpr int kAStages = 6;  // A tiles in flight: each carries ~600 cycles of MMA work
-constexpr int kBStages = 2;
+constexpr int kBStages = 2;  // a power of two (stage index by mask)
 constexpr int kThreads = 128;
 constexpr uint32_t kATileBytes = kBM * 128;
 constexpr uint32_t kTmemCols = 512;
@@ -222,9 +222,15 @@ __device__ __forceinline__ double pow2i(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// One CTA computes the 128 x kBN tile (m0, n0) of C = A B^T for vector blockIdx.z.
+// One CTA computes the 128 x kBN tile (m0, n0) of C = A B^T for vector blockIdx.z, with
+// SA digit slices of A and SB of B (kLevels levels kept).
 // Warp 0 lane 0 loads (TMA), warp 1 lane 0 issues the MMAs, warp 2 owns the tensor
 // memory, all four warps run the epilogue (warp w reads TMEM lanes 32w .. 32w + 31).
+// The MMA issue loop is fully unrolled over the digit pairs with descriptors formed once
+// per tile: a tcgen05.mma costs the issuing thread about 45 cycles at best, and at
+// N = 48 any per-MMA address or loop arithmetic on that thread's critical path (a
+// runtime-bounded pair loop measured about 150 cycles per MMA) idles the tensor pipe.
+template <int SA, int SB>
 __global__ void __launch_bounds__(kThreads, 1)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const OzArgs g) {
@@ -232,7 +238,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ int abort_flag;
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int SA = g.SA, SB = g.SB, L = g.L;
+  constexpr int L = kLevels;
   const uint32_t bstage = (uint32_t)SB * b_slice_bytes();
   uint8_t *sB = base;
   uint8_t *sA = base + kBStages * bstage;
@@ -307,41 +313,47 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (lastB[i] >= 0) tc::mbar_wait(&fullB[i], (uint32_t)lastB[i], nullptr, 0);
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: level l = i + j of the digit pairs accumulates at column l * kBN
-    const uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
+    // ---- MMA issuer: level l = i + j of the digit pairs accumulates at column l * kBN.
+    // The first MMA of a level (K block 0, its smallest i, k-step 0) overwrites it.
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
+    constexpr uint64_t kSliceStep = b_slice_bytes() >> 4;  // descriptor units (16 bytes)
     bool ok = true;
-    int acount = 0;
-    uint32_t seen = 0;  // levels already written (the first MMA of a level overwrites it)
+    int sa = 0;
+    uint32_t pa = 0;  // A stage and its phase
     for (int kb = 0; kb < KB && ok; ++kb) {
-      const int sb = kb % kBStages;
+      const int sb = kb & (kBStages - 1);
       const uint32_t rb = (uint32_t)(kb / kBStages);
       if (!tc::mbar_wait(&fullB[sb], rb & 1u, g.err, 3)) {
         ok = false;
         break;
       }
       tc::tc_fence_after();
-      const uint32_t bbase = tc::smem_addr(sB + sb * bstage);
-      for (int i = 0; i < SA; ++i, ++acount) {
-        const int sa = acount % kAStages;
-        const uint32_t ra = (uint32_t)(acount / kAStages);
-        if (!tc::mbar_wait(&fullA[sa], ra & 1u, g.err, 4)) {
+      const uint64_t bdesc = tc::smem_desc_sw128(tc::smem_addr(sB + sb * bstage));
+      const bool later = kb > 0;
+#pragma unroll
+      for (int i = 0; i < SA; ++i) {
+        if (!tc::mbar_wait(&fullA[sa], pa, g.err, 4)) {
           ok = false;
           break;
         }
         tc::tc_fence_after();
-        const uint32_t abase = tc::smem_addr(sA + sa * kATileBytes);
-        for (int j = 0; j < SB && i + j < L; ++j) {
-          const int l = i + j;
-          const uint32_t d = tmem + (uint32_t)(l * kBN);
-          const uint32_t fresh = ((seen >> l) & 1u) ^ 1u;
+        const uint64_t adesc = tc::smem_desc_sw128(tc::smem_addr(sA + sa * kATileBytes));
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk)
-            tc::mma_bf16(d, tc::smem_desc_sw128(abase + kk * 32),
-                         tc::smem_desc_sw128(bbase + j * b_slice_bytes() + kk * 32), idesc,
-                         (kk == 0 && fresh) ? 0u : 1u);
-          seen |= 1u << l;
+        for (int j = 0; j < SB; ++j) {
+          if (i + j < L) {
+            const bool first = i == (i + j >= SB ? i + j - SB + 1 : 0);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+              tc::mma_bf16(tmem + (uint32_t)((i + j) * kBN), adesc + (uint64_t)(2 * kk),
+                           bdesc + (uint64_t)j * kSliceStep + (uint64_t)(2 * kk), idesc,
+                           (later || kk > 0 || !first) ? 1u : 0u);
+          }
         }
         tc::mma_commit(&emptyA[sa]);  // the A stage is free once these MMAs are done
+        if (++sa == kAStages) {
+          sa = 0;
+          pa ^= 1u;
+        }
       }
       if (ok) tc::mma_commit(&emptyB[sb]);
     }
@@ -470,13 +482,23 @@ cudaError_t launch_oz(const CUtensorMap &mA, const CUtensorMap &mB, const OzArgs
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)oz_smem_bytes(kMaxSlices));
+    const int bytes = (int)oz_smem_bytes(kMaxSlices);
+    attr = cudaFuncSetAttribute(k_oz_gemm<kOpSlices, kPsiSlices>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_oz_gemm<kPsiSlices, kOpSlices>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   });
   if (attr != cudaSuccess) return attr;
+  if (g.L != kLevels) return cudaErrorInvalidValue;
   const dim3 grid((g.M + kBM - 1) / kBM, (g.N + kBN - 1) / kBN, nvec);
   count_launch();
-  k_oz_gemm<<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
+  if (g.SA == kOpSlices && g.SB == kPsiSlices)
+    k_oz_gemm<kOpSlices, kPsiSlices><<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
+  else if (g.SA == kPsiSlices && g.SB == kOpSlices)
+    k_oz_gemm<kPsiSlices, kOpSlices><<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -44,8 +44,7 @@ TC_PAIRS = 54
 # DRAM bytes (read + write) per launch of each kernel, mean over the launches captured by
 # ncu (profiles/k_update_k_gram_1d_n512.md, profiles/k_oz_gemm_1d_n512.md); a kernel that
 # changes after its capture is removed from this table
-TRAFFIC_BYTES_PER_LAUNCH = {"k_update": 42.12e6, "k_gram": 42.13e6, "k_oz_gemm": 62.6e6,
-                            "k_tf32_gemm": 5.07e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_gram": 42.13e6, "k_tf32_gemm": 5.07e6}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
 
 
@@ -424,7 +423,10 @@ def run_ours(args):
             "fp64_equivalent_tflops": h_fl / (h_ms / 1000.0) / 1e12,
             "launches": tot("h_launches"), "share": h_ms / 1000.0 / step_s}
     for key, f, what in (("k_gram", "gram", "FP64 Gram products A^T B (one launch, split rows)"),
-                         ("k_update", "upd", "FP64 block updates C = bC + a A Y")):
+                         ("k_update", "upd", "FP64-accurate block updates C = bC + a A Y: "
+                          "digit-split BF16 products (k_update_split, mma.sync) for blocks of "
+                          ">= 1e5 rows, FP64 FMA (k_update) below; rate in FP64-equivalent "
+                          "FLOP/s against the FP64 pipe the FMA form is bound by")):
         # every 4th launch is timed (stats doc): rates from the timed ones, the share of
         # the step scaled up to all launches
         ms, fl, by = tot(f + "_ms"), tot(f + "_flops"), tot(f + "_bytes")

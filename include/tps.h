@@ -202,6 +202,11 @@ typedef struct tps_solver_opts {
                          solve (projectors, GMRES Arnoldi), which is solved to inner_tol and
                          whose result is orthonormalised in FP64 before it enters the basis:
                          TPS_F32 (default) or TPS_F64 */
+  int update_dtype;   /* arithmetic of the FP64 block updates of the outer iteration (Ritz
+                         vectors, restarts, orthogonalisation; the Cholesky-QR product stays
+                         on the FMA pipe): TPS_F64_TC (default: digit-split products on the
+                         tensor cores, tps_block_update_tc, for blocks of 10^5 rows or more
+                         and p >= 8; smaller ones on the FMA pipe) or TPS_F64 (FMA pipe) */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -296,6 +301,16 @@ int tps_gram(tps_ctx *ctx, const double *A_dev, long long lda, int p, const doub
 int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *Y_dev,
                      int ldy, int q, double beta, double *C_dev, long long ldc, long long nrows,
                      cudaStream_t stream);
+
+/* The same block update, FP64-accurate, computed as digit-split BF16 products on the
+ * tensor cores (the Ozaki scheme; the solver's default for its FP64 updates): each row of A
+ * and each column of Y is scaled by a power of two and cut into nine 6-bit digits, the
+ * digit pairs of nine or fewer levels are multiplied exactly and combined in integer
+ * arithmetic.  Error per entry at most about 2^-53 max_k |A[r][k]| sum_k |Y[k][j]|.  Same
+ * arguments, limits and errors as tps_block_update. */
+int tps_block_update_tc(tps_ctx *ctx, const double *A_dev, long long lda, int p,
+                        const double *Y_dev, int ldy, int q, double beta, double *C_dev,
+                        long long ldc, long long nrows, cudaStream_t stream);
 
 /* Orthonormalise the block T (b <= 32 columns) against the orthonormal block Q
  * (nq columns, may be 0) and within itself: two passes of block classical

@@ -756,6 +756,19 @@ int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, co
   return TPS_OK;
 }
 
+int tps_block_update_tc(tps_ctx *ctx, const double *A_dev, long long lda, int p,
+                        const double *Y_dev, int ldy, int q, double beta, double *C_dev,
+                        long long ldc, long long nrows, cudaStream_t stream) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  if (p < 0 || q < 1 || p > 64 || q > 64 || nrows < 0 || lda < nrows || ldc < nrows || ldy < p ||
+      !C_dev || (p > 0 && (!A_dev || !Y_dev)))
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "bad block_update arguments");
+  launch_update_split(A_dev, lda, 0, p, Y_dev, ldy, 0, q, 1.0, beta, C_dev, ldc, 0, nrows, 1,
+                      stream);
+  TPS_CUDA_TRY(ctx, cudaGetLastError());
+  return TPS_OK;
+}
+
 int tps_small_eigh(tps_ctx *ctx, const double *G_dev, int m, int ldg, double *theta_dev,
                    double *Y_dev, int ldy, cudaStream_t stream) {
   if (!ctx) return TPS_ERR_INVALID_ARG;

@@ -133,6 +133,7 @@ void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
 
 // Timers of the running solve (tps_solver_opts.timing), for the skinny-kernel wrappers.
 thread_local PhaseTiming *tl_timing = nullptr;
+thread_local bool tl_split_updates = false;  // FP64 updates as digit-split tensor-core products
 
 // launch_gram / launch_update with CUDA-event timing and algorithmic work counts
 // low: FP32-arithmetic products (the correction equation's); like conditional launches
@@ -163,7 +164,7 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
 void tupdate(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
              long long bsy, int q, double alpha, double beta, double *C, long long ldc,
              long long bsc, long long nrows, int batch, cudaStream_t s,
-             const int *need = nullptr, bool low = false) {
+             const int *need = nullptr, bool low = false, bool split_ok = true) {
   PhaseTiming *t = tl_timing;
   const bool live = !need && !low && t && t->on && p > 0 && q > 0 && batch > 0 && nrows > 0;
   if (live) t->launches[4] += 1;
@@ -174,8 +175,14 @@ void tupdate(const double *A, long long lda, long long bsa, int p, const double 
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s, need,
-                low);
+  // the split pays on tall blocks: at the sweep's sizes (n <= 384, fewer than 10^5 rows
+  // per sector) its fixed per-row work made the 256-instance sweep 7 % slower than FMA
+  if (!low && split_ok && tl_split_updates && nrows * batch >= 100000 && p >= 8)
+    launch_update_split(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s,
+                        need);
+  else
+    launch_update(A, lda, bsa, p, Y, ldy, bsy, q, alpha, beta, C, ldc, bsc, nrows, batch, s, need,
+                  low);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[4].push_back({a, b});
@@ -296,7 +303,11 @@ int orthonormalize(Ctx &c, const double *B1, int nb1, const double *B2, int nb2,
     tgram(T, c.N, 0, b, T, c.N, 0, b, c.N, w.C, b, 0, 1, c.ctx->gscr, c.s);
     launch_chol_inv(w.C, b, pass == 0 ? w.ref : nullptr, pass == 0 ? 1e-7 : 1e-12, w.Rinv,
                     w.keep, c.s);
-    tupdate(T, c.N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, c.N, 0, c.N, 1, c.s);
+    // T Rinv stays on the FMA pipe: T's columns can differ in norm by many orders (nearly
+    // dependent directions), which a row-scaled digit split would resolve only relative to
+    // the largest column of each row
+    tupdate(T, c.N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, c.N, 0, c.N, 1, c.s, nullptr, false,
+            false);
     TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(T, w.T2, (size_t)b * c.N * sizeof(double),
                                         cudaMemcpyDeviceToDevice, c.s));
     if (pass == 0) {
@@ -566,9 +577,15 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 8 * sizeof(int), s));
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
   struct TimingScope {
-    explicit TimingScope(PhaseTiming *t) { tl_timing = t; }
-    ~TimingScope() { tl_timing = nullptr; }
-  } timing_scope(&w.tm);
+    explicit TimingScope(PhaseTiming *t, bool split) {
+      tl_timing = t;
+      tl_split_updates = split;
+    }
+    ~TimingScope() {
+      tl_timing = nullptr;
+      tl_split_updates = false;
+    }
+  } timing_scope(&w.tm, opts.update_dtype == TPS_F64_TC);
   // the TF32 tensor-core preconditioner exists for the 1D operator; 2D solves use FP32
   w.prec_dtype = opts.prec_dtype == TPS_F64
                      ? TPS_F64
@@ -933,6 +950,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->smooth_start = 2;
   o->prec_dtype = TPS_TF32_TC;  // 1D; 2D solves use TPS_F32
   o->correction_dtype = TPS_F32;
+  o->update_dtype = TPS_F64_TC;
   o->h_dtype = TPS_F64;
   o->switch_tol = 1e-6;
   o->refine_block = 0;

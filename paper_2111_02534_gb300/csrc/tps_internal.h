@@ -116,6 +116,12 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
                    long long bsc, long long nrows, int batch, cudaStream_t s,
                    const int *need = nullptr, bool low = false);
+// The same update, FP64-accurate, as digit-split BF16 products on the tensor cores
+// (update_mma.cu); q any, p any (slabs of 64).
+void launch_update_split(const double *A, long long lda, long long bsa, int p, const double *Y,
+                         int ldy, long long bsy, int q, double alpha, double beta, double *C,
+                         long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,
+                         const int *need = nullptr);
 // out[c] = squared 2-norm of column c (ld lda, nrows rows), c < ncols; uses scr.
 void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
                        GramScratch &scr, cudaStream_t s);

@@ -48,7 +48,8 @@ class SolverOpts(C.Structure):
                 ("refine_inner_steps", C.c_int), ("refine_inner_dtype", C.c_int),
                 ("h64_dtype", C.c_int), ("rr_method", C.c_int),
                 ("rr_refine_max", C.c_int),
-                ("correction_dtype", C.c_int)]
+                ("correction_dtype", C.c_int),
+                ("update_dtype", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -102,6 +103,8 @@ _sig = {
     "tps_gram": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
     "tps_block_update": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, C.c_int, C.c_int, C.c_double,
                                    _vp, _ll, _ll, _vp]),
+    "tps_block_update_tc": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, C.c_int, C.c_int, C.c_double,
+                                      _vp, _ll, _ll, _vp]),
     "tps_orthonormalize": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _ip, _vp]),
     "tps_small_eigh": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp]),
     "tps_correction": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int,
@@ -287,9 +290,11 @@ class Context:
         self._check(_lib.tps_gram(self._h, _ptr(A), lda or nrows, p, _ptr(B), ldb or nrows, q,
                                   nrows, _ptr(G), ldg or p, _stream(stream)), "gram")
 
-    def block_update(self, A, p, Y, q, beta, Cm, nrows, ldy=None, stream=None):
-        self._check(_lib.tps_block_update(self._h, _ptr(A), nrows, p, _ptr(Y), ldy or p, q, beta,
-                                          _ptr(Cm), nrows, nrows, _stream(stream)), "block_update")
+    def block_update(self, A, p, Y, q, beta, Cm, nrows, ldy=None, stream=None, dtype=F64):
+        """C = beta C + A Y; dtype F64 (FMA pipe) or F64_TC (digit-split tensor-core products)."""
+        fn = _lib.tps_block_update_tc if dtype == F64_TC else _lib.tps_block_update
+        self._check(fn(self._h, _ptr(A), nrows, p, _ptr(Y), ldy or p, q, beta, _ptr(Cm), nrows,
+                       nrows, _stream(stream)), "block_update")
 
     def orthonormalize(self, Q, nq, T, b, nrows, stream=None):
         rank = C.c_int()

@@ -42,20 +42,44 @@ def test_gram(ctx, nrows, p, q):
                                             # column tiles 1, 2, 4 (ragged), 8, 8 + 1
                                             (40001, 11, 1, 1.0), (3001, 5, 2, 0.0),
                                             (131584, 32, 5, -1.0), (20003, 9, 9, 0.5)])
-def test_block_update(ctx, nrows, p, q, beta):
+@pytest.mark.parametrize("dtype", ["f64", "f64_tc"])
+def test_block_update(ctx, nrows, p, q, beta, dtype):
+    from paper_2111_02534_gb300 import tps
+    dt = tps.F64_TC if dtype == "f64_tc" else tps.F64
     A = random_block(max(p, 1), nrows, 3)[:p]
     Y = np.random.default_rng(4).standard_normal((p, q))
     C0 = random_block(q, nrows, 5)
     Cd = dev(C0)
     if p > 64:
-        from paper_2111_02534_gb300 import tps
         with pytest.raises(tps.TpsError):
-            ctx.block_update(dev(A), p, dev(Y.T.copy()), q, beta, Cd, nrows)
+            ctx.block_update(dev(A), p, dev(Y.T.copy()), q, beta, Cd, nrows, dtype=dt)
         return
     ctx.block_update(dev(A) if p else None, p, dev(Y.T.copy()) if p else None, q, beta, Cd, nrows,
-                     ldy=max(p, 1))
+                     ldy=max(p, 1), dtype=dt)
     ref = beta * C0 + (Y.T @ A if p else 0.0)
     assert np.max(np.abs(host(Cd) - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nrows,p,q", [(70001, 48, 8), (4099, 64, 13), (1000, 17, 3)])
+def test_block_update_tc_graded(ctx, nrows, p, q):
+    # digit-split update on data spanning many binades: rows scaled over 1e-12 .. 1e12,
+    # entries within a row over 1e-6 .. 1, Y columns over 1e-8 .. 1e8, exact zeros; the
+    # bound per entry is the scheme's, 2^-53 max_k |A[r][k]| sum_k |Y[k][j]| (with slack 4),
+    # plus the worst-case rounding of the FP64 reference, p 2^-53 sum_k |Y[k][j] A[r][k]|
+    from paper_2111_02534_gb300 import tps
+    rng = np.random.default_rng(nrows)
+    A = rng.standard_normal((p, nrows)) * 10.0 ** rng.uniform(-6, 0, (p, nrows))
+    A *= 10.0 ** rng.uniform(-12, 12, nrows)[None, :]
+    A[:, ::97] = 0.0
+    Y = rng.standard_normal((p, q)) * 10.0 ** rng.uniform(-8, 8, q)[None, :]
+    Cd = dev(np.zeros((q, nrows)))
+    ctx.block_update(dev(A), p, dev(Y.T.copy()), q, 0.0, Cd, nrows, ldy=p, dtype=tps.F64_TC)
+    got = host(Cd)
+    ref = Y.T @ A
+    bound = 4 * 2.0 ** -53 * np.outer(np.abs(Y).sum(axis=0), np.abs(A).max(axis=0))
+    bound += p * 2.0 ** -53 * (np.abs(Y).T @ np.abs(A))
+    assert np.all(np.abs(got - ref) <= bound + 1e-300)
+    assert np.all(got[:, ::97] == 0.0)
 
 
 @pytest.mark.parametrize("m,kind", [(1, "rand"), (2, "rand"), (7, "rand"), (32, "rand"),

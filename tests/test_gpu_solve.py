@@ -354,3 +354,37 @@ def test_correction_products_fp32_and_fp64_agree_full_size():
         applies[cd] = st.h_applies
     assert applies[tps.F32] <= 1.25 * applies[tps.F64], applies
     ctx.close()
+
+
+@pytest.mark.parametrize("parity", [0, 1, 2])
+def test_split_updates_brute_force_small(parity):
+    # the outer iteration's block updates as digit-split tensor-core products
+    # (update_dtype = F64_TC): eigenvalues of a 16 x 16 problem against dense brute force
+    require_gpu()
+    tps = _tps()
+    n, L = (16, 16), (6.0, 6.0)
+    P = problem_1d(20.0, 1.0, 1.0, n, L, 1.0, 1.0)
+    ctx = make_ctx_1d(20.0, 1.0, n, L, 1.0, 1.0)
+    lam, X, st = _solve(ctx, 5, parity, 3, update_dtype=tps.F64_TC)
+    full = all_eigenvalues_dense(P, [O_ANY, O_EVEN, O_ODD][parity])
+    assert np.max(np.abs(lam - full[:5]) / np.abs(full[:5])) <= 1e-10
+    _check_vectors(P, lam, X, parity_sign=[None, 1.0, -1.0][parity])
+    ctx.close()
+
+
+def test_split_updates_full_size():
+    # update_dtype = F64_TC on the 1d_n512 workload: the same certified eigenpairs
+    require_gpu()
+    tps = _tps()
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, gold["v0"], w.sigma)
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, gold["v0"], w.sigma)
+    ref = np.array(gold["evals"])
+    lam, X, st = _solve(ctx, w.k, tps.X_EVEN, w.block, update_dtype=tps.F64_TC)
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+    res = _check_vectors(P, lam, X, parity_sign=1.0)
+    weyl, kt = certify(lam, res, ref)
+    assert np.all(kt <= 1e-12 * np.abs(lam))
+    ctx.close()

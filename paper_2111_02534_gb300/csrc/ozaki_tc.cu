@@ -209,7 +209,8 @@ struct OzArgs {
   long long expB_bs;
   double *out;                   // out[v * out_bs + n * ldo + m]
   long long ldo, out_bs;
-  int epi;                       // 0 store, 1 accumulate, 2 store + (V - theta_v) psi
+  int epi;                       // 0 store, 1 accumulate, 2 store + (V - theta_v) psi,
+                                 // 3 atomic add, 4 atomic add with (V - theta_v) psi
   const double *V;               // [n * ldo + m]
   const double *psi;             // psi[v * out_bs + n * ldo + m]
   const double *theta_dev;       // theta_v (null: theta0)
@@ -231,11 +232,11 @@ __device__ __forceinline__ double pow2i(int e) {
 // N = 48 any per-MMA address or loop arithmetic on that thread's critical path (a
 // runtime-bounded pair loop measured about 150 cycles per MMA) idles the tensor pipe.
 template <int SA, int SB>
-__global__ void __launch_bounds__(kThreads, 1)
-k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const OzArgs g) {
-  extern __shared__ uint8_t smem_raw[];
+__device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorMap *tmBp,
+                                        const OzArgs &g, int m0, int n0, int v,
+                                        uint8_t *smem_raw) {
   __shared__ int abort_flag;
+  const CUtensorMap &tmA = *tmAp, &tmB = *tmBp;
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int L = kLevels;
@@ -249,7 +250,6 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   uint32_t *holder = reinterpret_cast<uint32_t *>(accum + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, v = blockIdx.z;
   const int KB = (g.K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
@@ -373,7 +373,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const bool mvalid = m < g.M;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
     const int Em = mvalid ? (int)g.expA[v * g.expA_bs + m] - 1022 : 0;
-    const double th = (g.epi == 2) ? (g.theta_dev ? g.theta_dev[v] : g.theta0) : 0.0;
+    const bool vterm = g.epi == 2 || g.epi == 4;
+    const double th = vterm ? (g.theta_dev ? g.theta_dev[v] : g.theta0) : 0.0;
     const int h = (L + 1) / 2;
     for (int c = 0; c < kBN / 8; ++c) {
       long long hi[8], lo[8];
@@ -408,18 +409,43 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                                (double)hi[q] * pow2i(Em + En - kBeta * (h + 1)));
         const long long idx = (long long)n * g.ldo + m;
         double *o = g.out + v * g.out_bs + idx;
-        if (g.epi == 0)
-          *o = val;
+        const double add = vterm ? fma(g.V[idx] - th, g.psi[v * g.out_bs + idx], val) : val;
+        if (g.epi == 0 || g.epi == 2)
+          *o = add;
         else if (g.epi == 1)
-          *o += val;
+          *o += add;
         else
-          *o = fma(g.V[idx] - th, g.psi[v * g.out_bs + idx], val);
+          atomicAdd(o, add);  // epi 3, 4: one of exactly two terms added to a zeroed output
       }
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 2) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Both products of the 1D H-apply in one launch: CTAs [0, T) compute tiles of
+// C1 = K_y P^T (+ (V - theta) P), CTAs [T, 2T) tiles of C2 = P^T K_x^T, T = tiles x vectors,
+// m fastest, then n, then the vector.  Each adds its tile to the zeroed output with an
+// FP64 atomic: the two terms of an element are added to 0 in either order with the same
+// result (0 + a is exact, and a + b = b + a), so the sum is deterministic.  One launch of
+// 2T CTAs packs onto the SMs better than two of T each (T = 192 on 152 SMs at n = 512:
+// each launch's second wave ran a quarter full).
+__global__ void __launch_bounds__(kThreads, 1)
+k_oz_gemm(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
+          const __grid_constant__ OzArgs g1, const __grid_constant__ CUtensorMap tmA2,
+          const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ OzArgs g2) {
+  extern __shared__ uint8_t smem_raw[];
+  const int tm = (g1.M + kBM - 1) / kBM, tn = (g1.N + kBN - 1) / kBN;
+  const int per = (int)(gridDim.x >> 1);
+  const bool second = (int)blockIdx.x >= per;
+  const int r = (int)blockIdx.x - (second ? per : 0);
+  const int v = r / (tm * tn), t = r % (tm * tn);
+  const int m0 = (t % tm) * kBM, n0 = (t / tm) * kBN;
+  if (!second)
+    oz_tile<kOpSlices, kPsiSlices>(&tmA1, &tmB1, g1, m0, n0, v, smem_raw);
+  else
+    oz_tile<kPsiSlices, kOpSlices>(&tmA2, &tmB2, g2, m0, n0, v, smem_raw);
 }
 
 
@@ -477,28 +503,27 @@ void launch_split(const double *X, int R, int C, long long bs, int batch, int S,
                                                           outT, ldt);
 }
 
-cudaError_t launch_oz(const CUtensorMap &mA, const CUtensorMap &mB, const OzArgs &g, int nvec,
-                      cudaStream_t s) {
+// The two products of the H-apply (pass 1: A = K_y slices, B = psi slices; pass 2: A =
+// psi^T slices, B = K_x slices), same output tiling, into an output zeroed beforehand.
+cudaError_t launch_oz_pair(const CUtensorMap &mA1, const CUtensorMap &mB1, const OzArgs &g1,
+                           const CUtensorMap &mA2, const CUtensorMap &mB2, const OzArgs &g2,
+                           int nvec, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    const int bytes = (int)oz_smem_bytes(kMaxSlices);
-    attr = cudaFuncSetAttribute(k_oz_gemm<kOpSlices, kPsiSlices>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(k_oz_gemm<kPsiSlices, kOpSlices>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oz_smem_bytes(kMaxSlices));
   });
   if (attr != cudaSuccess) return attr;
-  if (g.L != kLevels) return cudaErrorInvalidValue;
-  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + kBN - 1) / kBN, nvec);
-  count_launch();
-  if (g.SA == kOpSlices && g.SB == kPsiSlices)
-    k_oz_gemm<kOpSlices, kPsiSlices><<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
-  else if (g.SA == kPsiSlices && g.SB == kOpSlices)
-    k_oz_gemm<kPsiSlices, kOpSlices><<<grid, kThreads, oz_smem_bytes(g.SB), s>>>(mA, mB, g);
-  else
+  if (g1.L != kLevels || g2.L != kLevels || g1.SA != kOpSlices || g1.SB != kPsiSlices ||
+      g2.SA != kPsiSlices || g2.SB != kOpSlices || g1.M != g2.M || g1.N != g2.N ||
+      (g1.epi != 3 && g1.epi != 4) || (g2.epi != 3 && g2.epi != 4))
     return cudaErrorInvalidValue;
+  const long long tiles = (long long)((g1.M + kBM - 1) / kBM) * ((g1.N + kBN - 1) / kBN) * nvec;
+  if (2 * tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  count_launch();
+  k_oz_gemm<<<(unsigned)(2 * tiles), kThreads, oz_smem_bytes(kMaxSlices), s>>>(mA1, mB1, g1, mA2,
+                                                                             mB2, g2);
   return cudaGetLastError();
 }
 
@@ -597,6 +622,8 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
     if (e != cudaSuccess) return e;
     launch_exponents(P, nx, ny, op.N, nv, erow, ecol, s);
     launch_split(P, nx, ny, op.N, nv, Sp, erow, t.Pn, t.ldy, ecol, t.PT, t.ldx, s);
+    e = cudaMemsetAsync(O, 0, sizeof(double) * (size_t)nv * op.N, s);
+    if (e != cudaSuccess) return e;
     OzArgs g;
     std::memset(&g, 0, sizeof(g));
     g.L = kLevels;
@@ -616,25 +643,24 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
     g.expA_bs = 0;
     g.expB = erow;
     g.expB_bs = nx;
-    g.epi = 2;
+    g.epi = 4;
     g.V = op.V;
     g.psi = P;
     g.theta_dev = theta_dev ? theta_dev + v0 : nullptr;
     g.theta0 = theta;
-    e = launch_oz(t.mKy, t.mPn, g, nv, s);
-    if (e != cudaSuccess) return e;
-    // P^T K_x^T accumulated: A = psi^T slices, B = K_x slices (shared)
-    g.K = nx;
-    g.SA = Sp;
-    g.SB = So;
-    g.zA = Sp;
-    g.zB = 0;
-    g.expA = ecol;
-    g.expA_bs = ny;
-    g.expB = t.eKx;
-    g.expB_bs = 0;
-    g.epi = 1;
-    e = launch_oz(t.mPT, t.mKx, g, nv, s);
+    // P^T K_x^T: A = psi^T slices, B = K_x slices (shared)
+    OzArgs g2 = g;
+    g2.K = nx;
+    g2.SA = Sp;
+    g2.SB = So;
+    g2.zA = Sp;
+    g2.zB = 0;
+    g2.expA = ecol;
+    g2.expA_bs = ny;
+    g2.expB = t.eKx;
+    g2.expB_bs = 0;
+    g2.epi = 3;
+    e = launch_oz_pair(t.mKy, t.mPn, g, t.mPT, t.mKx, g2, nv, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -24,11 +24,11 @@ namespace {
 // costs ~150 cycles almost whatever its N (measured on the BF16 kernel), so the widest
 // MMA (128 x 256 x 8) does the most work per instruction, and a 512-wide product needs two
 // tiles instead of eight.
-constexpr int kBM = 128, kBNMax = 256, kBK = 32;  // K block: 32 FP32 = one 128-byte row
-constexpr int kStages = 4;
+constexpr int kBM = 128, kBNMax = 128, kBK = 32;  // K block: 32 FP32 = one 128-byte row
+constexpr int kStages = 6;
 constexpr int kThreads = 128;
 constexpr uint32_t kATile = kBM * kBK * 4;        // 16 KB
-constexpr uint32_t kBTileMax = kBNMax * kBK * 4;  // 32 KB
+constexpr uint32_t kBTileMax = kBNMax * kBK * 4;  // 16 KB
 constexpr int kTmemCols = 256;
 constexpr size_t kSmemBytes = 1024 + kStages * (kATile + kBTileMax) + 256;
 
@@ -297,8 +297,14 @@ bool make_f32_map(CUtensorMap *map, const float *base, int cols, long long rows,
 int pad4(int n) { return (n + 3) & ~3; }
 
 // tile width for N columns: as few tiles of at most 256 as possible, each a multiple of 16
-int tile_n(int N) {
-  const int tiles = (N + kBNMax - 1) / kBNMax;
+// Output tile width for N columns when the M side has mtiles tiles: the fewest tiles of at
+// most kBNMax columns, then more (narrower, down to about 64 columns) tiles while all of
+// them fit in one wave on the 152 SMs.  The passes are latency-bound (a short K loop per
+// CTA), so spreading a pass over more SMs shortens it; below 64 columns an MMA costs as
+// much as at 64 (about 45 issue cycles), so narrower tiles would only add MMAs.
+int tile_n(int N, int mtiles) {
+  int tiles = (N + kBNMax - 1) / kBNMax;
+  while (tiles + 1 <= (N + 63) / 64 && (long long)(tiles + 1) * mtiles <= 152) ++tiles;
   const int bn = (N + tiles - 1) / tiles;
   return (bn + 15) & ~15;
 }
@@ -345,8 +351,9 @@ int ensure_tf_operator(const DevOperator &op) {
   t->ny = op.n[1];
   t->XP = pad4(t->nx);
   t->YP = pad4(t->ny);
-  t->BNx = tile_n(t->nx);
-  t->BNy = tile_n(t->ny);
+  // tiles sized for blocks of 8 vectors (the solver's usual block); other counts work too
+  t->BNx = tile_n(t->nx, (8 * t->ny + kBM - 1) / kBM);
+  t->BNy = tile_n(t->ny, (8 * t->nx + kBM - 1) / kBM);
   const size_t fx = (size_t)t->nx * t->XP, fy = (size_t)t->ny * t->YP;
   if (cudaMalloc((void **)&t->Sx, (2 * fx + 2 * fy) * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void **)&t->err, sizeof(int)) != cudaSuccess ||

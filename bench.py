@@ -45,7 +45,8 @@ TC_PAIRS = 54
 # ncu (profiles/k_update_split_1d_n512.md, profiles/k_update_k_gram_1d_n512.md,
 # profiles/k_oz_gemm_1d_n512.md, profiles/k_tf32_gemm_1d_n512.md); a kernel that changes
 # after its capture is removed from this table
-TRAFFIC_BYTES_PER_LAUNCH = {"k_update": 37.93e6, "k_gram": 42.13e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_update": 37.93e6, "k_gram": 42.13e6, "k_oz_gemm": 49.35e6,
+                            "k_tf32_gemm": 5.08e6}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
 
 

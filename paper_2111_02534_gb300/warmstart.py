@@ -144,7 +144,7 @@ def homotopy_solve(ctx, inst, k, block, tol, ev, step=HOMOTOPY_STEP, timed=True)
 def evaluate(model, instances, k, block=None, tol=1e-12, device=0, homotopy=True):
     """Cold start, learned warm start and (homotopy=True) the homotopy start on each
     instance: outer iterations, H applications (MVMs, the paper's Table 2 count), solve
-    time and the largest relative eigenvalue difference to the cold solve (the tests judge
+    time and the largest relative eigenvalue difference to the cold solve (the tests check
     the eigenpairs with the oracle)."""
     import torch
     block = block or k

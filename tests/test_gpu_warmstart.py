@@ -2,7 +2,7 @@
 projection, prediction) against the CPU oracle (oracle/mlp.py), and a test of what the
 trained network gains: fewer H applications than the cold-started solver on unseen
 instances (H applications, the paper's MVM count), with the same eigenvalues (the
-oracle's residual as judge).
+oracle's residual as the check).
 
 Tolerances from the arithmetic: FP32 forward through three 256-wide layers, ~1e-6
 relative per layer -> 1e-5 on outputs; gradients 1e-4 relative (FP32 sums over the
@@ -218,7 +218,7 @@ def test_trained_network_beats_cold_start():
         assert all(r["used_warm"] for r in rows)
         assert max(r["rel_diff"] for r in rows) <= 1e-10
         assert warm < frac * cold, (n, warm, cold)
-    # the oracle's residual judges one warm-started solution
+    # the oracle's residual checks one warm-started solution
     inst = test_set[0]
     ctx, v0 = warmstart.make_context(inst)
     ev = torch.empty(4, ctx.info()[0], dtype=torch.float64, device="cuda")
@@ -234,7 +234,7 @@ def test_trained_network_beats_cold_start():
 def test_homotopy_start_saves_h_applications():
     # the non-learned baseline: the previous point of a decreasing-E0 sweep (E0 x 1.25,
     # same M/m, sigma and grid) starts the instance's solve; fewer H applications than a
-    # cold start, eigenvalues equal to the cold ones to 1e-10, the oracle's residual as judge
+    # cold start, eigenvalues equal to the cold ones to 1e-10, the oracle's residual as the check
     require_gpu()
     from paper_2111_02534_gb300 import tps, warmstart
     from paper_2111_02534_gb300.inputs import warmstart_instances

@@ -68,7 +68,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
-    ap.add_argument("--sweep-streams", type=int, default=16)
+    ap.add_argument("--sweep-streams", type=int, default=32)
     return ap.parse_args()
 
 

@@ -150,6 +150,19 @@ k_update_split(const double *__restrict__ A, long long lda, long long bsa, int p
   for (long long blk = (long long)blockIdx.x * 4 + warp; blk < nblk; blk += (long long)gridDim.x * 4) {
     const long long ra = blk * 16 + g, rb = ra + 8;
     const bool va = ra < nrows, vb = rb < nrows;
+    {
+      // the warp's next 16-row block into L1 while this one is split and multiplied (the
+      // kernel is bound by load latency): rows r and r + 8 share a 128-byte line
+      const long long nr = ra + (long long)gridDim.x * 64;
+      if (nr < nrows)
+        for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
+            if (k < p)
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(As + (long long)k * lda + nr));
+          }
+    }
     // row exponents: the thread's k values of rows ra and rb, then across the quad
     unsigned ea = 0, eb = 0;
     for (int kt = 0; kt < KT; ++kt)

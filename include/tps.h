@@ -128,6 +128,16 @@ int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma);
 int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, double sigma,
                     int n, double L, double *v0_out);
 
+/* Sec. 3.1, the paper's own discretisation of one coordinate: collocation on the n roots
+ * of the Chebyshev polynomial T_n, t_j = -cos(pi (j + 1/2) / n) (ascending), mapped to the
+ * real line by the algebraic map y = L t / sqrt(1 - t^2), and the second-derivative
+ * matrix there, D2 = diag((dt/dy)^2) D D + diag(d^2t/dy^2) D with D the derivative of the
+ * polynomial interpolant on the roots (dense and non-symmetric).  Host-side setup
+ * computation: writes y_host[n] and D2_host[n * n] (row-major); 2 <= n <= 1024, L > 0,
+ * else TPS_ERR_INVALID_ARG.  (The solver works on the periodic Fourier grid; this is the
+ * operator construction for the paper's grid.) */
+int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host);
+
 /* Tile autotuning of the mode-product GEMMs (on by default, process-wide): the first
  * launch of each GEMM shape times the candidate tile shapes on the caller's stream (which
  * adds a host synchronisation to that first call) and later launches use the fastest.

@@ -548,6 +548,38 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est) {
   return TPS_OK;
 }
 
+int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host) {
+  if (n < 2 || n > 1024 || !(L > 0) || !y_host || !D2_host) return TPS_ERR_INVALID_ARG;
+  // roots of T_n: t_j = cos(theta_j), theta_j = pi - pi (j + 1/2) / n, so 1 - t_j^2 = s_j^2
+  // with s_j = sin(pi (j + 1/2) / n) > 0
+  std::vector<double> t(n), sn(n), D((size_t)n * n), DD((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    const double a = kPi * (j + 0.5) / n;
+    t[j] = -std::cos(a);
+    sn[j] = std::sin(a);
+    y_host[j] = L * t[j] / sn[j];
+  }
+  // derivative of the interpolant on first-kind Chebyshev points, closed form:
+  // D_ij = (-1)^(i+j) (s_j / s_i) / (t_i - t_j), D_ii = t_i / (2 s_i^2)
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      D[(size_t)i * n + j] = (i == j) ? t[i] / (2.0 * sn[i] * sn[i])
+                                      : (((i + j) & 1) ? -1.0 : 1.0) * (sn[j] / sn[i]) / (t[i] - t[j]);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const double dik = D[(size_t)i * n + k];
+      for (int j = 0; j < n; ++j) DD[(size_t)i * n + j] += dik * D[(size_t)k * n + j];
+    }
+  // chain rule: dt/dy = s^3 / L, d^2t/dy^2 = -3 t s^4 / L^2
+  for (int i = 0; i < n; ++i) {
+    const double s2 = sn[i] * sn[i];
+    const double tp = s2 * sn[i] / L, tpp = -3.0 * t[i] * s2 * s2 / (L * L);
+    for (int j = 0; j < n; ++j)
+      D2_host[(size_t)i * n + j] = tp * tp * DD[(size_t)i * n + j] + tpp * D[(size_t)i * n + j];
+  }
+  return TPS_OK;
+}
+
 int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, double sigma, int n,
                     double L, double *v0_out) {
   if ((dim != 1 && dim != 2) || !(mu_hl > 0) || !(hbar > 0) || !(E0 > 0) || !(sigma > 0) ||

@@ -93,6 +93,7 @@ _sig = {
     "tps_set_pair_potential": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
     "tps_two_body_v0": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                   C.c_double, C.c_int, C.c_double, _dp]),
+    "tps_chebyshev_grid": (C.c_int, [C.c_int, C.c_double, _dp, _dp]),
     "tps_get_info": (C.c_int, [_vp, C.POINTER(_ll), _dp]),
     "tps_set_autotune": (C.c_int, [C.c_int]),
     "tps_apply_h": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
@@ -199,6 +200,16 @@ def two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L) -> float:
     if st != OK:
         raise TpsError(st, "tps_two_body_v0")
     return out.value
+
+
+def chebyshev_grid(n, L):
+    """tps_chebyshev_grid: (y [n], D2 [n, n]) of the paper's mapped Chebyshev grid."""
+    y = np.empty(n)
+    D2 = np.empty((n, n))
+    st = _lib.tps_chebyshev_grid(n, L, y.ctypes.data_as(_dp), D2.ctypes.data_as(_dp))
+    if st != OK:
+        raise TpsError(st, "tps_chebyshev_grid")
+    return y, D2
 
 
 class Context:

@@ -1,6 +1,7 @@
 """The library's host-side construction of the paper's mapped Chebyshev grid
 (tps_chebyshev_grid, C++) against the oracle's (oracle/chebyshev.py, NumPy): the two are
-written independently (the library takes the closed-form diagonal of the derivative matrix, the oracle the negative row sum)."""
+written independently (the library takes the closed-form diagonal of the derivative
+matrix, the oracle the negative row sum)."""
 import numpy as np
 import pytest
 

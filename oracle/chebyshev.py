@@ -116,3 +116,20 @@ def tune_v0(E0: float, mu_hl: float, sigma: float, shape: int, n: int, L: float,
     F = np.diag(shape_function(np.abs(y) / sigma, shape))
     mu = sl.eigvals(sl.solve(T + E0 * np.eye(n), F))
     return float(1.0 / np.max(mu.real))
+
+
+def tune_v0_2d(E0: float, mu_hl: float, sigma: float, shape: int, n: int, L: float,
+               hbar: float = 1.0) -> float:
+    """The 2D two-body depth (Sec. 5.2) on the n x n tensor grid of mapped points: the same
+    generalized problem with T = -hbar^2/(2 mu_hl) (D2 (x) I + I (x) D2) and
+    F = diag f(|xi| / sigma), dense (n^2 unknowns)."""
+    if not E0 > 0:
+        raise ValueError("E0 must be positive")
+    y = mapped_points(n, L)
+    T1 = -(hbar ** 2) / (2.0 * mu_hl) * d2_mapped(n, L)
+    I = np.eye(n)
+    T = np.kron(T1, I) + np.kron(I, T1)
+    Y1, Y2 = np.meshgrid(y, y, indexing="ij")
+    F = np.diag(shape_function(np.sqrt(Y1 ** 2 + Y2 ** 2).ravel() / sigma, shape))
+    mu = sl.eigvals(sl.solve(T + E0 * np.eye(n * n), F))
+    return float(1.0 / np.max(mu.real))

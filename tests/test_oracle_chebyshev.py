@@ -97,3 +97,21 @@ def test_table1_three_body_fermion_ground_state_on_the_mapped_grid():
     B = cb.x_sector_basis(64, 64, -1)
     lam = cb.lowest_eigenvalues(B.T @ H @ B, 1) / r["E0"]
     assert abs(lam[0] - r["fermions"][0]) <= 5e-9
+
+
+def _table3():
+    with open(os.path.join(GOLD, "table3_v0.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("row,key,shape,n,L", [
+    (0, "gauss", GAUSS, 48, 4.0),
+    (0, "lorentz3", 1, 40, 3.0),
+    (1, "gauss", GAUSS, 64, 6.0),
+])
+def test_table3_two_body_depth_2d_on_the_mapped_grid(row, key, shape, n, L):
+    # Table 3 prints v0 to 8 decimals: half a unit of the last digit, plus 1e-9 for the
+    # grid's own convergence (measured: the next larger grids move v0 by less)
+    r = _table3()["rows"][row]
+    v0 = cb.tune_v0_2d(r["E0"], 1.0, 1.0, shape, n, L)
+    assert abs(v0 - r[key]) <= 6e-9

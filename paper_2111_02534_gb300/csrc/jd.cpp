@@ -576,16 +576,17 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   w.tm.reset(opts.timing != 0);
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 8 * sizeof(int), s));
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
-  struct TimingScope {
-    explicit TimingScope(PhaseTiming *t, bool split) {
+  // per-solve thread-local state of tupdate/tgram: the phase timers and the update arithmetic
+  struct SolveScope {
+    explicit SolveScope(PhaseTiming *t, bool split) {
       tl_timing = t;
       tl_split_updates = split;
     }
-    ~TimingScope() {
+    ~SolveScope() {
       tl_timing = nullptr;
       tl_split_updates = false;
     }
-  } timing_scope(&w.tm, opts.update_dtype == TPS_F64_TC);
+  } solve_scope(&w.tm, opts.update_dtype == TPS_F64_TC);
   // the TF32 tensor-core preconditioner exists for the 1D operator; 2D solves use FP32
   w.prec_dtype = opts.prec_dtype == TPS_F64
                      ? TPS_F64

@@ -133,3 +133,29 @@ def tune_v0_2d(E0: float, mu_hl: float, sigma: float, shape: int, n: int, L: flo
     F = np.diag(shape_function(np.sqrt(Y1 ** 2 + Y2 ** 2).ravel() / sigma, shape))
     mu = sl.eigvals(sl.solve(T + E0 * np.eye(n * n), F))
     return float(1.0 / np.max(mu.real))
+
+
+def kinetic_sylvester_solve(a, n, L, theta: float, R: np.ndarray) -> np.ndarray:
+    """The preconditioner of Sec. 4.2 on the mapped grid (V neglected): X with
+    a_x D2_x X + a_y X D2_y^T - theta X = R (R, X: n_x x n_y, x slow), i.e.
+    (a_x D2_x (x) I + a_y I (x) D2_y - theta) vec X = vec R, solved as a Sylvester equation
+    by Bartels-Stewart (scipy.linalg.solve_sylvester), the paper's 1D method (Eq.
+    sylvester_equation)."""
+    A = a[0] * d2_mapped(n[0], L[0]) - theta * np.eye(n[0])
+    B = (a[1] * d2_mapped(n[1], L[1])).T
+    return sl.solve_sylvester(A, B, np.asarray(R, dtype=np.float64).reshape(n[0], n[1]))
+
+
+def kinetic_fast_diag_solve(a, n, L, theta: float, R: np.ndarray) -> np.ndarray:
+    """The same solve by fast diagonalisation, D2_k = S_k diag(lam_k) S_k^-1 (a real
+    spectrum, non-orthogonal S_k): X = S_x [(S_x^-1 R S_y^-T) ./ (a_x lam_x + a_y lam_y -
+    theta)] S_y^T."""
+    lx, Sx = np.linalg.eig(d2_mapped(n[0], L[0]))
+    ly, Sy = np.linalg.eig(d2_mapped(n[1], L[1]))
+    if np.max(np.abs(lx.imag)) > 0 or np.max(np.abs(ly.imag)) > 0:
+        raise ValueError("complex spectrum")
+    lx, Sx, ly, Sy = lx.real, Sx.real, ly.real, Sy.real
+    Rt = np.linalg.solve(Sx, np.asarray(R, dtype=np.float64).reshape(n[0], n[1]))
+    Rt = np.linalg.solve(Sy, Rt.T).T
+    Xt = Rt / (a[0] * lx[:, None] + a[1] * ly[None, :] - theta)
+    return Sx @ Xt @ Sy.T

@@ -115,3 +115,20 @@ def test_table3_two_body_depth_2d_on_the_mapped_grid(row, key, shape, n, L):
     r = _table3()["rows"][row]
     v0 = cb.tune_v0_2d(r["E0"], 1.0, 1.0, shape, n, L)
     assert abs(v0 - r[key]) <= 6e-9
+
+
+def test_kinetic_solves_on_the_mapped_grid():
+    # the Sec. 4.2 preconditioner on the paper's grid: Bartels-Stewart (Sylvester form)
+    # against a dense LU solve of the Kronecker-sum matrix, and the fast diagonalisation
+    # (non-orthogonal eigenbases) against both
+    ax, ay = coefficients_from_alpha(20.0)
+    n, L, theta = (12, 10), (1.5, 3.0), -0.7
+    R = np.random.default_rng(5).standard_normal(n)
+    K = ax * np.kron(cb.d2_mapped(n[0], L[0]), np.eye(n[1]))
+    K += ay * np.kron(np.eye(n[0]), cb.d2_mapped(n[1], L[1]))
+    dense = np.linalg.solve(K - theta * np.eye(n[0] * n[1]), R.ravel()).reshape(n)
+    syl = cb.kinetic_sylvester_solve((ax, ay), n, L, theta, R)
+    fd = cb.kinetic_fast_diag_solve((ax, ay), n, L, theta, R)
+    scale = np.abs(dense).max()
+    assert np.max(np.abs(syl - dense)) <= 1e-12 * scale
+    assert np.max(np.abs(fd - dense)) <= 1e-10 * scale

@@ -134,9 +134,14 @@ int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, do
  * matrix there, D2 = diag((dt/dy)^2) D D + diag(d^2t/dy^2) D with D the derivative of the
  * polynomial interpolant on the roots (dense and non-symmetric).  Host-side setup
  * computation: writes y_host[n] and D2_host[n * n] (row-major); 2 <= n <= 1024, L > 0,
- * else TPS_ERR_INVALID_ARG.  (The solver works on the periodic Fourier grid; this is the
- * operator construction for the paper's grid.) */
-int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host);
+ * else TPS_ERR_INVALID_ARG.  With lam_host, S_host and Sinv_host non-null it also writes
+ * the fast-diagonalisation factors of the Sec. 4.2 preconditioner on this grid,
+ * D2 = S diag(lam) S^-1 (lam ascending, unit columns of S, row-major), from a host QR
+ * eigensolver; TPS_ERR_SINGULAR if D2 has a complex pair or S is singular.  (The solver
+ * works on the periodic Fourier grid; this is the operator construction for the
+ * paper's grid.) */
+int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host, double *lam_host,
+                       double *S_host, double *Sinv_host);
 
 /* Tile autotuning of the mode-product GEMMs (on by default, process-wide): the first
  * launch of each GEMM shape times the candidate tile shapes on the caller's stream (which

@@ -548,8 +548,11 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est) {
   return TPS_OK;
 }
 
-int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host) {
+int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host, double *lam_host,
+                       double *S_host, double *Sinv_host) {
   if (n < 2 || n > 1024 || !(L > 0) || !y_host || !D2_host) return TPS_ERR_INVALID_ARG;
+  const bool factors = lam_host || S_host || Sinv_host;
+  if (factors && !(lam_host && S_host && Sinv_host)) return TPS_ERR_INVALID_ARG;
   // roots of T_n: t_j = cos(theta_j), theta_j = pi - pi (j + 1/2) / n, so 1 - t_j^2 = s_j^2
   // with s_j = sin(pi (j + 1/2) / n) > 0
   std::vector<double> t(n), sn(n), D((size_t)n * n), DD((size_t)n * n, 0.0);
@@ -577,6 +580,7 @@ int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host) {
     for (int j = 0; j < n; ++j)
       D2_host[(size_t)i * n + j] = tp * tp * DD[(size_t)i * n + j] + tpp * D[(size_t)i * n + j];
   }
+  if (factors && real_eig(n, D2_host, lam_host, S_host, Sinv_host) != 0) return TPS_ERR_SINGULAR;
   return TPS_OK;
 }
 

@@ -122,6 +122,10 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
                          int ldy, long long bsy, int q, double alpha, double beta, double *C,
                          long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,
                          const int *need = nullptr);
+// Host: A = S diag(lam) S^-1 for a real n x n row-major A with a real spectrum (ascending
+// lam, unit columns of S; Sinv nullable).  0 on success, 1 for a complex pair or no
+// convergence, 2 for a singular S (host_eig.cpp).
+int real_eig(int n, const double *A, double *lam, double *S, double *Sinv);
 // out[c] = squared 2-norm of column c (ld lda, nrows rows), c < ncols; uses scr.
 void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
                        GramScratch &scr, cudaStream_t s);

@@ -93,7 +93,7 @@ _sig = {
     "tps_set_pair_potential": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
     "tps_two_body_v0": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                   C.c_double, C.c_int, C.c_double, _dp]),
-    "tps_chebyshev_grid": (C.c_int, [C.c_int, C.c_double, _dp, _dp]),
+    "tps_chebyshev_grid": (C.c_int, [C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp]),
     "tps_get_info": (C.c_int, [_vp, C.POINTER(_ll), _dp]),
     "tps_set_autotune": (C.c_int, [C.c_int]),
     "tps_apply_h": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp]),
@@ -202,14 +202,17 @@ def two_body_v0(dim, mu_hl, hbar, E0, shape, sigma, n, L) -> float:
     return out.value
 
 
-def chebyshev_grid(n, L):
-    """tps_chebyshev_grid: (y [n], D2 [n, n]) of the paper's mapped Chebyshev grid."""
+def chebyshev_grid(n, L, factors=False):
+    """tps_chebyshev_grid: (y [n], D2 [n, n]) of the paper's mapped Chebyshev grid, plus
+    (lam [n], S [n, n], Sinv [n, n]) with D2 = S diag(lam) S^-1 when factors is true."""
     y = np.empty(n)
     D2 = np.empty((n, n))
-    st = _lib.tps_chebyshev_grid(n, L, y.ctypes.data_as(_dp), D2.ctypes.data_as(_dp))
+    f = [np.empty(n), np.empty((n, n)), np.empty((n, n))] if factors else [None] * 3
+    ptr = lambda a: a.ctypes.data_as(_dp) if a is not None else None
+    st = _lib.tps_chebyshev_grid(n, L, ptr(y), ptr(D2), *[ptr(a) for a in f])
     if st != OK:
         raise TpsError(st, "tps_chebyshev_grid")
-    return y, D2
+    return (y, D2, *f) if factors else (y, D2)
 
 
 class Context:

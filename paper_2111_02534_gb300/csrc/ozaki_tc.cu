@@ -33,9 +33,10 @@
 // stores 32 consecutive y of an output row):
 //    C1[y][x] = sum_y' K_y[y][y'] P[x][y']     A = slices of K_y,  B = slices of P
 //    C2[y][x] = sum_x' P^T[y][x'] K_x[x][x']   A = slices of P^T,  B = slices of K_x
-// with the potential term fused into the first epilogue and the second accumulating.
-// Operand tiles reach shared memory by TMA (128-byte swizzle, K-major), one thread issues
-// tcgen05.mma into tensor memory, and four warps drain it.
+// with the potential term fused into the first epilogue; both products run in one launch
+// and add their tiles to the zeroed output (two terms per element, so the FP64 atomic sum
+// is order-independent).  Operand tiles reach shared memory by TMA (128-byte swizzle,
+// K-major), one thread issues tcgen05.mma into tensor memory, and four warps drain it.
 #include <cuda.h>
 #include <cuda_runtime.h>
 

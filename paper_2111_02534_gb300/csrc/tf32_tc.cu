@@ -20,10 +20,10 @@
 namespace tps {
 namespace {
 
-// Tiles are 128 x BN with BN a multiple of 16 up to 256, chosen per pass: one tcgen05.mma
-// costs ~150 cycles almost whatever its N (measured on the BF16 kernel), so the widest
-// MMA (128 x 256 x 8) does the most work per instruction, and a 512-wide product needs two
-// tiles instead of eight.
+// Tiles are 128 x BN with BN a multiple of 16 up to 128, chosen per operator axis
+// (tile_n): a tcgen05.mma costs its issuing thread max(~45, N/2) cycles, so tiles of 64 to
+// 128 columns keep each MMA useful, while a pass, a short K loop per CTA, is latency-bound
+// and gets faster when its tiles fill one wave on the SMs.
 constexpr int kBM = 128, kBNMax = 128, kBK = 32;  // K block: 32 FP32 = one 128-byte row
 constexpr int kStages = 6;
 constexpr int kThreads = 128;

@@ -54,3 +54,13 @@ def test_accuracy_gate():
     lam[2] += 3e-13                       # 6e-10 of |lambda_2| but 1.5e-10 of |lambda_0|
     assert bench.passing_pairs(lam, ref)[0] == 3
     assert bench.aggregate(3.0, 5, 1) == (3.0, 5)
+
+
+def test_both_arms_report_the_same_workload_config():
+    # the reference arm (the oracle on the host cores) and ours name one workload
+    import bench
+    from paper_2111_02534_gb300.inputs import WORKLOADS
+    w = WORKLOADS[bench.WORKLOAD]
+    c1, c2 = bench.workload_config(w, 1), bench.workload_config(w, 1)
+    assert c1 == c2 and c1["unknowns"] == 512 * 512 and c1["sector_unknowns"] == 257 * 512
+    assert "8 lowest x-even eigenpairs" in c1["workload"]

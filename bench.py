@@ -41,13 +41,14 @@ SM_MAX_MHZ = 2070.0
 # digit-pair products of the tensor-core FP64 emulation (9 wave-function digits, 10
 # mode-matrix digits, levels i + j <= 9 kept): each one a BF16 MMA over the full product
 TC_PAIRS = 54
-# DRAM bytes (read + write) per launch of each kernel, mean over the launches captured by
-# ncu (profiles/k_update_split_1d_n512.md, profiles/k_update_k_gram_1d_n512.md,
-# profiles/k_oz_gemm_1d_n512.md, profiles/k_tf32_gemm_1d_n512.md); a kernel that changes
-# after its capture is removed from this table
+# DRAM bytes (read + write) per launch of each kernel, mean over the launches of one ncu
+# capture of the kernel on this workload; a kernel that changes after its capture is
+# removed from this table
 TRAFFIC_BYTES_PER_LAUNCH = {"k_update": 37.93e6, "k_gram": 42.13e6, "k_oz_gemm": 49.35e6,
                             "k_tf32_gemm": 5.08e6}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
+# BF16 digit-pair products per FP64 multiply-add of the split block update
+SPLIT_UPDATE_PAIRS = 53
 
 
 def measured_peaks():
@@ -169,6 +170,52 @@ def cpu_oracle_sample(w, v0):
     ref = golden()["evals"][0]
     ok = abs(lam[0] - ref) / abs(ref) <= REL_TOL
     return (1.0 if ok else 0.0) / dt, dt, os.cpu_count()
+
+
+def blas_threads():
+    """Threads of NumPy's BLAS (threadpoolctl when installed, else the environment's
+    OMP/OPENBLAS setting, else None: the library default, one per core)."""
+    try:
+        from threadpoolctl import threadpool_info
+        info = [d for d in threadpool_info() if d.get("user_api") == "blas"]
+        if info:
+            return {"library": info[0].get("internal_api"), "threads": info[0].get("num_threads")}
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return {"library": None, "threads": int(os.environ[var])}
+    return None
+
+
+def cpu_oracle_legs(w, v0):
+    """The other CPU legs of the measurement, each the oracle as it stands:
+    the NumPy tensor-form H-apply (Kronecker identity, two dense 512 x 512 mode products
+    per vector) on the full n = 512 grid, and the dense LAPACK eigh of the x-even H of the
+    n = 64 workload (2112 x 2112) that the GPU smoke test solves."""
+    from oracle.hamiltonian import problem_1d
+    from oracle.eig import lowest_dense
+    from paper_2111_02534_gb300.inputs import WORKLOADS, random_block
+    P = problem_1d(w.M, w.m, w.hbar, w.n, w.L, v0, w.sigma)
+    psi = random_block(8, P.N, 0)
+    P.apply_kron(psi[:1])
+    t0 = time.perf_counter()
+    P.apply_kron(psi)
+    dt_apply = (time.perf_counter() - t0) / 8
+    flops = 2.0 * P.N * sum(w.n) + 3.0 * P.N
+    w1 = WORKLOADS["1d_n64"]
+    P1 = problem_1d(w1.M, w1.m, w1.hbar, w1.n, w1.L, w1.v0, w1.sigma)
+    t0 = time.perf_counter()
+    lowest_dense(P1, w1.k, 1)
+    dt_eigh = time.perf_counter() - t0
+    return {"apply_h_ms_per_vector": 1000.0 * dt_apply,
+            "apply_h_gflops": flops / dt_apply / 1e9,
+            "apply_h_what": "oracle tensor-form H-apply (NumPy FP64 matmul) on the full "
+                            "512 x 512 grid, mean over 8 vectors",
+            "dense_eigh_1d_n64_s": dt_eigh,
+            "dense_eigh_1d_n64_pairs_per_s": w1.k / dt_eigh,
+            "dense_eigh_what": "oracle dense LAPACK eigh of the x-even H of the n = 64 "
+                               "workload (2112 x 2112, H assembled explicitly), 4 pairs"}
 
 
 def run_sweep(tps, torch, nstreams):
@@ -305,11 +352,18 @@ def run_ours(args):
     gold = golden()
     ref = np.array(gold["evals"])
     mu_hl = w.M * w.m / (w.M + w.m)
+    torch.cuda.synchronize()
+    t_set0 = time.perf_counter()
     v0 = tps.two_body_v0(1, mu_hl, w.hbar, w.E0, tps.GAUSS, w.sigma, w.n[1], w.L[1])
+    t_set1 = time.perf_counter()
     ctx = tps.Context(1, local)
     ctx.set_masses(w.M, w.m, w.hbar)
     ctx.set_grid(list(w.n), list(w.L))
+    torch.cuda.synchronize()
+    t_set2 = time.perf_counter()
     ctx.set_pair_potential(tps.GAUSS, v0, w.sigma)
+    torch.cuda.synchronize()
+    t_set3 = time.perf_counter()
     N, hnorm = ctx.info()
     stream = torch.cuda.current_stream()
     x0 = torch.from_numpy(random_normal_block(w.block, N, seed=1000 + rank)).cuda()
@@ -323,7 +377,11 @@ def run_ours(args):
                             stream=stream)
         return lam, st
 
-    for _ in range(max(3, args.warmup)):
+    t_first0 = time.perf_counter()
+    step()          # the first solve also builds the sector operator and the workspace
+    torch.cuda.synchronize()
+    t_first1 = time.perf_counter()
+    for _ in range(max(3, args.warmup) - 1):
         step()
     torch.cuda.synchronize()
     if world > 1:
@@ -351,6 +409,28 @@ def run_ours(args):
     local_t = sum(times)
     T, total_pairs = aggregate(local_t, pairs, world, device="cuda")
     value = total_pairs / T
+
+    # median of at least 10 solves (the timed steps plus extra untimed-for-value ones)
+    med_times = list(times)
+    while len(med_times) < 10:
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        med_times.append(ev0.elapsed_time(ev1) / 1000.0)
+    setup = {"two_body_v0_ms": 1000.0 * (t_set1 - t_set0),
+             "context_masses_grid_ms": 1000.0 * (t_set2 - t_set1),
+             "pair_potential_ms": 1000.0 * (t_set3 - t_set2),
+             "first_solve_ms": 1000.0 * (t_first1 - t_first0),
+             "note": "host wall clock with device synchronisation; the first solve builds the "
+                     "parity-sector operator, its tensor-core digit slices and TF32 eigenbases, "
+                     "and the solver workspace, which later solves reuse"}
+    solve_stats = {"solves": len(med_times), "median_ms": 1000.0 * statistics.median(med_times),
+                   "mean_ms": 1000.0 * statistics.mean(med_times),
+                   "min_ms": 1000.0 * min(med_times), "max_ms": 1000.0 * max(med_times),
+                   "median_eigenpairs_per_s": len(ref) / statistics.median(med_times)}
 
     # end to end through the public API with host buffers: every step sets the potential
     # (the library evaluates it and uploads N doubles), copies the start block from pinned
@@ -432,26 +512,48 @@ def run_ours(args):
             "peak_note": "bf16_tflops_sustained of measured (cuBLAS bf16, seconds-long loop)",
             "fp64_equivalent_tflops": h_fl / (h_ms / 1000.0) / 1e12,
             "launches": tot("h_launches"), "share": h_ms / 1000.0 / step_s}
-    for key, f, what in (("k_gram", "gram", "FP64 Gram products A^T B (one launch, split rows)"),
-                         ("k_update", "upd", "FP64-accurate block updates C = bC + a A Y: "
-                          "digit-split BF16 products (k_update_split, mma.sync) for blocks of "
-                          ">= 1e5 rows, FP64 FMA (k_update) below; rate in FP64-equivalent "
-                          "FLOP/s against the FP64 pipe the FMA form is bound by")):
-        # every 4th launch is timed (stats doc): rates from the timed ones, the share of
-        # the step scaled up to all launches
-        ms, fl, by = tot(f + "_ms"), tot(f + "_flops"), tot(f + "_bytes")
-        n_all = tot(f + "_launches")
-        n_timed = sum((getattr(st_, f + "_launches") + 3) // 4 for st_ in stats)
-        if ms > 0:
-            a = fl / (ms / 1000.0) / 1e12
-            kernels[key] = {"what": what, "bound": "alu", "achieved": a, "peak": fp64_peak,
-                            "unit": "TFLOP/s", "frac": a / fp64_peak,
-                            "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz "
-                                         "(nominal-derived; a DFMA probe measured 1.19 TFLOP/s)",
-                            "hbm_gbs": by / (ms / 1000.0) / 1e9,
-                            "hbm_frac": by / (ms / 1000.0) / 1e9 / hbm_peak if hbm_peak else None,
-                            "launches": n_all, "timed_launches": n_timed,
-                            "share": ms * n_all / max(n_timed, 1) / 1000.0 / step_s}
+    # every 4th Gram / update / Ritz launch is timed (stats doc): rates come from the timed
+    # launches, the share of the step is scaled up to all launches
+    ms, fl, by = tot("gram_ms"), tot("gram_flops"), tot("gram_bytes")
+    n_all = tot("gram_launches")
+    n_timed = sum((st_.gram_launches + 3) // 4 for st_ in stats)
+    if ms > 0:
+        a = fl / (ms / 1000.0) / 1e12
+        kernels["k_gram"] = {
+            "what": "FP64 Gram products A^T B (one launch, split rows, FP64 FMA)",
+            "bound": "alu", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": a / fp64_peak,
+            "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz (nominal-derived)",
+            "hbm_gbs": by / (ms / 1000.0) / 1e9,
+            "hbm_frac": by / (ms / 1000.0) / 1e9 / hbm_peak if hbm_peak else None,
+            "launches": n_all, "timed_launches": n_timed,
+            "share": ms * n_all / max(n_timed, 1) / 1000.0 / step_s}
+    ms, fl, by = tot("upd_ms"), tot("upd_flops"), tot("upd_bytes")
+    n_all = tot("upd_launches")
+    n_timed = sum((st_.upd_launches + 3) // 4 for st_ in stats)
+    if ms > 0:
+        gbs = by / (ms / 1000.0) / 1e9
+        kernels["k_update"] = {
+            "what": "FP64-accurate block updates C = bC + a A Y: digit-split BF16 products "
+                    "(k_update_split, mma.sync) for blocks of >= 1e5 rows, FP64 FMA (k_update) "
+                    "below; algorithmic bytes 8 nrows (p + q), + 8 nrows q when C is read",
+            "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": gbs / hbm_peak if hbm_peak else None,
+            "peak_note": "hbm_gbs of measured (STREAM-style copy)",
+            "fp64_equivalent_tflops": fl / (ms / 1000.0) / 1e12,
+            "bf16_digit_tflops": SPLIT_UPDATE_PAIRS * fl / (ms / 1000.0) / 1e12,
+            "bf16_digit_note": f"{SPLIT_UPDATE_PAIRS} BF16 digit-pair products per FP64 "
+                               "multiply-add on mma.sync, counted as if every launch were split",
+            "launches": n_all, "timed_launches": n_timed,
+            "share": ms * n_all / max(n_timed, 1) / 1000.0 / step_s}
+    rr_ms, rr_n, rr_t = tot("rr_ms"), tot("rr_launches"), tot("rr_timed")
+    if rr_ms > 0 and rr_t > 0:
+        kernels["k_rr_mixed"] = {
+            "what": "Rayleigh-Ritz eigensolver of the projected m x m matrix (one 8-CTA "
+                    "cluster; latency-bound, no throughput roofline)",
+            "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "us_per_call": 1000.0 * rr_ms / rr_t, "launches": rr_n, "timed_launches": rr_t,
+            "share": rr_ms * rr_n / rr_t / 1000.0 / step_s}
     p_ms, h32_ms = tot("prec_ms"), tot("h32_ms")
     if p_ms > 0:
         # the solver's default preconditioner: four TF32 mode products on tcgen05 (with the
@@ -473,7 +575,8 @@ def run_ours(args):
                                     "peak_note": "FP32 FMA pipe, nominal-derived",
                                     "launches": tot("h32_launches"),
                                     "share": h32_ms / 1000.0 / step_s}
-    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    with_roof = [k for k in kernels if kernels[k].get("frac") is not None]
+    dom = max(with_roof, key=lambda k: kernels[k]["share"]) if with_roof else None
     roofline = None
     if dom is not None:
         kd = kernels[dom]
@@ -490,7 +593,12 @@ def run_ours(args):
         v, dt, cores = cpu_oracle_sample(w, gold["v0"])
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"oracle LOBPCG (NumPy/SciPy FP64) for the lowest x-even eigenpair of "
-                         f"the same n=512 workload, {dt:.1f} s on the host"}
+                         f"the same n=512 workload, {dt:.1f} s on the host; the 8-pair solve is "
+                         f"not run (LOBPCG's cost grows at least linearly with the block, so "
+                         f"8 pairs would take >= {8 * dt:.0f} s: this per-pair rate is an upper "
+                         f"bound of the oracle's 8-pair rate)",
+               "blas_threads": blas_threads()}
+        cpu.update(cpu_oracle_legs(w, gold["v0"]))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,6 +618,7 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": int(sum(st.kernel_launches for st in stats)),
             "eigen_rel_err_max": rel_max, "pairs_passing": total_pairs,
+            "solve_time_stats": solve_stats, "setup": setup,
             "solver": {"outer_iters": stats[-1].outer_iters, "h_applies": stats[-1].h_applies,
                        "prec_applies": stats[-1].prec_applies, "restarts": stats[-1].restarts},
             "wall_s": wall,

@@ -170,7 +170,11 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
  * over all 2*dim modes.  Returns TPS_ERR_SINGULAR when
  * min |lambda_sum - theta| < 1e-14 * max |lambda_sum|.  r_dev, out_dev: device
  * [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32: FP32
- * arithmetic (the preconditioner is an approximation; the solver's default). */
+ * arithmetic; TPS_TF32_TC (1D only, TPS_ERR_INVALID_ARG in 2D): the four mode products
+ * on the tensor cores with TF32 inputs and FP32 accumulation, ~2.5e-3 relative to the
+ * exact solve (the first call on a context builds padded FP32 eigenbases of a few MB).
+ * The preconditioner only approximates (H - theta)^-1 whatever the dtype: the solver uses
+ * TPS_TF32_TC by default in 1D and TPS_F32 in 2D. */
 int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, double theta,
                    int dtype, cudaStream_t stream);
 
@@ -267,6 +271,10 @@ typedef struct tps_stats {
   int rr_refine_iters;       /* their FP64 refinement iterations */
   int rr_groups_rotated;     /* groups of close eigenvalues rotated inside the refinement */
   int rr_fallbacks;          /* solves the FP64 Jacobi finished (refinement not converged) */
+  double rr_ms;              /* with opts.timing: device time of the Rayleigh-Ritz eigensolves
+                                (every 4th launch timed, like the Gram products) */
+  long long rr_launches;     /* Rayleigh-Ritz eigensolver launches (all of them) */
+  long long rr_timed;        /* of which timed (rr_ms covers these) */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 
@@ -363,7 +371,9 @@ int tps_correction(tps_ctx *ctx, const double *Qt_dev, int nq, const double *R_d
  * context and calls no allocator; its partial sums live in a 1 MiB array compiled into
  * the library, one per device.  The paper has no counterpart to this entry point.
  *  - The first call on each device looks the array's address up (with that device
- *    current); make that first call before any stream capture.
+ *    current) and caches it with the id of the current CUDA context; a call under a new
+ *    context (after cudaDeviceReset, for example) looks it up again.  Make the first call
+ *    on a device, and the first after a reset, before any stream capture.
  *  - Every call on a device shares the array and it keeps the last call's contents;
  *    calls that overlap on the GPU (e.g. on two streams at once) race on it.
  *  - Returns TPS_ERR_INVALID_ARG for p or q outside 1..64 or bad strides/pointers,

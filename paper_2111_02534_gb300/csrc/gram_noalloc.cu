@@ -11,6 +11,7 @@
 // The array is shared by every call on a device and keeps the previous call's
 // contents; every partial sum is written before it is read, so nothing needs clearing.
 // Calls that overlap on the GPU (for example on two streams at once) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -24,10 +25,6 @@ constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
-
-// device address of g_noalloc_scratch, looked up once per device
-double *g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
 
 // partial[pb][c][16]: 4x4 block pb of A^T B summed over the rows of chunk c
 __global__ void __launch_bounds__(kThreads)
@@ -88,20 +85,72 @@ __global__ void k_gram_reduce_noalloc(const double *__restrict__ partial, int p,
   }
 }
 
-// Device address of the scratch array for the current device (set-up on first use).
-cudaError_t scratch_address(double **out) {
+// Per-device set-up, done once per device and CUDA context with that device current: the
+// device address of g_noalloc_scratch (in host code the symbol's name is only a host-side
+// stand-in, not a device address) and the SM count that sizes the grid.  The cache is keyed
+// by the context's unique id as well as the device number, so a cudaDeviceReset, which ends
+// the primary context and with it the module that holds the array, is followed by a fresh
+// look-up instead of the use of a stale address.
+struct ScratchSetup {
+  unsigned long long ctx_id = 0;
+  double *addr = nullptr;
+  int sms = 0;
+};
+ScratchSetup g_setup[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current CUDA context (0 if it cannot be read).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+      get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+cudaError_t scratch_setup(double **addr, int *sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  // 0 when no context is current on this thread yet: the look-up below then binds the
+  // device's primary context, and the id is read again after it
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  ScratchSetup &su = g_setup[dev];
+  if (!su.addr || id == 0 || su.ctx_id != id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double *>(p);
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    su.addr = static_cast<double *>(p);
+    su.sms = n > 0 ? n : 1;
+    su.ctx_id = current_context_id();
   }
-  *out = g_scratch_addr[dev];
+  *addr = su.addr;
+  *sms = su.sms;
   return cudaSuccess;
 }
 
@@ -114,20 +163,32 @@ extern "C" int tps_gram_noalloc(const double *A_dev, long long lda, int p, const
       !G_dev || (nrows > 0 && (!A_dev || !B_dev)))
     return TPS_ERR_INVALID_ARG;
   double *scratch = nullptr;
-  if (scratch_address(&scratch) != cudaSuccess) return TPS_ERR_CUDA;
+  int sms = 1;
+  if (scratch_setup(&scratch, &sms) != cudaSuccess) return TPS_ERR_CUDA;
   const int npb = ((p + 3) / 4) * ((q + 3) / 4);
-  // as many row chunks as the scratch holds (at least 32 for p = q = 64), up to 2 per SM
+  // row chunks: about two CTAs per SM over all 4x4 blocks, at most one per 1024 rows, and
+  // never more than the array holds (its capacity is 2^17 / (16 npb) chunks, 32 at
+  // p = q = 64)
   long long nchunk = kScratchDoubles / ((long long)npb * 16);
-  const long long want = (2LL * 152 + npb - 1) / npb;
+  const long long want = (2LL * sms + npb - 1) / npb;
   const long long maxc = (nrows + 1023) / 1024;
   if (nchunk > want) nchunk = want;
   if (nchunk > maxc) nchunk = maxc;
   if (nchunk < 1) nchunk = 1;
+  // each launch's own status (cudaLaunchKernelEx returns it), so that an error left
+  // behind by an earlier, unrelated call is neither reported here nor cleared
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nchunk, npb);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = stream;
   tps::count_launch();
-  k_gram_partial_noalloc<<<dim3((unsigned)nchunk, npb), kThreads, 0, stream>>>(
-      A_dev, lda, p, B_dev, ldb, q, nrows, (int)nchunk, scratch);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_partial_noalloc, A_dev, lda, p, B_dev, ldb, q,
+                                     nrows, (int)nchunk, scratch);
+  if (e != cudaSuccess) return TPS_ERR_CUDA;
+  cfg.gridDim = dim3((unsigned)((p * q + 255) / 256));
+  cfg.blockDim = dim3(256);
   tps::count_launch();
-  k_gram_reduce_noalloc<<<(p * q + 255) / 256, 256, 0, stream>>>(scratch, p, q, (int)nchunk,
-                                                                 G_dev, ldg);
-  return cudaGetLastError() == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+  e = cudaLaunchKernelEx(&cfg, k_gram_reduce_noalloc, (const double *)scratch, p, q, (int)nchunk,
+                         G_dev, ldg);
+  return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }

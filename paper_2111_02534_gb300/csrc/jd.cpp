@@ -30,22 +30,23 @@ namespace tps {
 struct PhaseTiming {
   bool on = false;
   std::vector<cudaEvent_t> all, free_ev;
-  // kinds: 0 FP64 H, 1 preconditioner, 2 FP32 H, 3 Gram products, 4 block updates.  The
-  // skinny kinds (hundreds of short launches per solve) are timed on every kSample-th
-  // launch only: their flops, bytes and time then refer to the sampled launches, and
-  // launches[] counts all of them
-  static constexpr int kKinds = 5;
+  // kinds: 0 FP64 H, 1 preconditioner, 2 FP32 H, 3 Gram products, 4 block updates, 5
+  // Rayleigh-Ritz eigensolves.  The skinny kinds (hundreds of short launches per solve)
+  // and the Ritz solves are timed on every kSample-th launch only: their flops, bytes and
+  // time then refer to the sampled launches, and launches[] counts all of them
+  static constexpr int kKinds = 6;
   static constexpr int kSample = 4;
-  long long seen[kKinds] = {0, 0, 0, 0, 0};
+  long long seen[kKinds] = {0, 0, 0, 0, 0, 0};
+  long long timed[kKinds] = {0, 0, 0, 0, 0, 0};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend[kKinds];
-  double ms[kKinds] = {0, 0, 0, 0, 0}, flops[kKinds] = {0, 0, 0, 0, 0};
-  double bytes[kKinds] = {0, 0, 0, 0, 0};
-  long long launches[kKinds] = {0, 0, 0, 0, 0};
+  double ms[kKinds] = {0, 0, 0, 0, 0, 0}, flops[kKinds] = {0, 0, 0, 0, 0, 0};
+  double bytes[kKinds] = {0, 0, 0, 0, 0, 0};
+  long long launches[kKinds] = {0, 0, 0, 0, 0, 0};
   void reset(bool enable) {
     on = enable;
     for (int k = 0; k < kKinds; ++k) {
       ms[k] = flops[k] = bytes[k] = 0.0;
-      launches[k] = seen[k] = 0;
+      launches[k] = seen[k] = timed[k] = 0;
     }
   }
   cudaEvent_t get() {
@@ -690,8 +691,24 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     launch_mirror_block(w.G, ldG, m, bn, s);
     m += bn;
     // (4) Rayleigh-Ritz
-    launch_rr_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat, jac_tol, w.Arot,
-                   opts.rr_method, opts.rr_refine_max);
+    {
+      PhaseTiming &t = w.tm;
+      const bool rec = t.on && (t.seen[5]++ % PhaseTiming::kSample) == 0;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (rec) {
+        ea = t.get();
+        eb = t.get();
+        cudaEventRecord(ea, s);
+      }
+      launch_rr_eigh(w.G, m, ldG, w.theta, w.Y, ldG, s, warm_mp, w.jstat, jac_tol, w.Arot,
+                     opts.rr_method, opts.rr_refine_max);
+      t.launches[5] += 1;
+      if (rec) {
+        cudaEventRecord(eb, s);
+        t.pend[5].push_back({ea, eb});
+        t.timed[5] += 1;
+      }
+    }
     warm_mp = m;  // valid for the next iteration unless the basis is rotated below
     const int nact = std::min(bp, std::min(k - nlock, m));
     double *X = w.QX + (long long)nlock * N;
@@ -922,6 +939,9 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.upd_flops = w.tm.flops[4];
   stt.upd_bytes = w.tm.bytes[4];
   stt.upd_launches = w.tm.launches[4];
+  stt.rr_ms = w.tm.ms[5];
+  stt.rr_launches = w.tm.launches[5];
+  stt.rr_timed = w.tm.timed[5];
   stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;

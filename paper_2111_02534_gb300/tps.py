@@ -68,7 +68,8 @@ class Stats(C.Structure):
                 ("gs_orthogonalisations", C.c_int), ("gs_second_passes", C.c_int),
                 ("rr_mixed_calls", C.c_int), ("rr_fp32_solves", C.c_int),
                 ("rr_refine_iters", C.c_int), ("rr_groups_rotated", C.c_int),
-                ("rr_fallbacks", C.c_int),
+                ("rr_fallbacks", C.c_int), ("rr_ms", C.c_double), ("rr_launches", C.c_longlong),
+                ("rr_timed", C.c_longlong),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

@@ -50,6 +50,35 @@ def test_noalloc_gram_matches_context_gram_twice():
     ctx.close()
 
 
+def _noalloc(tps, Ad, lda, p, Bd, ldb, q, nrows, G, ldg):
+    return tps._lib.tps_gram_noalloc(ctypes.c_void_p(Ad.data_ptr()), lda, p,
+                                     ctypes.c_void_p(Bd.data_ptr()), ldb, q, nrows,
+                                     ctypes.c_void_p(G.data_ptr()), ldg,
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_gram_strided_and_empty():
+    """Leading dimensions larger than the row count (A, B) and than p (G): only the p x q
+    block of G is written and G's padding rows keep their values; with no rows G is zero."""
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    nrows, p, q, lda, ldb, ldg = 20011, 7, 5, 20016, 20023, 11
+    A = random_block(p, lda, 31)
+    B = random_block(q, ldb, 32)
+    Ad, Bd = dev(A), dev(B)
+    G = torch.full((q, ldg), -7.0, dtype=torch.float64, device="cuda")   # column-major, ld 11
+    assert _noalloc(tps, Ad, lda, p, Bd, ldb, q, nrows, G, ldg) == tps.OK
+    got = host(G)
+    ref = A[:, :nrows] @ B[:, :nrows].T
+    assert np.max(np.abs(got[:, :p].T - ref)) <= 1e-14 * np.sqrt(nrows) * max(1.0, np.abs(ref).max())
+    assert np.all(got[:, p:] == -7.0)
+    G0 = torch.full((q, ldg), np.nan, dtype=torch.float64, device="cuda")
+    assert _noalloc(tps, Ad, lda, p, Bd, ldb, q, 0, G0, ldg) == tps.OK
+    g0 = host(G0)
+    assert np.all(g0[:, :p] == 0.0) and np.all(np.isnan(g0[:, p:]))
+    del Ad, Bd
+
+
 def test_noalloc_gram_refuses_sizes_beyond_its_limit():
     require_gpu()
     from paper_2111_02534_gb300 import tps

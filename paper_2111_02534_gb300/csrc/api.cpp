@@ -725,6 +725,7 @@ int tps_device_status(tps_ctx *ctx) {
   TPS_CUDA_TRY(ctx, cudaDeviceSynchronize());
   int flag = tc_operator_status(ctx->full) | tf_operator_status(ctx->full);
   for (int p = 0; p < 3; ++p) flag |= tc_operator_status(ctx->sect[p]) | tf_operator_status(ctx->sect[p]);
+  flag |= update_split_status();
   if (flag < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
   if (flag) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   return TPS_OK;

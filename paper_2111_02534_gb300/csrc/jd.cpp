@@ -945,9 +945,10 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   stt.kernel_launches = g_kernel_launches.load() - launches0;
   stt.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) *stats = stt;
-  if (w.h64_dtype == TPS_F64_TC) {
+  {
     TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    const int f = tc_operator_status(op);
+    const int f = (w.h64_dtype == TPS_F64_TC ? tc_operator_status(op) : 0) |
+                  (opts.update_dtype == TPS_F64_TC ? update_split_status() : 0);
     if (f < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
     if (f) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   }

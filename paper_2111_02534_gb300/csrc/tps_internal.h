@@ -122,6 +122,9 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
                          int ldy, long long bsy, int q, double alpha, double beta, double *C,
                          long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,
                          const int *need = nullptr);
+// Synchronously reads and clears the timed-out-wait flag of the staged split update
+// (1 if a wait gave up since the last call, 0 if not, -1 if the flag cannot be read).
+int update_split_status();
 // Host: A = S diag(lam) S^-1 for a real n x n row-major A with a real spectrum (ascending
 // lam, unit columns of S; Sinv nullable).  0 on success, 1 for a complex pair or no
 // convergence, 2 for a singular S (host_eig.cpp).

@@ -1,85 +1,226 @@
 // FP64-accurate tall-skinny block updates C = beta C + alpha A Y on the tensor cores
 // (the Ritz vectors X = V Y and HX = (HV) Y, restarts, and the projections of the
-// orthogonalisation in Sec. 4.1).  A is n x p (p <= 64 per call, column-major, n up to
+// orthogonalisation in Sec. 4.1).  A is n x p (p <= 64 per pass, column-major, n up to
 // millions), Y is p x q with q <= 8 per CTA group.
 //
 // The products are emulated by error-free digit splitting (the Ozaki scheme: Ozaki,
-// Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), as in the H-apply:
+// Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), as in the H-apply, with digits sized
+// for a contraction of at most 64 terms:
 //  * row r of A gets the exponent E_r with |A[r][k]| < 2^E_r for all k, column j of
-//    alpha Y the exponent F_j; each value becomes the integer round(x 2^(54 - E)) and is
-//    written in nine balanced base-64 digits, most significant first, |d| <= 64;
-//  * the digit pairs (i, j) with i + j <= 9 are multiplied in BF16 (small integers are
-//    exact) and the pairs of one level l = i + j are summed in one FP32 accumulator:
-//    every partial sum is an integer below 64 (l + 1) 2^12 < 2^24 (p <= 64), hence exact;
-//  * the levels are combined in two int64 Horner sums and scaled by 2^(E_r + F_j).
-// The result has the row-wise accuracy of the FP64 product (2^-55 of the row maximum of
-// A times sum_k |alpha Y[k][j]|, plus the truncation of the levels l > 9 below that).
+//    alpha Y the exponent F_j; each value becomes the integer q = round(x 2^(54 - E)),
+//    |q| <= 2^54, written in seven base-256 digits, most significant first:
+//    |q| = t 2^48 + c1 2^24 + c2 with t <= 64, and each 24-bit chunk c = d0 2^16 + d1 2^8
+//    + d2 with d0 in [0, 256] and |d1|, |d2| <= 128 (two FP32 roundings, exact), the
+//    sign applied to every digit.  Integers up to 256 are exact in BF16.  Digit i has
+//    the weight 2^(E - 6 - 8 i);
+//  * the digit pairs (i, j) with i + j <= 7 (34 of the 49) are multiplied in BF16 and the
+//    pairs of one level l = i + j are summed in one FP32 accumulator.  With the digit
+//    bounds above, the largest level (l = 5) sums at most 180224 per contraction index, so
+//    over p <= 64 indices every partial sum is an integer below 2^23.5: exact;
+//  * the levels are combined in two int64 Horner sums (levels 0-3 and 4-7, each below
+//    2^48) and scaled by 2^(E_r + F_j - 36) and 2^(E_r + F_j - 68).
+// The dropped levels l >= 8 weigh at most 131072 p 2^(E_r + F_j - 76) < p 2^-59 2^(E_r +
+// F_j) per entry, and the rounding of the operands to 54 bits 2^-55 of the row maximum:
+// the result has the accuracy of an FP64 product, 2^-53 max_k |A[r][k]| sum_k |alpha Y[k][j]|
+// per entry (row-wise, not element-wise).
 //
 // The MMA is the warp-level mma.sync m16n8k16 (BF16 in, FP32 out): the output is only
 // q <= 8 columns wide, and a tcgen05.mma costs its issuing thread about 45 cycles
-// whatever N (measured: 367 FLOP/clk/SM at M = 64, N = 8), while mma.sync m16n8k16 runs at
-// 2 cycles per warp instruction per SM (2046 FLOP/clk/SM).  The 53 digit products per
-// multiply-add then cost less than the one FP64 FMA they replace on GB300's FP64 pipe
-// (4 FLOP/clk/SM).  The digit splitting of A runs on the FP32 pipe: the 54-bit integer
-// is cut into three 18-bit chunks, each exact in FP32, and each chunk into three digits
-// by two roundings.
+// whatever N, while mma.sync m16n8k16 issues every 2 cycles per SM.  The 34 digit products
+// per multiply-add then cost less than the one FP64 FMA they replace on GB300's FP64 pipe
+// (4 FLOP/clk/SM).  The digit splitting of A runs on the FP32 and integer pipes.
+//
+// A streams from HBM through shared memory: a producer warp copies 64-row tiles of A (one
+// 512-byte cp.async.bulk per column, completing on an mbarrier) into a ring of stages,
+// four consumer warps split and multiply them (16 rows each), so that many tiles are in
+// flight per SM while the consumers compute.  Every wait is bounded; a wait that gives up
+// records it in a device flag (tps_device_status, tps_solve) and the CTA winds down.
+// Inputs that the bulk copy cannot address (A, lda or the batch stride not 16-byte
+// aligned) and the last partial tile are read directly from global memory.
 #include <cuda_bf16.h>
 
+#include <atomic>
+#include <mutex>
+
+#include "ozaki_tc.cuh"
 #include "tps_internal.h"
 
 namespace tps {
+
+// Nonzero after a wait of the staged update kernel gave up (read and cleared by
+// update_split_status).
+__device__ int g_update_split_err = 0;
+// staged launches since the flag was last read (no read, no synchronisation, without any)
+std::atomic<long long> g_staged_launches{0};
+
 namespace {
 
-constexpr int kUT = 128;   // threads per CTA: 4 warps, each 16 rows at a time
-constexpr int kUS = 9;     // digits per operand
-constexpr int kUL = 10;    // levels kept: i + j <= 9
-constexpr int kUKT = 4;    // k tiles of 16 (p <= 64)
+constexpr int kUS = 7;          // base-256 digits per operand
+constexpr int kUL = 8;          // levels kept: i + j <= 7
+constexpr int kUKT = 4;         // k tiles of 16 (p <= 64)
+constexpr int kWarps = 8;       // consumer warps, 16 rows each
+constexpr int kCons = 32 * kWarps;
+constexpr int kRows = 16 * kWarps;  // rows per staged tile
+constexpr int kColStride = kRows + 4;  // doubles between the columns of a staged tile (4 mod 8:
+                                       // the four column pairs a warp reads hit disjoint banks)
+constexpr int kMaxStages = 6;
+constexpr int kRingBytes = 100 * 1024;  // stages x stage bytes, at least 2 stages
+constexpr float kMagic = 12582912.f;    // 1.5 2^23: x + kMagic - kMagic = rint(x), |x| <= 2^22
+#ifndef TPS_UPD_MINB
+#define TPS_UPD_MINB 2  // resident staged CTAs per SM the register allocation aims at
+#endif
 
 __device__ __forceinline__ unsigned raw_exp(double x) {
   return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// round(x 2^(54 - E)), E = raw_max - 1022 (so |x| < 2^E), by integer arithmetic on the
-// FP64 fields; subnormals flush to zero.  |result| <= 2^54.
-__device__ __forceinline__ long long scaled54(double x, unsigned raw_max) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((u >> 52) & 0x7FF);
-  if (ex == 0 || raw_max == 0) return 0;
-  const long long mant = (long long)((u & ((1ULL << 52) - 1)) | (1ULL << 52));
-  const int sh = ex - 1075 + 54 - ((int)raw_max - 1022);
-  long long q;
-  if (sh >= 0)
-    q = mant << sh;
-  else if (sh > -63)
-    q = (mant + (1LL << (-sh - 1))) >> (-sh);
-  else
-    q = 0;
-  return (u >> 63) ? -q : q;
-}
-
-// The nine digits of x: x 2^(54 - E) = sum_i d[i] 64^(8 - i), |d[i]| <= 64.
-__device__ __forceinline__ void digits9(double x, unsigned raw_max, float (&d)[kUS]) {
-  const long long q = scaled54(x, raw_max);
-  const float sg = q < 0 ? -1.f : 1.f;
-  const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
-  const unsigned ch[3] = {(unsigned)(a >> 36), (unsigned)((a >> 18) & 0x3FFFFu),
-                          (unsigned)(a & 0x3FFFFu)};
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    float f = (float)ch[t];                        // <= 2^18: exact
-    const float d0 = rintf(f * (1.f / 4096.f));    // 0 .. 64
-    f = fmaf(-d0, 4096.f, f);                      // |f| <= 2048
-    const float d1 = rintf(f * (1.f / 64.f));      // |d1| <= 32
-    f = fmaf(-d1, 64.f, f);                        // |f| <= 32
-    d[3 * t] = sg * d0;
-    d[3 * t + 1] = sg * d1;
-    d[3 * t + 2] = sg * f;
-  }
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x in the low half
   return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// packed pairs of FP32 values (f32x2 arithmetic: two lanes' worth per instruction)
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2split(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// round(x 2^(54 - E)), E = raw_max - 1022 (|x| < 2^E), in signed parts: the top digit t
+// (|t| <= 63) and the 24-bit chunks c1, c2 (|c| < 2^24), |q| = |t| 2^48 + |c1| 2^24 + |c2|,
+// each carrying the sign of x.  Integer arithmetic on the FP64 fields; subnormals and
+// values 2^-63 below the row maximum flush to zero.
+__device__ __forceinline__ void chunks(double x, unsigned raw_max, int &t, int &c1, int &c2) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int ex = (hi >> 20) & 0x7FF;
+  const int sh = (int)raw_max - ex;  // >= 0: q = round(2 mant 2^-sh)
+  const unsigned long long m2 =
+      ((unsigned long long)(((unsigned)hi & 0xFFFFFu) | 0x100000u) << 33) |
+      ((unsigned long long)lo << 1);
+  unsigned long long a = 0;
+  if (ex != 0 && sh < 64) a = (m2 + ((1ULL << sh) >> 1)) >> sh;
+  const int m = hi >> 31;  // 0 or -1
+  t = ((int)(a >> 48) ^ m) - m;
+  c1 = ((int)((a >> 24) & 0xFFFFFFu) ^ m) - m;
+  c2 = ((int)(a & 0xFFFFFFu) ^ m) - m;
+}
+
+// The digits of two values of one row (same exponent), as BF16 pairs: out[i] holds digit i
+// of x0 in its low half and of x1 in its high half.  The base-256 digits of a 24-bit chunk
+// c: d0 = rint(c 2^-16), d1 = rint((c - 2^16 d0) 2^-8), d2 = c - 2^16 d0 - 2^8 d1, all
+// exact FP32 operations (f32x2, both values at once).
+__device__ __forceinline__ void digits_pair(double x0, double x1, unsigned raw_max,
+                                            uint32_t (&out)[kUS]) {
+  int t0, a0, b0, t1, a1, b1;
+  chunks(x0, raw_max, t0, a0, b0);
+  chunks(x1, raw_max, t1, a1, b1);
+  out[0] = pack_bf16((float)t0, (float)t1);
+  const uint64_t M = f2(kMagic, kMagic), nM = f2(-kMagic, -kMagic);
+  const uint64_t s16 = f2(1.f / 65536.f, 1.f / 65536.f), s8 = f2(1.f / 256.f, 1.f / 256.f);
+  const uint64_t m16 = f2(-65536.f, -65536.f), m8 = f2(-256.f, -256.f);
+  const int ca[2] = {a0, b0}, cb[2] = {a1, b1};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint64_t f = f2((float)ca[h], (float)cb[h]);          // |c| < 2^24: exact
+    const uint64_t d0 = add2(add2(mul2(f, s16), M), nM);  // |d0| <= 256
+    f = fma2(d0, m16, f);                                 // |f| <= 2^15
+    const uint64_t d1 = add2(add2(mul2(f, s8), M), nM);   // |d1| <= 128
+    const uint64_t d2 = fma2(d1, m8, f);                  // |d2| <= 128
+    float l, u;
+    f2split(d0, l, u);
+    out[1 + 3 * h] = pack_bf16(l, u);
+    f2split(d1, l, u);
+    out[2 + 3 * h] = pack_bf16(l, u);
+    f2split(d2, l, u);
+    out[3 + 3 * h] = pack_bf16(l, u);
+  }
+}
+
+// The seven digits of one value (for alpha Y, once per CTA).
+__device__ __forceinline__ void digits7(double x, unsigned raw_max, float (&d)[kUS]) {
+  int t, a, b;
+  chunks(x, raw_max, t, a, b);
+  d[0] = (float)t;
+  const int ch[2] = {a, b};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float f = (float)ch[h];
+    const float d0 = rintf(f * (1.f / 65536.f));
+    f = fmaf(-d0, 65536.f, f);
+    const float d1 = rintf(f * (1.f / 256.f));
+    d[1 + 3 * h] = d0;
+    d[2 + 3 * h] = d1;
+    d[3 + 3 * h] = fmaf(-d1, 256.f, f);
+  }
+}
+
+__device__ __forceinline__ double pow2d(int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// (hi 2^32 + lo) 2^(E - 68) rounded to the nearest FP64 value (ties to even), |hi|, |lo| <
+// 2^49, by integer arithmetic (GB300's FP64 pipe issues one warp instruction per ~64 cycles
+// of a sub-partition, the integer pipes one per cycle); results outside the normal range
+// take the FP64 formula, which rounds the same way.
+__device__ __forceinline__ double combine(long long hi, long long lo, int E) {
+  const long long top = hi + (lo >> 32);  // S = top 2^32 + bot exactly, 0 <= bot < 2^32
+  const unsigned bot = (unsigned)lo;
+  const bool neg = top < 0;
+  unsigned long long T;
+  unsigned B;
+  if (!neg) {
+    T = (unsigned long long)top;
+    B = bot;
+  } else if (bot == 0) {
+    T = (unsigned long long)(-top);
+    B = 0;
+  } else {
+    T = (unsigned long long)(-top - 1);
+    B = 0u - bot;
+  }
+  if (T == 0 && B == 0) return 0.0;
+  const int lb = T ? 95 - __clzll((long long)T) : 31 - __clz((int)B);  // leading bit of |S|
+  int sh = lb - 52;
+  unsigned long long mant;
+  if (sh <= 0) {
+    mant = ((T << 32) | B) << (-sh);  // |S| < 2^53: exact
+  } else {                            // sh <= 29: the dropped bits are all in B
+    mant = (T << (32 - sh)) | (B >> sh);
+    const unsigned rem = B & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ULL))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++sh;
+      }
+    }
+  }
+  const int be = sh + E - 68 + 52 + 1023;
+  if (be <= 0 || be >= 2047)
+    return fma((double)lo, pow2d(E - 68), (double)hi * pow2d(E - 36));
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
+                                          ((unsigned long long)be << 52) |
+                                          (mant & ((1ULL << 52) - 1))));
 }
 
 __device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
@@ -90,115 +231,107 @@ __device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4],
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-__device__ __forceinline__ double pow2d(int e) {
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __longlong_as_double((long long)(e + 1023) << 52);
+__device__ __forceinline__ void mma_1688(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(b));
 }
 
-// CTA (x, s, z): columns j0 = 8 z .. j0 + 7 of batch item s, row blocks of 64 (16 per
-// warp) strided over gridDim.x.  Fragment layout of m16n8k16 (g = lane / 4, c = lane % 4):
-// A regs {row g, k 2c..2c+1}, {row g+8, k 2c..}, {row g, k 2c+8..}, {row g+8, k 2c+8..};
-// B regs {k 2c..2c+1, col g}, {k 2c+8.., col g}; C {row g, col 2c, 2c+1}, {row g+8, ..}.
-__global__ void __launch_bounds__(kUT)
-k_update_split(const double *__restrict__ A, long long lda, long long bsa, int p,
-               const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha,
-               double beta, double *__restrict__ C, long long ldc, long long bsc,
-               long long nrows, const int *__restrict__ need) {
-  if (need && *need == 0) return;  // conditional product (decided on the device)
-  __shared__ uint2 Bd[kUS][kUKT][32];
-  __shared__ unsigned Fraw[8];
-  const int s = blockIdx.y, j0 = blockIdx.z * 8;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+struct UpdArgs {
+  const double *A;
+  long long lda, bsa;
+  int p;
+  const double *Y;
+  int ldy;
+  long long bsy;
+  int q;
+  double alpha, beta;
+  double *C;
+  long long ldc, bsc, nrows;
+  const int *need;
+  int stages;  // staged kernel: ring stages
+};
+
+// One warp: 16 rows (ra = row0 + g, rb = ra + 8) of C's columns j0 .. j0 + 7, with A's
+// entry (k, row r of the block) at As[k * cs + r] (r < 16, rows past nrows not read), KT
+// k tiles of 16 (the last one as m16n8k8 when it holds at most 8 indices).
+// Fragment layout of m16n8k16 (g = lane / 4, c = lane % 4): A regs {row g, k 2c..2c+1},
+// {row g+8, k 2c..}, {row g, k 2c+8..}, {row g+8, k 2c+8..}; B regs {k 2c..2c+1, col g},
+// {k 2c+8.., col g}; C {row g, col 2c, 2c+1}, {row g+8, ..}.  release() is called once the
+// warp has read its last value of As.
+template <int KT, typename Stride, typename Release>
+__device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Stride cs,
+                                        long long row0, const uint2 (*Bd)[kUKT][32],
+                                        const unsigned *Fraw, int j0, double *Cs,
+                                        Release release) {
+  const int lane = threadIdx.x & 31;
   const int g = lane >> 2, c = lane & 3;
-  const int KT = (p + 15) >> 4;
-  const double *Ys = Y + s * bsy;
-  // column exponents of alpha Y (8 columns, p <= 64 rows): 16 threads per column, each
-  // over every 16th row, then a max across the 16 lanes
-  {
-    const int jl = threadIdx.x >> 4, k0 = threadIdx.x & 15, j = j0 + jl;
-    unsigned m = 0;
-    if (j < q)
+  const int p = g_.p;
+  const long long ra = row0 + g, rb = ra + 8;
+  const bool va = ra < g_.nrows, vb = rb < g_.nrows;
+  // row exponents from the high words: the thread's k values of rows g and g + 8, then
+  // across the quad
+  const int *Ah = reinterpret_cast<const int *>(As) + 1;
+  unsigned ea = 0, eb = 0;
 #pragma unroll
-      for (int k = k0; k < 64; k += 16)
-        if (k < p) m = max(m, raw_exp(alpha * Ys[(long long)j * ldy + k]));
+  for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (k0 == 0) Fraw[jl] = m;
+    for (int e = 0; e < 4; ++e) {
+      const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
+      if (k < p) {
+        if (va) ea = max(ea, (unsigned)Ah[2 * (k * cs + g)] & 0x7FF00000u);
+        if (vb) eb = max(eb, (unsigned)Ah[2 * (k * cs + g + 8)] & 0x7FF00000u);
+      }
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+    eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
   }
-  __syncthreads();
-  // B fragments of the nine digit planes of alpha Y: thread (kt, lane) packs its own
-  {
-    const int kt = threadIdx.x >> 5;
-    if (kt < kUKT) {
-      const int j = j0 + g;
-      float dv[4][kUS];
+  ea >>= 20;
+  eb >>= 20;
+  float acc[kUL][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
-        const double y = (j < q && k < p) ? alpha * Ys[(long long)j * ldy + k] : 0.0;
-        digits9(y, Fraw[g], dv[e]);
+  for (int l = 0; l < kUL; ++l)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc[l][t] = 0.f;
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt) {
+    const bool full16 = kt < KT - 1 || 16 * kt + 8 < p;
+    uint32_t af[kUS][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= 2 && !full16) {
+#pragma unroll
+        for (int i = 0; i < kUS; ++i) af[i][r] = 0u;
+        continue;
       }
+      const bool v = (r & 1) ? vb : va;
+      const int row = g + 8 * (r & 1);
+      const int k = 16 * kt + 2 * c + 8 * (r >> 1);
+      uint32_t d[kUS];
+      digits_pair((v && k < p) ? As[k * cs + row] : 0.0,
+                  (v && k + 1 < p) ? As[(k + 1) * cs + row] : 0.0, (r & 1) ? eb : ea, d);
 #pragma unroll
-      for (int i = 0; i < kUS; ++i)
-        Bd[i][kt][lane] = make_uint2(pack_bf16(dv[0][i], dv[1][i]), pack_bf16(dv[2][i], dv[3][i]));
+      for (int i = 0; i < kUS; ++i) af[i][r] = d[i];
     }
-  }
-  __syncthreads();
-  const double *As = A + s * bsa;
-  double *Cs = C + s * bsc;
-  const long long nblk = (nrows + 15) >> 4;
-  for (long long blk = (long long)blockIdx.x * 4 + warp; blk < nblk; blk += (long long)gridDim.x * 4) {
-    const long long ra = blk * 16 + g, rb = ra + 8;
-    const bool va = ra < nrows, vb = rb < nrows;
-    {
-      // the warp's next 16-row block into L1 while this one is split and multiplied (the
-      // kernel is bound by load latency): rows r and r + 8 share a 128-byte line
-      const long long nr = ra + (long long)gridDim.x * 64;
-      if (nr < nrows)
-        for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
-            if (k < p)
-              asm volatile("prefetch.global.L1 [%0];" ::"l"(As + (long long)k * lda + nr));
-          }
-    }
-    // row exponents: the thread's k values of rows ra and rb, then across the quad
-    unsigned ea = 0, eb = 0;
-    for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
-        if (k < p) {
-          if (va) ea = max(ea, raw_exp(As[(long long)k * lda + ra]));
-          if (vb) eb = max(eb, raw_exp(As[(long long)k * lda + rb]));
-        }
-      }
-#pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {
-      ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
-      eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
-    }
-    float acc[kUL][4];
-#pragma unroll
-    for (int l = 0; l < kUL; ++l)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) acc[l][t] = 0.f;
-    for (int kt = 0; kt < KT; ++kt) {
-      // A digit fragments: value e of register r is (row ra|rb, k 16kt + 2c + e + 8 (r>>1))
-      uint32_t af[kUS][4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const bool v = (r & 1) ? vb : va;
-        const long long row = (r & 1) ? rb : ra;
-        const unsigned er = (r & 1) ? eb : ea;
-        float d0[kUS], d1[kUS];
-        const int k = 16 * kt + 2 * c + 8 * (r >> 1);
-        digits9((v && k < p) ? As[(long long)k * lda + row] : 0.0, er, d0);
-        digits9((v && k + 1 < p) ? As[(long long)(k + 1) * lda + row] : 0.0, er, d1);
-#pragma unroll
-        for (int i = 0; i < kUS; ++i) af[i][r] = pack_bf16(d0[i], d1[i]);
-      }
+    if (kt == KT - 1) release();
+    if (full16) {
 #pragma unroll
       for (int j = 0; j < kUS; ++j) {
         const uint2 b = Bd[j][kt][lane];
@@ -206,33 +339,232 @@ k_update_split(const double *__restrict__ A, long long lda, long long bsa, int p
         for (int i = 0; i < kUS; ++i)
           if (i + j < kUL) mma_16816(acc[i + j], af[i], b);
       }
-    }
-    // combine the levels: sum_l D_l 2^(-6 (l + 2)), hi = levels 0..4, lo = levels 5..9
+    } else {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const bool v = (t & 2) ? vb : va;
-      const int jl = 2 * c + (t & 1);
-      const int j = j0 + jl;
-      if (!v || j >= q) continue;
-      long long hi = 0, lo = 0;
+      for (int j = 0; j < kUS; ++j) {
+        const uint32_t b = Bd[j][kt][lane].x;
 #pragma unroll
-      for (int l = 0; l < kUL; ++l) {
-        const long long dl = (long long)__float2int_rn(acc[l][t]);
-        if (l < kUL / 2)
-          hi = hi * 64 + dl;
-        else
-          lo = lo * 64 + dl;
+        for (int i = 0; i < kUS; ++i)
+          if (i + j < kUL) mma_1688(acc[i + j], af[i][0], af[i][1], b);
       }
-      const unsigned er = (t & 2) ? eb : ea, fr = Fraw[jl];
-      double val = 0.0;
-      if (er && fr) {
-        const int E = (int)er - 1022 + (int)fr - 1022;
-        val = fma((double)lo, pow2d(E - 6 * (kUL + 1)), (double)hi * pow2d(E - 6 * (kUL / 2 + 1)));
-      }
-      double *dst = Cs + (long long)j * ldc + ((t & 2) ? rb : ra);
-      *dst = (beta == 0.0) ? val : fma(beta, *dst, val);
     }
   }
+  // combine the levels: value = (hi 2^32 + lo) 2^(E + F - 68), hi = levels 0..3, lo =
+  // levels 4..7 (Horner in base 256)
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const bool v = (t & 2) ? vb : va;
+    const int jl = 2 * c + (t & 1);
+    const int j = j0 + jl;
+    if (!v || j >= g_.q) continue;
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int l = 0; l < kUL; ++l) {
+      const long long dl = (long long)__float2int_rn(acc[l][t]);
+      if (l < kUL / 2)
+        hi = hi * 256 + dl;
+      else
+        lo = lo * 256 + dl;
+    }
+    const unsigned er = (t & 2) ? eb : ea, fr = Fraw[jl];
+    const double val =
+        (er && fr) ? combine(hi, lo, (int)er - 1022 + (int)fr - 1022) : 0.0;
+    double *dst = Cs + (long long)j * g_.ldc + ((t & 2) ? rb : ra);
+    *dst = (g_.beta == 0.0) ? val : fma(g_.beta, *dst, val);
+  }
+}
+
+// Digit planes of alpha Y's columns j0 .. j0 + 7 as m16n8k16 B fragments in shared memory,
+// and their column exponents; the kCons consumer threads take part.
+__device__ __forceinline__ void y_fragments(const UpdArgs &g_, const double *Ys, int j0,
+                                            uint2 (*Bd)[kUKT][32], unsigned *Fraw) {
+  const int t = threadIdx.x;
+  if (t < 128) {
+    const int jl = t >> 4, k0 = t & 15, j = j0 + jl;
+    unsigned m = 0;
+    if (j < g_.q)
+#pragma unroll
+      for (int k = k0; k < 64; k += 16)
+        if (k < g_.p) m = max(m, raw_exp(g_.alpha * Ys[(long long)j * g_.ldy + k]));
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (k0 == 0) Fraw[jl] = m;
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(kCons) : "memory");
+  if (t < 32 * kUKT) {
+    const int kt = t >> 5, lane = t & 31, g = lane >> 2, c = lane & 3;
+    const int j = j0 + g;
+    float dv[4][kUS];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 16 * kt + 2 * c + (e & 1) + 8 * (e >> 1);
+      const double y = (j < g_.q && k < g_.p) ? g_.alpha * Ys[(long long)j * g_.ldy + k] : 0.0;
+      digits7(y, Fraw[g], dv[e]);
+    }
+#pragma unroll
+    for (int i = 0; i < kUS; ++i)
+      Bd[i][kt][lane] = make_uint2(pack_bf16(dv[0][i], dv[1][i]), pack_bf16(dv[2][i], dv[3][i]));
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(kCons) : "memory");
+}
+
+// Direct variant (kCons threads): A read from global memory, 16-row blocks strided over
+// the grid.  For inputs the bulk copy cannot address.
+template <int KT>
+__global__ void __launch_bounds__(kCons)
+k_update_split(const __grid_constant__ UpdArgs g_) {
+  if (g_.need && *g_.need == 0) return;  // conditional product (decided on the device)
+  __shared__ uint2 Bd[kUS][kUKT][32];
+  __shared__ unsigned Fraw[8];
+  const int s = blockIdx.y, j0 = blockIdx.z * 8, warp = threadIdx.x >> 5;
+  y_fragments(g_, g_.Y + s * g_.bsy, j0, Bd, Fraw);
+  const double *As = g_.A + s * g_.bsa;
+  double *Cs = g_.C + s * g_.bsc;
+  const long long nblk = (g_.nrows + 15) >> 4;
+  for (long long blk = (long long)blockIdx.x * kWarps + warp; blk < nblk;
+       blk += (long long)gridDim.x * kWarps)
+    block16<KT>(g_, As + blk * 16, g_.lda, blk * 16, Bd, Fraw, j0, Cs, [] {});
+}
+
+// Staged variant (kCons + 32 threads): warps 0..kWarps-1 consume kRows-row tiles of A
+// from a ring of g_.stages shared-memory stages (kColStride doubles between columns), the
+// last warp fills it with one cp.async.bulk per column.  CTA i takes tiles i, i + gridDim.x,
+// ...  The last tile, if partial, is read from global memory by the consumers.
+template <int KT>
+__global__ void __launch_bounds__(kCons + 32, TPS_UPD_MINB)
+k_update_split_staged(const __grid_constant__ UpdArgs g_) {
+  if (g_.need && *g_.need == 0) return;
+  extern __shared__ __align__(128) double ring[];
+  __shared__ uint2 Bd[kUS][kUKT][32];
+  __shared__ unsigned Fraw[8];
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ int abort_flag;
+  const int s = blockIdx.y, j0 = blockIdx.z * 8, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = g_.stages, p = g_.p;
+  const int stage_d = p * kColStride;  // doubles per stage
+  const long long ntiles = (g_.nrows + kRows - 1) / kRows;
+  const long long nfull = g_.nrows / kRows;
+  const double *As = g_.A + s * g_.bsa;
+  double *Cs = g_.C + s * g_.bsc;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], kWarps);
+    }
+    abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (warp == kWarps) {
+    // ---- producer: one bulk copy of kRows doubles per column of a full tile, spread over
+    // the lanes
+    int last[kMaxStages];
+    for (int i = 0; i < kMaxStages; ++i) last[i] = -1;
+    bool ok = true;
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int st = it % S;
+      const uint32_t round = (uint32_t)(it / S);
+      if (round > 0) {
+        bool w = true;
+        if (lane == 0) w = tc::mbar_wait(&empty[st], (round - 1) & 1u, &g_update_split_err, 11);
+        w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+        if (!w || *((volatile int *)&abort_flag)) {
+          ok = false;
+          break;
+        }
+      }
+      const bool fulltile = tile < nfull;
+      if (lane == 0) {
+        if (fulltile)
+          tc::mbar_arrive_expect_tx(&full[st], (uint32_t)p * kRows * 8);
+        else
+          mbar_arrive(&full[st]);  // partial tile: the consumers read global memory
+      }
+      __syncwarp();
+      if (fulltile)
+        for (int k = lane; k < p; k += 32)
+          bulk_load(ring + st * stage_d + k * kColStride,
+                    As + (long long)k * g_.lda + tile * kRows, kRows * 8, &full[st]);
+      last[st] = fulltile ? (int)(round & 1u) : -1;
+    }
+    if (!ok && lane == 0) atomicExch(&abort_flag, 1);
+    __syncthreads();
+    // after a failed wait anywhere in the CTA, let every copy this warp started land
+    // before the CTA exits (the consumers may have stopped before reading them)
+    if (lane == 0 && *((volatile int *)&abort_flag))
+      for (int i = 0; i < S; ++i)
+        if (last[i] >= 0) tc::mbar_wait(&full[i], (uint32_t)last[i], nullptr, 0);
+    return;
+  }
+  // ---- consumers
+  y_fragments(g_, g_.Y + s * g_.bsy, j0, Bd, Fraw);
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it % S;
+    const uint32_t round = (uint32_t)(it / S);
+    bool w = tc::mbar_wait(&full[st], round & 1u, &g_update_split_err, 12);
+    w = __all_sync(0xffffffffu, w);
+    if (!w || *((volatile int *)&abort_flag)) {
+      if (lane == 0) atomicExch(&abort_flag, 1);
+      break;
+    }
+    const long long row0 = tile * kRows + 16 * warp;
+    auto release = [&] {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    };
+    if (tile < nfull)
+      block16<KT>(g_, ring + st * stage_d + 16 * warp, kColStride, row0, Bd, Fraw, j0, Cs,
+                  release);
+    else
+      block16<KT>(g_, As + row0, g_.lda, row0, Bd, Fraw, j0, Cs, release);
+  }
+  __syncthreads();
+}
+
+using UpdKernel = void (*)(UpdArgs);
+const UpdKernel kStagedK[kUKT] = {k_update_split_staged<1>, k_update_split_staged<2>,
+                                  k_update_split_staged<3>, k_update_split_staged<4>};
+const UpdKernel kDirectK[kUKT] = {k_update_split<1>, k_update_split<2>, k_update_split<3>,
+                                  k_update_split<4>};
+
+int stages_for(int p) {
+  const int stage_bytes = p * kColStride * 8;
+  int S = kRingBytes / stage_bytes;
+  return S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+}
+
+struct StagedCfg {
+  int sms = 0;
+  int per_sm[65] = {0};  // resident staged CTAs per SM by p (0: not yet queried)
+};
+
+// SM count and residency of the staged kernel on the current device (cached per device).
+const StagedCfg &staged_cfg(int p) {
+  static StagedCfg cfg[64];
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  StagedCfg &c = cfg[dev];
+  if (c.sms == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    c.sms = n > 0 ? n : 1;
+    for (int i = 0; i < kUKT; ++i)
+      cudaFuncSetAttribute(kStagedK[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * 64 * kColStride * 8);
+  }
+  if (p >= 1 && p <= 64 && c.per_sm[p] == 0) {
+    int b = 0;
+    const size_t smem = (size_t)stages_for(p) * p * kColStride * 8;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kStagedK[(p + 15) / 16 - 1], kCons + 32,
+                                                  smem);
+    c.per_sm[p] = b > 0 ? b : 1;
+  }
+  return c;
 }
 
 }  // namespace
@@ -247,16 +579,56 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
                   need, false);
     return;
   }
-  const long long blocks64 = (nrows + 63) / 64;
   // p is processed in slabs of 64 rows of Y; the first slab applies beta
   for (int i0 = 0; i0 < p; i0 += 64) {
-    const int pp = p - i0 < 64 ? p - i0 : 64;
-    const long long gx = blocks64 < 152LL * 8 ? blocks64 : 152LL * 8;
-    const dim3 grid((unsigned)gx, batch, (q + 7) / 8);
+    UpdArgs g;
+    g.A = A + (long long)i0 * lda;
+    g.lda = lda;
+    g.bsa = bsa;
+    g.p = p - i0 < 64 ? p - i0 : 64;
+    g.Y = Y + i0;
+    g.ldy = ldy;
+    g.bsy = bsy;
+    g.q = q;
+    g.alpha = alpha;
+    g.beta = i0 == 0 ? beta : 1.0;
+    g.C = C;
+    g.ldc = ldc;
+    g.bsc = bsc;
+    g.nrows = nrows;
+    g.need = need;
+    const int kt = (g.p + 15) / 16 - 1;
+    const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (lda & 1) == 0 &&
+                         (batch == 1 || (bsa & 1) == 0);
+    const long long ntiles = (nrows + kRows - 1) / kRows;
+    const StagedCfg &cfg = staged_cfg(g.p);
     count_launch();
-    k_update_split<<<grid, kUT, 0, s>>>(A + (long long)i0 * lda, lda, bsa, pp, Y + i0, ldy, bsy, q,
-                                        alpha, i0 == 0 ? beta : 1.0, C, ldc, bsc, nrows, need);
+    if (aligned && nrows >= kRows) {
+      g.stages = stages_for(g.p);
+      const long long want = (long long)cfg.sms * cfg.per_sm[g.p];
+      const long long gx = ntiles < want ? ntiles : want;
+      const size_t smem = (size_t)g.stages * g.p * kColStride * 8;
+      g_staged_launches.fetch_add(1, std::memory_order_relaxed);
+      kStagedK[kt]<<<dim3((unsigned)gx, batch, (q + 7) / 8), kCons + 32, smem, s>>>(g);
+    } else {
+      g.stages = 0;
+      const long long blocks = (nrows + kRows - 1) / kRows;
+      const long long gx = blocks < cfg.sms * 4LL ? blocks : cfg.sms * 4LL;
+      kDirectK[kt]<<<dim3((unsigned)gx, batch, (q + 7) / 8), kCons, 0, s>>>(g);
+    }
   }
+}
+
+// Synchronously reads and clears the timed-out-wait flag of the staged update kernel.
+int update_split_status() {
+  if (g_staged_launches.exchange(0) == 0) return 0;
+  int h = 0;
+  if (cudaMemcpyFromSymbol(&h, g_update_split_err, sizeof(int)) != cudaSuccess) return -1;
+  if (h) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(g_update_split_err, &z, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return h;
 }
 
 }  // namespace tps

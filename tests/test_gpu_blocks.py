@@ -41,7 +41,10 @@ def test_gram(ctx, nrows, p, q):
                                             (513, 1, 17, -0.5), (1000, 0, 4, 2.0),
                                             # column tiles 1, 2, 4 (ragged), 8, 8 + 1
                                             (40001, 11, 1, 1.0), (3001, 5, 2, 0.0),
-                                            (131584, 32, 5, -1.0), (20003, 9, 9, 0.5)])
+                                            (131584, 32, 5, -1.0), (20003, 9, 9, 0.5),
+                                            # staged split path: partial last tile, p in
+                                            # two slabs, two column groups
+                                            (131590, 36, 8, 1.0), (200002, 100, 12, -1.0)])
 @pytest.mark.parametrize("dtype", ["f64", "f64_tc"])
 def test_block_update(ctx, nrows, p, q, beta, dtype):
     from paper_2111_02534_gb300 import tps
@@ -60,7 +63,12 @@ def test_block_update(ctx, nrows, p, q, beta, dtype):
     assert np.max(np.abs(host(Cd) - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("nrows,p,q", [(70001, 48, 8), (4099, 64, 13), (1000, 17, 3)])
+@pytest.mark.parametrize("nrows,p,q", [(70001, 48, 8), (4099, 64, 13), (1000, 17, 3),
+                                       # even row counts: A streamed through shared memory
+                                       # by bulk copies (partial last tile, last k tile of
+                                       # 4 and of 8 indices, two column groups)
+                                       (131590, 36, 8), (262144, 64, 8), (100002, 40, 16),
+                                       (64, 9, 2)])
 def test_block_update_tc_graded(ctx, nrows, p, q):
     # digit-split update on data spanning many binades: rows scaled over 1e-12 .. 1e12,
     # entries within a row over 1e-6 .. 1, Y columns over 1e-8 .. 1e8, exact zeros; the

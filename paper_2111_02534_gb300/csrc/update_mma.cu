@@ -5,22 +5,17 @@
 //
 // The products are emulated by error-free digit splitting (the Ozaki scheme: Ozaki,
 // Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), as in the H-apply, with digits sized
-// for a contraction of at most 64 terms:
+// for a contraction of at most 64 terms (split_digits.cuh):
 //  * row r of A gets the exponent E_r with |A[r][k]| < 2^E_r for all k, column j of
-//    alpha Y the exponent F_j; each value becomes the integer q = round(x 2^(54 - E)),
-//    |q| <= 2^54, written in seven base-256 digits, most significant first:
-//    |q| = t 2^48 + c1 2^24 + c2 with t <= 64, and each 24-bit chunk c = d0 2^16 + d1 2^8
-//    + d2 with d0 in [0, 256] and |d1|, |d2| <= 128 (two FP32 roundings, exact), the
-//    sign applied to every digit.  Integers up to 256 are exact in BF16.  Digit i has
-//    the weight 2^(E - 6 - 8 i);
+//    alpha Y the exponent F_j; each value becomes the integer |x| 2^(55 - E), truncated,
+//    written in seven signed base-256 digits, most significant first;
 //  * the digit pairs (i, j) with i + j <= 7 (34 of the 49) are multiplied in BF16 and the
-//    pairs of one level l = i + j are summed in one FP32 accumulator.  With the digit
-//    bounds above, the largest level (l = 5) sums at most 180224 per contraction index, so
-//    over p <= 64 indices every partial sum is an integer below 2^23.5: exact;
-//  * the levels are combined in two int64 Horner sums (levels 0-3 and 4-7, each below
-//    2^48) and scaled by 2^(E_r + F_j - 36) and 2^(E_r + F_j - 68).
-// The dropped levels l >= 8 weigh at most 131072 p 2^(E_r + F_j - 76) < p 2^-59 2^(E_r +
-// F_j) per entry, and the rounding of the operands to 54 bits 2^-55 of the row maximum:
+//    pairs of one level l = i + j are summed in one FP32 accumulator, exactly (every
+//    partial sum is an integer below 2^23.6 for p <= 64);
+//  * the levels are combined in two int64 Horner sums (levels 0-3 and 4-7) and rounded
+//    once to FP64 by integer arithmetic.
+// The dropped levels l >= 8 weigh at most 131072 p 2^(E_r + F_j - 78) < p 2^-61 2^(E_r +
+// F_j) per entry, and the truncation of the operands to 55 bits 2^-55 of the row maximum:
 // the result has the accuracy of an FP64 product, 2^-53 max_k |A[r][k]| sum_k |alpha Y[k][j]|
 // per entry (row-wise, not element-wise).
 //
@@ -43,6 +38,7 @@
 #include <mutex>
 
 #include "ozaki_tc.cuh"
+#include "split_digits.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -55,8 +51,7 @@ std::atomic<long long> g_staged_launches{0};
 
 namespace {
 
-constexpr int kUS = 7;          // base-256 digits per operand
-constexpr int kUL = 8;          // levels kept: i + j <= 7
+using namespace b256;
 constexpr int kUKT = 4;         // k tiles of 16 (p <= 64)
 constexpr int kWarps = 8;       // consumer warps, 16 rows each
 constexpr int kCons = 32 * kWarps;
@@ -65,163 +60,9 @@ constexpr int kColStride = kRows + 4;  // doubles between the columns of a stage
                                        // the four column pairs a warp reads hit disjoint banks)
 constexpr int kMaxStages = 6;
 constexpr int kRingBytes = 100 * 1024;  // stages x stage bytes, at least 2 stages
-constexpr float kMagic = 12582912.f;    // 1.5 2^23: x + kMagic - kMagic = rint(x), |x| <= 2^22
 #ifndef TPS_UPD_MINB
 #define TPS_UPD_MINB 2  // resident staged CTAs per SM the register allocation aims at
 #endif
-
-__device__ __forceinline__ unsigned raw_exp(double x) {
-  return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x in the low half
-  return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// packed pairs of FP32 values (f32x2 arithmetic: two lanes' worth per instruction)
-__device__ __forceinline__ uint64_t f2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2split(uint64_t v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
-// round(x 2^(54 - E)), E = raw_max - 1022 (|x| < 2^E), in signed parts: the top digit t
-// (|t| <= 63) and the 24-bit chunks c1, c2 (|c| < 2^24), |q| = |t| 2^48 + |c1| 2^24 + |c2|,
-// each carrying the sign of x.  Integer arithmetic on the FP64 fields; subnormals and
-// values 2^-63 below the row maximum flush to zero.
-__device__ __forceinline__ void chunks(double x, unsigned raw_max, int &t, int &c1, int &c2) {
-  const int hi = __double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
-  const int ex = (hi >> 20) & 0x7FF;
-  const int sh = (int)raw_max - ex;  // >= 0: q = round(2 mant 2^-sh)
-  const unsigned long long m2 =
-      ((unsigned long long)(((unsigned)hi & 0xFFFFFu) | 0x100000u) << 33) |
-      ((unsigned long long)lo << 1);
-  unsigned long long a = 0;
-  if (ex != 0 && sh < 64) a = (m2 + ((1ULL << sh) >> 1)) >> sh;
-  const int m = hi >> 31;  // 0 or -1
-  t = ((int)(a >> 48) ^ m) - m;
-  c1 = ((int)((a >> 24) & 0xFFFFFFu) ^ m) - m;
-  c2 = ((int)(a & 0xFFFFFFu) ^ m) - m;
-}
-
-// The digits of two values of one row (same exponent), as BF16 pairs: out[i] holds digit i
-// of x0 in its low half and of x1 in its high half.  The base-256 digits of a 24-bit chunk
-// c: d0 = rint(c 2^-16), d1 = rint((c - 2^16 d0) 2^-8), d2 = c - 2^16 d0 - 2^8 d1, all
-// exact FP32 operations (f32x2, both values at once).
-__device__ __forceinline__ void digits_pair(double x0, double x1, unsigned raw_max,
-                                            uint32_t (&out)[kUS]) {
-  int t0, a0, b0, t1, a1, b1;
-  chunks(x0, raw_max, t0, a0, b0);
-  chunks(x1, raw_max, t1, a1, b1);
-  out[0] = pack_bf16((float)t0, (float)t1);
-  const uint64_t M = f2(kMagic, kMagic), nM = f2(-kMagic, -kMagic);
-  const uint64_t s16 = f2(1.f / 65536.f, 1.f / 65536.f), s8 = f2(1.f / 256.f, 1.f / 256.f);
-  const uint64_t m16 = f2(-65536.f, -65536.f), m8 = f2(-256.f, -256.f);
-  const int ca[2] = {a0, b0}, cb[2] = {a1, b1};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    uint64_t f = f2((float)ca[h], (float)cb[h]);          // |c| < 2^24: exact
-    const uint64_t d0 = add2(add2(mul2(f, s16), M), nM);  // |d0| <= 256
-    f = fma2(d0, m16, f);                                 // |f| <= 2^15
-    const uint64_t d1 = add2(add2(mul2(f, s8), M), nM);   // |d1| <= 128
-    const uint64_t d2 = fma2(d1, m8, f);                  // |d2| <= 128
-    float l, u;
-    f2split(d0, l, u);
-    out[1 + 3 * h] = pack_bf16(l, u);
-    f2split(d1, l, u);
-    out[2 + 3 * h] = pack_bf16(l, u);
-    f2split(d2, l, u);
-    out[3 + 3 * h] = pack_bf16(l, u);
-  }
-}
-
-// The seven digits of one value (for alpha Y, once per CTA).
-__device__ __forceinline__ void digits7(double x, unsigned raw_max, float (&d)[kUS]) {
-  int t, a, b;
-  chunks(x, raw_max, t, a, b);
-  d[0] = (float)t;
-  const int ch[2] = {a, b};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float f = (float)ch[h];
-    const float d0 = rintf(f * (1.f / 65536.f));
-    f = fmaf(-d0, 65536.f, f);
-    const float d1 = rintf(f * (1.f / 256.f));
-    d[1 + 3 * h] = d0;
-    d[2 + 3 * h] = d1;
-    d[3 + 3 * h] = fmaf(-d1, 256.f, f);
-  }
-}
-
-__device__ __forceinline__ double pow2d(int e) {
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// (hi 2^32 + lo) 2^(E - 68) rounded to the nearest FP64 value (ties to even), |hi|, |lo| <
-// 2^49, by integer arithmetic (GB300's FP64 pipe issues one warp instruction per ~64 cycles
-// of a sub-partition, the integer pipes one per cycle); results outside the normal range
-// take the FP64 formula, which rounds the same way.
-__device__ __forceinline__ double combine(long long hi, long long lo, int E) {
-  const long long top = hi + (lo >> 32);  // S = top 2^32 + bot exactly, 0 <= bot < 2^32
-  const unsigned bot = (unsigned)lo;
-  const bool neg = top < 0;
-  unsigned long long T;
-  unsigned B;
-  if (!neg) {
-    T = (unsigned long long)top;
-    B = bot;
-  } else if (bot == 0) {
-    T = (unsigned long long)(-top);
-    B = 0;
-  } else {
-    T = (unsigned long long)(-top - 1);
-    B = 0u - bot;
-  }
-  if (T == 0 && B == 0) return 0.0;
-  const int lb = T ? 95 - __clzll((long long)T) : 31 - __clz((int)B);  // leading bit of |S|
-  int sh = lb - 52;
-  unsigned long long mant;
-  if (sh <= 0) {
-    mant = ((T << 32) | B) << (-sh);  // |S| < 2^53: exact
-  } else {                            // sh <= 29: the dropped bits are all in B
-    mant = (T << (32 - sh)) | (B >> sh);
-    const unsigned rem = B & ((1u << sh) - 1u), half = 1u << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ULL))) {
-      ++mant;
-      if (mant >> 53) {
-        mant >>= 1;
-        ++sh;
-      }
-    }
-  }
-  const int be = sh + E - 68 + 52 + 1023;
-  if (be <= 0 || be >= 2047)
-    return fma((double)lo, pow2d(E - 68), (double)hi * pow2d(E - 36));
-  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
-                                          ((unsigned long long)be << 52) |
-                                          (mant & ((1ULL << 52) - 1))));
-}
 
 __device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
   asm volatile(
@@ -264,7 +105,8 @@ struct UpdArgs {
   double *C;
   long long ldc, bsc, nrows;
   const int *need;
-  int stages;  // staged kernel: ring stages
+  int stages;     // staged kernel: ring stages
+  bool has_beta;  // beta != 0: C is read
 };
 
 // One warp: 16 rows (ra = row0 + g, rb = ra + 8) of C's columns j0 .. j0 + 7, with A's
@@ -349,7 +191,7 @@ __device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Str
       }
     }
   }
-  // combine the levels: value = (hi 2^32 + lo) 2^(E + F - 68), hi = levels 0..3, lo =
+  // combine the levels: value = (hi 2^32 + lo) 2^(E + F - 70), hi = levels 0..3, lo =
   // levels 4..7 (Horner in base 256)
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -370,7 +212,7 @@ __device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Str
     const double val =
         (er && fr) ? combine(hi, lo, (int)er - 1022 + (int)fr - 1022) : 0.0;
     double *dst = Cs + (long long)j * g_.ldc + ((t & 2) ? rb : ra);
-    *dst = (g_.beta == 0.0) ? val : fma(g_.beta, *dst, val);
+    *dst = g_.has_beta ? fma(g_.beta, *dst, val) : val;
   }
 }
 
@@ -597,6 +439,7 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
     g.bsc = bsc;
     g.nrows = nrows;
     g.need = need;
+    g.has_beta = g.beta != 0.0;
     const int kt = (g.p + 15) / 16 - 1;
     const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (lda & 1) == 0 &&
                          (batch == 1 || (bsa & 1) == 0);

@@ -61,7 +61,7 @@ enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2, TPS_TF32_TC = 3 };  /* arithmet
 /* TPS_F64_TC: FP64-accurate mode products emulated on the BF16 tensor cores by error-free
  * splitting into six-bit digit slices per operand row (9 for the wave function, 10 for the
  * mode matrices; Ozaki scheme), exact FP32 accumulation per digit level, FP64
- * recombination; 1D H-apply only.
+ * recombination; H-apply only (1D, and 2D with at most 128 points per mode).
  * TPS_TF32_TC: the preconditioner's four mode products on the tensor cores with TF32 inputs
  * (10 explicit mantissa bits) and FP32 accumulation, ~2.5e-3 relative to the exact
  * (T - sigma)^-1 r; 1D preconditioner only. */
@@ -158,10 +158,12 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est);
  * vectors, H = sum_k a_k (I x .. x D2_k x .. x I) + diag(V).  psi_dev, out_dev:
  * device, [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32:
  * FP32 arithmetic (error ~ n eps_32 ||H|| |psi|), the low-precision phase's operator;
- * TPS_F64_TC (1D only): FP64-accurate products on the tensor cores (error below
+ * TPS_F64_TC: FP64-accurate products on the tensor cores (error below
  * 2^-53 n of row max x column max per product, like FP64 arithmetic).  The first
  * TPS_F64_TC call on a context builds the operator's digit slices (a few MB) and a
- * slice workspace of up to 256 MB; TPS_ERR_INVALID_ARG in 2D. */
+ * slice workspace of up to 256 MB (2D: the four mode products one after the other, a
+ * fiber-slice workspace of up to 1 GB; TPS_ERR_INVALID_ARG for more than 128 points in a
+ * mode). */
 int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, double theta,
                 int dtype, cudaStream_t stream);
 
@@ -213,7 +215,8 @@ typedef struct tps_solver_opts {
   int refine_inner_dtype; /* arithmetic of H inside the refinement's GMRES (TPS_F64 default) */
   int h64_dtype;      /* how every FP64 H-apply of the solver runs (refinement phase, FP64-only
                          mode, final Rayleigh quotients): TPS_F64_TC (default: tensor-core
-                         emulation, 1D; 2D solves use the FMA pipe) or TPS_F64 (FMA pipe) */
+                         emulation; 2D grids with more than 128 points in a mode use the FMA
+                         pipe) or TPS_F64 (FMA pipe) */
   int rr_method;      /* Rayleigh-Ritz eigensolver: TPS_RR_MIXED (default) or TPS_RR_JACOBI64 */
   int rr_refine_max;  /* TPS_RR_MIXED: FP64 refinement iterations before the FP64 Jacobi
                          takes over (0: 12) */

@@ -693,8 +693,10 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
   if ((dtype != TPS_F64 && dtype != TPS_F32 && dtype != TPS_F64_TC) || nvec < 0 ||
       (nvec > 0 && (!psi_dev || !out_dev)) || !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_h arguments");
-  if (dtype == TPS_F64_TC && ctx->dim != 1)
-    return set_error(ctx, TPS_ERR_INVALID_ARG, "TPS_F64_TC is implemented for 1D only");
+  if (dtype == TPS_F64_TC && ctx->dim == 2)
+    for (int k = 0; k < 4; ++k)
+      if (ctx->n[k] > 128)
+        return set_error(ctx, TPS_ERR_INVALID_ARG, "TPS_F64_TC in 2D needs n <= 128 per mode");
   const char *a = (const char *)psi_dev, *b = (const char *)out_dev;
   const size_t bytes = (size_t)nvec * ctx->full.N * sizeof(double);
   if (nvec > 0 && a < b + bytes && b < a + bytes)

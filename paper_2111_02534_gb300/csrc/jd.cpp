@@ -597,8 +597,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
     const int st_tf = ensure_tf_operator(op);  // allocation errors here, not mid-solve
     if (st_tf) return set_error(ctx, st_tf, "building the TF32 preconditioner operator failed");
   }
-  // the tensor-core FP64 H-apply exists for the 1D operator; 2D solves use the FMA pipe
-  w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && op.nmodes == 2) ? TPS_F64_TC : TPS_F64;
+  // the tensor-core FP64 H-apply: 1D, and 2D with at most 128 points per mode (else the
+  // FMA pipe)
+  bool tc_ok = op.nmodes == 2;
+  if (op.nmodes == 4) {
+    tc_ok = true;
+    for (int kk = 0; kk < 4; ++kk) tc_ok = tc_ok && op.n[kk] <= 128;
+  }
+  w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && tc_ok) ? TPS_F64_TC : TPS_F64;
   if (w.h64_dtype == TPS_F64_TC)
     TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));  // allocation errors here, not mid-solve
   const long long launches0 = g_kernel_launches.load();

@@ -45,6 +45,7 @@
 #include <mutex>
 
 #include "ozaki_tc.cuh"
+#include "split_digits.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -61,7 +62,7 @@ constexpr int kBN = 48;        // output columns per CTA; kLevels * kBN <= 512 T
 constexpr int kBK = 64;        // contraction depth per stage (128-byte rows)
 constexpr int kAStages = 6;  // A tiles in flight: each carries ~600 cycles of MMA work
 constexpr int kBStages = 2;  // a power of two (stage index by mask)
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // 8 warps drain the accumulators (two per TMEM lane quarter)
 constexpr uint32_t kATileBytes = kBM * 128;
 constexpr uint32_t kTmemCols = 512;
 static_assert(kLevels * kBN <= (int)kTmemCols, "levels must fit in tensor memory");
@@ -199,6 +200,63 @@ __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs
 }
 
 
+// Exponents and digit slices of the fibers of one mode of a batch of 2D tensors (the
+// contraction index of that mode's product), for a mode with stride sigma >= 32: fiber m
+// of vector v holds the nk elements X[v bs + (m / sigma) nk sigma + m % sigma + i sigma],
+// i < nk.  Writes the fiber's raw exponent maximum fexp[v M + m] and its S digit slices
+// out[((v S + plane) M + m) ld + i] (most significant first).  Block: 256 threads over 32
+// fibers (nk <= kMaxFiber); reads run across fibers (adjacent in memory), writes along
+// them.  (The fibers of the fastest mode are the rows of the tensor: k_split.)
+constexpr int kMaxFiber = 128;
+__global__ void __launch_bounds__(256)
+k_split_fibers(const double *__restrict__ X, long long bs, long long M, int nk, long long sigma,
+               int S, unsigned *__restrict__ fexp, uint16_t *__restrict__ out, int ld) {
+  __shared__ double tile[32][kMaxFiber + 1];
+  __shared__ unsigned ex[32];
+  __shared__ long long base[32];
+  const int v = blockIdx.y, tid = threadIdx.x;
+  const long long m0 = (long long)blockIdx.x * 32;
+  const double *Xv = X + (long long)v * bs;
+  if (tid < 32) {
+    const long long m = m0 + tid;
+    base[tid] = m < M ? (m / sigma) * (nk * sigma) + m % sigma : -1;
+  }
+  __syncthreads();
+  {
+    const int f = tid & 31;
+    const long long b = base[f];
+    for (int i = tid >> 5; i < nk; i += 8) tile[f][i] = b >= 0 ? Xv[b + (long long)i * sigma] : 0.0;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    unsigned mx = 0;
+    for (int i = 0; i < nk; ++i) {
+      const unsigned r = raw_exponent(tile[tid][i]);
+      mx = r > mx ? r : mx;
+    }
+    ex[tid] = mx;
+    if (m0 + tid < M) fexp[(long long)v * M + m0 + tid] = mx;
+  }
+  __syncthreads();
+  const long long plane = M * ld;
+  for (int f = tid >> 4; f < 32; f += 16) {
+    const long long m = m0 + f;
+    if (m >= M) continue;
+    uint16_t *row = out + ((long long)v * S) * plane + m * ld;
+    for (int i = tid & 15; i < nk; i += 16) {
+      long long q = scaled_integer(tile[f][i], ex[f], S);
+      uint16_t *dst = row + i;
+      for (int j = S - 1; j > 0; --j) {
+        long long d = q & 63;
+        if (d >= 32) d -= 64;
+        dst[j * plane] = bf16_of_int((int)d);
+        q = (q - d) >> kBeta;
+      }
+      dst[0] = bf16_of_int((int)q);
+    }
+  }
+}
+
 // ------------------------------ the product kernel ------------------------------
 struct OzArgs {
   int M, N, K;
@@ -208,8 +266,9 @@ struct OzArgs {
   long long expA_bs;
   const unsigned *expB;          // raw row exponents of B [.][N]
   long long expB_bs;
-  double *out;                   // out[v * out_bs + n * ldo + m]
-  long long ldo, out_bs;
+  double *out;                   // out[v * out_bs + idx(m, n)], idx = n * ldo + m, or with
+  long long ldo, out_bs;         // inner > 0: (m / inner) * outer + m % inner + n * inner
+  long long inner, outer;        // (the 2D mode products: m a fiber, n the mode index)
   int epi;                       // 0 store, 1 accumulate, 2 store + (V - theta_v) psi,
                                  // 3 atomic add, 4 atomic add with (V - theta_v) psi
   const double *V;               // [n * ldo + m]
@@ -219,9 +278,12 @@ struct OzArgs {
   int *err;                      // nonzero after a timed-out wait
 };
 
-__device__ __forceinline__ double pow2i(int e) {
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __longlong_as_double((long long)(e + 1023) << 52);
+// (hi 2^30 + lo) 2^(E - 66) rounded to the nearest FP64 value, |hi|, |lo| < 2^49: as
+// (top 2^32 + 4 bot) 2^(E - 68) with top = hi + floor(lo / 2^30), bot = lo mod 2^30.
+__device__ __forceinline__ double combine30(long long hi, long long lo, int E) {
+  const long long top = hi + (lo >> 30);
+  const long long bot4 = (lo & 0x3FFFFFFFLL) << 2;
+  return b256::combine(top, bot4, E + 2);
 }
 
 // One CTA computes the 128 x kBN tile (m0, n0) of C = A B^T for vector blockIdx.z, with
@@ -370,51 +432,77 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
   const int aborted = __shfl_sync(0xffffffffu, *((volatile int *)&abort_flag), 0);
   tc::tc_fence_after();
   if (ok && !aborted) {
-    const int m = m0 + 32 * warp + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and columns of half w / 4
+    const int quarter = warp & 3, half = warp >> 2;
+    const int m = m0 + 32 * quarter + lane;
     const bool mvalid = m < g.M;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
     const int Em = mvalid ? (int)g.expA[v * g.expA_bs + m] - 1022 : 0;
     const bool vterm = g.epi == 2 || g.epi == 4;
+    // output index of (m, n): mbase + n * nstride (one division per thread, not per output)
+    const long long mbase = g.inner ? (long long)(m / g.inner) * g.outer + m % g.inner : m;
+    const long long nstride = g.inner ? g.inner : g.ldo;
     const double th = vterm ? (g.theta_dev ? g.theta_dev[v] : g.theta0) : 0.0;
-    const int h = (L + 1) / 2;
-    for (int c = 0; c < kBN / 8; ++c) {
+    static_assert(kBN % 16 == 0, "two column halves of whole 8-column groups");
+    for (int c = half * (kBN / 16); c < (half + 1) * (kBN / 16); ++c) {
       long long hi[8], lo[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
       // all levels of these 8 columns in flight at once, one wait
       uint32_t r[kLevels][8];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l)
-        if (l < L) tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r[l]);
+      for (int l = 0; l < kLevels; ++l) tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r[l]);
       tc::tmem_ld_wait();
+      // levels 0..4 and 5..9 in base 64: pairs of levels fit in 32 bits (|D_l| < 2^24)
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) {
-        if (l >= L) break;
+      for (int q = 0; q < 8; ++q) {
+        int d[kLevels];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const long long d = (long long)__float2int_rn(__uint_as_float(r[l][q]));
-          if (l < h)
-            hi[q] = hi[q] * 64 + d;
-          else
-            lo[q] = lo[q] * 64 + d;
-        }
+        for (int l = 0; l < kLevels; ++l) d[l] = __float2int_rn(__uint_as_float(r[l][q]));
+        hi[q] = (long long)(d[0] * 64 + d[1]) * (1LL << 18) + (long long)(d[2] * 64 + d[3]) * 64 +
+                d[4];
+        lo[q] = (long long)(d[5] * 64 + d[6]) * (1LL << 18) + (long long)(d[7] * 64 + d[8]) * 64 +
+                d[9];
       }
       if (!mvalid) continue;
+      // the group's 8 outputs: every load (V and psi for the potential term, the previous
+      // value for an accumulating store) is issued before any store, so the loads' latency
+      // is paid once per group, not once per output
+      static_assert(kLevels == 10 && kBeta == 6, "hi 2^30 + lo needs levels 0..4 / 5..9");
+      double val[8], ld1[8], ld2[8];
+      long long idx[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + c * 8 + q;
+        idx[q] = mbase + (long long)(n < g.N ? n : n0) * nstride;
+        ld1[q] = ld2[q] = 0.0;
+        if (n < g.N) {
+          if (vterm) {
+            ld1[q] = g.V[idx[q]];
+            ld2[q] = g.psi[v * g.out_bs + idx[q]];
+          } else if (g.epi == 1) {
+            ld1[q] = g.out[v * g.out_bs + idx[q]];
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int n = n0 + c * 8 + q;
         if (n >= g.N) break;
         const int En = (int)g.expB[v * g.expB_bs + n] - 1022;
-        // sum_l D_l 2^(-beta (l + 2)): hi carries levels 0 .. h-1, lo levels h .. L-1
-        const double val = fma((double)lo[q], pow2i(Em + En - kBeta * (L + 1)),
-                               (double)hi[q] * pow2i(Em + En - kBeta * (h + 1)));
-        const long long idx = (long long)n * g.ldo + m;
-        double *o = g.out + v * g.out_bs + idx;
-        const double add = vterm ? fma(g.V[idx] - th, g.psi[v * g.out_bs + idx], val) : val;
+        // sum_l D_l 2^(-beta (l + 2)) = (hi 2^30 + lo) 2^(Em + En - 66), hi carrying levels
+        // 0 .. 4 and lo levels 5 .. 9, rounded once to FP64 by integer arithmetic (GB300's
+        // FP64 pipe issues a warp instruction per ~64 cycles of a sub-partition)
+        val[q] = combine30(hi[q], lo[q], Em + En);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + c * 8 + q;
+        if (n >= g.N) break;
+        double *o = g.out + v * g.out_bs + idx[q];
+        const double add = vterm ? fma(ld1[q] - th, ld2[q], val[q]) : val[q];
         if (g.epi == 0 || g.epi == 2)
           *o = add;
         else if (g.epi == 1)
-          *o += add;
+          *o = ld1[q] + add;
         else
           atomicAdd(o, add);  // epi 3, 4: one of exactly two terms added to a zeroed output
       }
@@ -449,6 +537,20 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUte
     oz_tile<kPsiSlices, kOpSlices>(&tmA2, &tmB2, g2, m0, n0, v, smem_raw);
 }
 
+
+// One product C = A B^T (A = wave-function fiber slices, 9 digits; B = mode-matrix slices,
+// 10 digits) over tiles m fastest, then n, then the vector: a mode product of the 2D
+// H-apply.
+__global__ void __launch_bounds__(kThreads, 1)
+k_oz_gemm1(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ OzArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const int tm = (g.M + kBM - 1) / kBM, tn = (g.N + kBN - 1) / kBN;
+  const int r = (int)blockIdx.x;
+  const int v = r / (tm * tn), t = r % (tm * tn);
+  const int m0 = (t % tm) * kBM, n0 = (t / tm) * kBN;
+  oz_tile<kPsiSlices, kOpSlices>(&tmA, &tmB, g, m0, n0, v, smem_raw);
+}
 
 // ------------------------------------ host ------------------------------------
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -530,8 +632,9 @@ cudaError_t launch_oz_pair(const CUtensorMap &mA1, const CUtensorMap &mB1, const
 
 }  // namespace
 
-// Tensor-core (BF16 digit) form of a 1D operator: slices of K_y and K_x, fixed, and a
-// workspace for the slices of up to `chunk` vectors per launch.
+// Tensor-core (BF16 digit) form of an operator: 1D -- slices of K_y and K_x, fixed, and a
+// workspace for the slices of up to `chunk` vectors per launch; 2D -- slices of the four
+// K_k, and one workspace for the fiber slices of one mode at a time.
 struct TcOperator {
   int So = kOpSlices, Sp = kPsiSlices;
   int nx = 0, ny = 0, ldx = 0, ldy = 0, chunk = 0;
@@ -541,10 +644,26 @@ struct TcOperator {
   unsigned *eP = nullptr;                   // row exponents [chunk][nx], then column [chunk][ny]
   int *err = nullptr;                       // device flag of timed-out waits
   CUtensorMap mKy, mKx, mPn, mPT;
+  // 2D: mode k has n4[k] points, stride sig4[k] in the vector layout and M4[k] = N / n4[k]
+  // fibers; K4[k] [So][n][ld], fiber slices F [chunk][Sp][M4[k]][ld4[k]], exponents eF
+  bool two_d = false;
+  int n4[4] = {0, 0, 0, 0}, ld4[4] = {0, 0, 0, 0};
+  long long M4[4] = {0, 0, 0, 0}, sig4[4] = {0, 0, 0, 0};
+  uint16_t *K4[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned *eK4[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint16_t *F = nullptr;
+  unsigned *eF = nullptr;
+  CUtensorMap mK4[4], mF4[4];
 };
 
 void free_tc_operator(TcOperator *t) {
   if (!t) return;
+  for (int k = 0; k < 4; ++k) {
+    cudaFree(t->K4[k]);
+    cudaFree(t->eK4[k]);
+  }
+  cudaFree(t->F);
+  cudaFree(t->eF);
   cudaFree(t->Ky);
   cudaFree(t->Kx);
   cudaFree(t->eKy);
@@ -556,9 +675,70 @@ void free_tc_operator(TcOperator *t) {
   delete t;
 }
 
-// Build the tensor-core form of a 1D operator (idempotent).  Returns a cudaError_t.
+// The tensor-core form of a 2D operator (four modes).
+cudaError_t ensure_tc_operator_2d(const DevOperator &op, cudaStream_t s) {
+  TcOperator *t = new TcOperator();
+  t->two_d = true;
+  const int So = t->So, Sp = t->Sp;
+  long long maxw = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (op.n[k] < 1 || op.n[k] > kMaxFiber) {
+      delete t;
+      return cudaErrorInvalidValue;
+    }
+    t->n4[k] = op.n[k];
+    t->ld4[k] = round8(op.n[k]);
+    t->M4[k] = op.N / op.n[k];
+    long long sg = 1;
+    for (int j = k + 1; j < 4; ++j) sg *= op.n[j];
+    t->sig4[k] = sg;
+    const long long w = t->M4[k] * t->ld4[k];
+    maxw = w > maxw ? w : maxw;
+  }
+  // vectors per chunk: as many as keep the fiber-slice workspace near 1 GB
+  long long ch = (1LL << 30) / (2LL * Sp * maxw);
+  t->chunk = (int)(ch < 1 ? 1 : (ch > 64 ? 64 : ch));
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  for (int k = 0; k < 4; ++k) {
+    chk(cudaMalloc(&t->K4[k], 2LL * So * t->n4[k] * t->ld4[k]));
+    chk(cudaMalloc(&t->eK4[k], sizeof(unsigned) * t->n4[k]));
+  }
+  long long maxM = 0;
+  for (int k = 0; k < 4; ++k) maxM = t->M4[k] > maxM ? t->M4[k] : maxM;
+  chk(cudaMalloc(&t->F, 2LL * Sp * t->chunk * maxw));
+  chk(cudaMalloc(&t->eF, sizeof(unsigned) * t->chunk * maxM));
+  chk(cudaMalloc(&t->err, sizeof(int)));
+  if (e != cudaSuccess) {
+    free_tc_operator(t);
+    return e;
+  }
+  chk(cudaMemsetAsync(t->err, 0, sizeof(int), s));
+  bool ok = true;
+  for (int k = 0; k < 4; ++k) {
+    const int n = t->n4[k];
+    chk(cudaMemsetAsync(t->eK4[k], 0, sizeof(unsigned) * n, s));
+    launch_exponents(op.K[k], n, n, 0, 1, t->eK4[k], nullptr, s);
+    launch_split(op.K[k], n, n, 0, 1, So, t->eK4[k], t->K4[k], t->ld4[k], nullptr, nullptr, 0, s);
+    ok = ok && make_slice_map(&t->mK4[k], t->K4[k], n, n, So, t->ld4[k], kBN) &&
+         make_slice_map(&t->mF4[k], t->F, n, t->M4[k], (long long)Sp * t->chunk, t->ld4[k], kBM);
+  }
+  chk(cudaGetLastError());
+  if (e == cudaSuccess && !ok) e = cudaErrorInvalidValue;
+  if (e != cudaSuccess) {
+    free_tc_operator(t);
+    return e;
+  }
+  op.tc = t;
+  return cudaSuccess;
+}
+
+// Build the tensor-core form of an operator (idempotent).  Returns a cudaError_t.
 cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s) {
   if (op.tc) return cudaSuccess;
+  if (op.nmodes == 4) return ensure_tc_operator_2d(op, s);
   if (op.nmodes != 2) return cudaErrorInvalidValue;
   TcOperator *t = new TcOperator();
   t->nx = op.n[0];
@@ -607,11 +787,81 @@ cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// 2D H-apply (Eq. tensor_op2D): the four mode products one after the other, each as
+// C[m][j] = sum_i Psi[fiber m][i] K_k[j][i] over the fibers of mode k (A = fiber slices,
+// B = K_k slices); the y2 product stores its tiles with the (V - theta) Psi term, the
+// other three add theirs (one CTA per output tile in each launch, so the sum is
+// deterministic).
+cudaError_t launch_apply_h_tc_2d(const DevOperator &op, const double *psi, double *out,
+                                 int nvec, const double *theta_dev, double theta,
+                                 cudaStream_t s) {
+  TcOperator &t = *op.tc;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_oz_gemm1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oz_smem_bytes(kMaxSlices));
+  });
+  if (attr != cudaSuccess) return attr;
+  for (int v0 = 0; v0 < nvec; v0 += t.chunk) {
+    const int nv = nvec - v0 < t.chunk ? nvec - v0 : t.chunk;
+    const double *P = psi + (long long)v0 * op.N;
+    double *O = out + (long long)v0 * op.N;
+    for (int k = 3; k >= 0; --k) {
+      const long long M = t.M4[k];
+      const int n = t.n4[k];
+      if (t.sig4[k] == 1) {  // the fibers are the rows of the [M][n] view
+        const cudaError_t me = cudaMemsetAsync(t.eF, 0, sizeof(unsigned) * nv * M, s);
+        if (me != cudaSuccess) return me;
+        launch_exponents(P, (int)M, n, op.N, nv, t.eF, nullptr, s);
+        launch_split(P, (int)M, n, op.N, nv, t.Sp, t.eF, t.F, t.ld4[k], nullptr, nullptr, 0, s);
+      } else {
+        count_launch();
+        k_split_fibers<<<dim3((unsigned)((M + 31) / 32), nv), 256, 0, s>>>(
+            P, op.N, M, n, t.sig4[k], t.Sp, t.eF, t.F, t.ld4[k]);
+      }
+      OzArgs g;
+      std::memset(&g, 0, sizeof(g));
+      g.L = kLevels;
+      g.M = (int)M;
+      g.N = n;
+      g.K = n;
+      g.SA = t.Sp;
+      g.SB = t.So;
+      g.zA = t.Sp;
+      g.zB = 0;
+      g.expA = t.eF;
+      g.expA_bs = M;
+      g.expB = t.eK4[k];
+      g.expB_bs = 0;
+      g.out = O;
+      g.out_bs = op.N;
+      g.inner = t.sig4[k];
+      g.outer = (long long)n * t.sig4[k];
+      g.epi = k == 3 ? 2 : 1;
+      g.V = op.V;
+      g.psi = P;
+      g.theta_dev = theta_dev ? theta_dev + v0 : nullptr;
+      g.theta0 = theta;
+      g.err = t.err;
+      const long long tiles = ((M + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * nv;
+      if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+      count_launch();
+      k_oz_gemm1<<<(unsigned)tiles, kThreads, oz_smem_bytes(kMaxSlices), s>>>(t.mF4[k],
+                                                                            t.mK4[k], g);
+      const cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) return le;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *out, int nvec,
                               const double *theta_dev, double theta, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   cudaError_t e = ensure_tc_operator(op, s);
   if (e != cudaSuccess) return e;
+  if (op.nmodes == 4) return launch_apply_h_tc_2d(op, psi, out, nvec, theta_dev, theta, s);
   TcOperator &t = *op.tc;
   const int nx = t.nx, ny = t.ny, So = t.So, Sp = t.Sp;
   for (int v0 = 0; v0 < nvec; v0 += t.chunk) {

@@ -77,15 +77,60 @@ def test_apply_h_tc_matches_fp64_path(n, nvec):
     ctx.close()
 
 
-def test_apply_h_tc_rejects_2d():
+@pytest.mark.parametrize("n,nvec,theta", [((8, 8, 6, 6), 2, 0.0), ((6, 6, 10, 10), 3, -0.4),
+                                          ((12, 12, 8, 8), 1, 0.7), ((4, 4, 4, 4), 2, 0.0)])
+def test_apply_h_tc_2d_vs_oracle(n, nvec, theta):
+    """Eq. tensor_op2D with the four mode products on the tensor cores, against the
+    oracle's Kronecker-sum apply, element by element (the same bar as the FP64 path)."""
     require_gpu()
     tps = _tps()
-    ctx = make_ctx_2d(20.0, 1.0, (8, 8, 8, 8), (5.0,) * 4, 1.0, 1.0)
-    N = ctx.info()[0]
-    x = torch.zeros(1, N, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
-    with pytest.raises(tps.TpsError):
-        ctx.apply_h(x, y, 0.0, dtype=tps.F64_TC)
+    from oracle.hamiltonian import problem_2d
+    L = (5.0, 5.0, 4.0, 4.0)
+    P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+    ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    psi = random_block(nvec, P.N, 11 + nvec)
+    out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_h(dev(psi), out, theta, dtype=tps.F64_TC)
+    ctx.device_status()
+    got = host(out)
+    ref = P.apply_kron(psi, theta)
+    hn = P.norm_estimate()
+    err = np.linalg.norm(got - ref, axis=1) / (hn * np.linalg.norm(psi, axis=1))
+    assert err.max() <= 1e-12, err.max()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * hn * np.abs(psi).max()
+    ctx.close()
+
+
+def test_apply_h_tc_2d_full_size():
+    """The 48^4 workload (5.3 M unknowns) with more vectors than one fiber-slice chunk:
+    sampled rows against the oracle, whole vectors against the FP64-FMA path, and the same
+    bits on a second call."""
+    require_gpu()
+    tps = _tps()
+    from oracle.hamiltonian import problem_2d
+    w = WORKLOADS["2d_n48"]
+    P = problem_2d(w.M, w.m, w.hbar, w.n, w.L, w.v0, w.sigma)
+    ctx = make_ctx_2d(w.M, w.m, w.n, w.L, w.v0, w.sigma)
+    N, hn = ctx.info()
+    nvec = 12
+    psi = dev(random_normal_block(nvec, N, 5))
+    a = torch.empty_like(psi)
+    b = torch.empty_like(psi)
+    ctx.apply_h(psi, a, -0.3, dtype=tps.F64)
+    ctx.apply_h(psi, b, -0.3, dtype=tps.F64_TC)
+    ctx.device_status()
+    d = (a - b).norm(dim=1) / (hn * psi.norm(dim=1))
+    assert float(d.max()) <= 1e-14, float(d.max())
+    rows = np.random.default_rng(3).choice(N, 48, replace=False)
+    ph = host(psi)
+    got = host(b)
+    for v in (0, nvec - 1):
+        ref = P.apply_rows(ph[v], rows, -0.3)
+        assert np.max(np.abs(got[v][rows] - ref)) <= 1e-12 * hn * np.abs(ph[v]).max()
+    c = torch.empty_like(psi)
+    ctx.apply_h(psi, c, -0.3, dtype=tps.F64_TC)
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
     ctx.close()
 
 

@@ -4,6 +4,7 @@ Calls only oracle/ (never the CUDA path).  Usage: python tests/golden/make_golde
   1d_n512 : M/m = 40, n = 512 per coordinate on [-20, 20), v0 tuned to E0 = 1e-3 on the
             y grid (heavy-light reduced mass), sigma = 1, 8 lowest x-even eigenpairs.
   2d_n16  : 2D, M/m = 20, n = 16 per component on [-10, 10), v0 = 2, 4 lowest pairs.
+  2d_n24  : 2D, M/m = 20, n = 24 per component on [-12, 12), v0 = 2, 4 lowest pairs.
   sweep   : the 256 instances of inputs.sweep_instances(), 4 lowest x-even pairs each.
 """
 import json
@@ -49,6 +50,18 @@ def make_2d_n16():
             "seconds": time.time() - t, "method": "oracle.eig.lowest_iterative (LOBPCG), all states"}
 
 
+def make_2d_n24():
+    # 2D between the oracle-checked 16^4 and the 48^4 workload: 24 points per component
+    # on [-12, 12) (331,776 unknowns)
+    P = problem_2d(20.0, 1.0, 1.0, (24, 24, 24, 24), (12.0,) * 4, 2.0, 1.0)
+    t = time.time()
+    lam, X = lowest_iterative(P, 4, ANY, tol=1e-12, extra=6)
+    res = residual_norms(P, X, lam) / P.norm_estimate()
+    return {"workload": "2d_n24", "M": 20.0, "m": 1.0, "n": [24] * 4, "L": [12.0] * 4,
+            "v0": 2.0, "sigma": 1.0, "evals": lam.tolist(), "rel_resid": res.tolist(),
+            "seconds": time.time() - t, "method": "oracle.eig.lowest_iterative (LOBPCG), all states"}
+
+
 def _sweep_one(args):
     import os
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -75,7 +88,8 @@ def make_sweep():
             "method": "oracle.eig.lowest_iterative (LOBPCG), x-even sector, 4 pairs per instance"}
 
 
-MAKERS = {"1d_n512": make_1d_n512, "2d_n16": make_2d_n16, "sweep": make_sweep}
+MAKERS = {"1d_n512": make_1d_n512, "2d_n16": make_2d_n16, "2d_n24": make_2d_n24,
+          "sweep": make_sweep}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(MAKERS)

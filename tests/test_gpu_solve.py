@@ -221,6 +221,21 @@ def test_solve_2d_small_against_oracle():
     _check_vectors(P, lam, X)
 
 
+@pytest.mark.parametrize("h64_dtype", [0, 2])
+def test_solve_2d_n24_against_oracle(h64_dtype):
+    """The 2D solve at 24^4 (331,776 unknowns, between the brute-force-checked 16^4 and the
+    48^4 workload): the 4 lowest eigenvalues against the oracle's LOBPCG values, with the
+    FP64 H-applies on the FMA pipe and on the tensor cores."""
+    require_gpu()
+    tps = _tps()
+    with open(os.path.join(GOLD, "evals_2d_n24.json")) as f:
+        gold = json.load(f)
+    ctx = make_ctx_2d(gold["M"], gold["m"], gold["n"], gold["L"], gold["v0"], gold["sigma"])
+    lam, X, st = _solve(ctx, 4, tps.ANY, 8, h64_dtype=h64_dtype)
+    ref = np.array(gold["evals"])
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+
+
 def test_solve_workload_2d_n48_certified():
     # full 2D workload: certified by the oracle's residual (Weyl bound) at 1e-10 relative
     require_gpu()

@@ -77,6 +77,27 @@ def test_apply_h_tc_matches_fp64_path(n, nvec):
     ctx.close()
 
 
+def test_apply_h_tc_full_size_vs_oracle():
+    """The 512 x 512 grid with 30 vectors (more than one slice-workspace chunk of 27):
+    sampled rows of the first and last vectors against the oracle's row-by-row apply."""
+    require_gpu()
+    tps = _tps()
+    P = problem_1d(40.0, 1.0, 1.0, (512, 512), (20.0, 20.0), 0.0185, 1.0)
+    ctx = make_ctx_1d(40.0, 1.0, (512, 512), (20.0, 20.0), 0.0185, 1.0)
+    N, hn = ctx.info()
+    nvec = 30
+    psi = random_normal_block(nvec, N, 13)
+    out = torch.empty(nvec, N, dtype=torch.float64, device="cuda")
+    ctx.apply_h(dev(psi), out, -0.01, dtype=tps.F64_TC)
+    ctx.device_status()
+    got = host(out)
+    rows = np.random.default_rng(17).choice(N, 96, replace=False)
+    for v in (0, 26, 27, nvec - 1):
+        ref = P.apply_rows(psi[v], rows, -0.01)
+        assert np.max(np.abs(got[v][rows] - ref)) <= 1e-12 * hn * np.abs(psi[v]).max()
+    ctx.close()
+
+
 @pytest.mark.parametrize("n,nvec,theta", [((8, 8, 6, 6), 2, 0.0), ((6, 6, 10, 10), 3, -0.4),
                                           ((12, 12, 8, 8), 1, 0.7), ((4, 4, 4, 4), 2, 0.0)])
 def test_apply_h_tc_2d_vs_oracle(n, nvec, theta):

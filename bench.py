@@ -44,7 +44,7 @@ TC_PAIRS = 54
 # DRAM bytes (read + write) per launch of each kernel, mean over the launches of one ncu
 # capture of the kernel on this workload; a kernel that changes after its capture is
 # removed from this table
-TRAFFIC_BYTES_PER_LAUNCH = {"k_gram": 42.13e6, "k_oz_gemm": 49.35e6, "k_tf32_gemm": 5.08e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_gram": 42.13e6, "k_tf32_gemm": 5.08e6}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
 # BF16 digit-pair products per FP64 multiply-add of the split block update
 SPLIT_UPDATE_PAIRS = 34

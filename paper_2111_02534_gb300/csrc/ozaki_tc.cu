@@ -469,11 +469,13 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
       static_assert(kLevels == 10 && kBeta == 6, "hi 2^30 + lo needs levels 0..4 / 5..9");
       double val[8], ld1[8], ld2[8];
       long long idx[8];
+      int En[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int n = n0 + c * 8 + q;
         idx[q] = mbase + (long long)(n < g.N ? n : n0) * nstride;
         ld1[q] = ld2[q] = 0.0;
+        En[q] = n < g.N ? (int)g.expB[v * g.expB_bs + n] - 1022 : 0;
         if (n < g.N) {
           if (vterm) {
             ld1[q] = g.V[idx[q]];
@@ -487,11 +489,10 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
       for (int q = 0; q < 8; ++q) {
         const int n = n0 + c * 8 + q;
         if (n >= g.N) break;
-        const int En = (int)g.expB[v * g.expB_bs + n] - 1022;
         // sum_l D_l 2^(-beta (l + 2)) = (hi 2^30 + lo) 2^(Em + En - 66), hi carrying levels
         // 0 .. 4 and lo levels 5 .. 9, rounded once to FP64 by integer arithmetic (GB300's
         // FP64 pipe issues a warp instruction per ~64 cycles of a sub-partition)
-        val[q] = combine30(hi[q], lo[q], Em + En);
+        val[q] = combine30(hi[q], lo[q], Em + En[q]);
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {

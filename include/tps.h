@@ -110,6 +110,18 @@ int tps_set_alpha(tps_ctx *ctx, double alpha);
  * n_x1 = n_x2 and n_y1 = n_y2 (with equal L) are required. */
 int tps_set_grid(tps_ctx *ctx, const int *n, const double *L);
 
+/* Sec. 3.1, the paper's own discretisation (1D contexts): each coordinate on the n[k]
+ * roots of the Chebyshev polynomial T_n mapped to the real line by y = L t / sqrt(1 - t^2)
+ * (tps_chebyshev_grid), with the dense non-symmetric D2 there; n[k] even in [4, 1024],
+ * L[k] > 0 (the map parameter).  Replaces the Fourier grid of tps_set_grid.  Builds the
+ * operators a_k D2_k, their eigen-decompositions D2 = S diag(lam) S^-1 (a real spectrum;
+ * TPS_ERR_SINGULAR otherwise) for the Sec. 4.2 preconditioner, which then applies S^-1 where
+ * the Fourier grid applies S^T.  Pair potentials are evaluated at the mapped points; the
+ * heavy-exchange sectors fold the mirror-image nodes x_i = -x_{n-1-i}; tps_solve runs a
+ * Jacobi-Davidson method for non-symmetric H (Ritz pairs of the non-symmetric projected
+ * matrix, Sec. 4.1); tps_apply_prec accepts TPS_F64 and TPS_F32 only. */
+int tps_set_grid_chebyshev(tps_ctx *ctx, const int *n, const double *L);
+
 /* Sec. 3.3 (Eq. tensor_form): an arbitrary diagonal potential V[N] in the vector
  * layout (no structure assumed), copied in.  on_device != 0: V is a device
  * pointer, else a host pointer.  Requires tps_set_grid first. */

@@ -88,6 +88,7 @@ std::vector<double> transpose(const std::vector<double> &A, int n) {
 struct HostMode {
   int n = 0;
   std::vector<double> K, S, lam;
+  std::vector<double> Sinv;  // S^-1 when the eigenbasis is not orthogonal (else empty)
 };
 
 // Mode k of the full grid: K = a D2, S = Fourier basis, lam = -a (k pi / L)^2.
@@ -178,11 +179,22 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
     int st;
     if ((st = upload(ctx, &op.K[k], m.K))) return st;
     if ((st = upload(ctx, &op.KT[k], transpose(m.K, m.n)))) return st;
-    if ((st = upload(ctx, &op.S[k], m.S))) return st;
-    if ((st = upload(ctx, &op.ST[k], transpose(m.S, m.n)))) return st;
+    // the fast diagonalisation multiplies mode 0 (x) from the left by S^-1, then S, and
+    // the last mode from the right by S^-T, then S^T (orthogonal bases: S^T and S); the
+    // S slot holds what is applied first from the right / last from the left
+    std::vector<double> Sl = m.S, Sr = transpose(m.S, m.n);
+    if (!m.Sinv.empty()) {
+      if (k == 0) {
+        Sr = m.Sinv;
+      } else {
+        Sl = transpose(m.Sinv, m.n);
+      }
+    }
+    if ((st = upload(ctx, &op.S[k], Sl))) return st;
+    if ((st = upload(ctx, &op.ST[k], Sr))) return st;
     if ((st = upload(ctx, &op.lam[k], m.lam))) return st;
-    if ((st = upload_f32(ctx, &op.Sf[k], m.S))) return st;
-    if ((st = upload_f32(ctx, &op.STf[k], transpose(m.S, m.n)))) return st;
+    if ((st = upload_f32(ctx, &op.Sf[k], Sl))) return st;
+    if ((st = upload_f32(ctx, &op.STf[k], Sr))) return st;
     if ((st = upload_f32(ctx, &op.lamf[k], m.lam))) return st;
     if ((st = upload_f32(ctx, &op.Kf[k], m.K))) return st;
     if ((st = upload_f32(ctx, &op.KTf[k], transpose(m.K, m.n)))) return st;
@@ -206,6 +218,40 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
   // non-blocking streams do not wait for: finish them before any kernel can read them
   TPS_CUDA_TRY(ctx, cudaStreamSynchronize(cudaStreamLegacy));
   return TPS_OK;
+}
+
+// Mode on the mapped Chebyshev grid: K = a D2 (non-symmetric), D2 = S diag(lam) S^-1.
+int chebyshev_mode(int n, double L, double a, HostMode &m, std::vector<double> &pts) {
+  m.n = n;
+  pts.assign(n, 0.0);
+  m.K.assign((size_t)n * n, 0.0);
+  m.S.assign((size_t)n * n, 0.0);
+  m.Sinv.assign((size_t)n * n, 0.0);
+  m.lam.assign(n, 0.0);
+  const int st = tps_chebyshev_grid(n, L, pts.data(), m.K.data(), m.lam.data(), m.S.data(),
+                                    m.Sinv.data());
+  if (st) return st;
+  for (auto &v : m.K) v *= a;
+  for (auto &v : m.lam) v *= a;
+  return TPS_OK;
+}
+
+// Mode x of the mapped Chebyshev grid folded into a heavy-exchange sector: the nodes are
+// mirror images (x_i = -x_{n-1-i}, none at 0), coordinates u_i = (P_i +- P_{n-1-i}) / sqrt 2
+// for i < n/2, operator K_ij +- K_{i, n-1-j}, its own eigen-decomposition.
+int chebyshev_sector_mode(const HostMode &full, int parity, HostMode &m) {
+  const int n = full.n, nr = n / 2;
+  const double sg = parity == TPS_X_EVEN ? 1.0 : -1.0;
+  m.n = nr;
+  m.K.assign((size_t)nr * nr, 0.0);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nr; ++j)
+      m.K[(size_t)i * nr + j] = full.K[(size_t)i * n + j] + sg * full.K[(size_t)i * n + (n - 1 - j)];
+  m.S.assign((size_t)nr * nr, 0.0);
+  m.Sinv.assign((size_t)nr * nr, 0.0);
+  m.lam.assign(nr, 0.0);
+  return real_eig(nr, m.K.data(), m.lam.data(), m.S.data(), m.Sinv.data()) ? TPS_ERR_SINGULAR
+                                                                           : TPS_OK;
 }
 
 double shape_f(int shape, double xi) {
@@ -320,7 +366,7 @@ int refresh_sector_potentials(tps_ctx *ctx) {
   for (int p = TPS_X_EVEN; p <= TPS_X_ODD; ++p) {
     if (!ctx->sect_ready[p]) continue;
     DevOperator &op = ctx->sect[p];
-    const int nr = op.n[0], off = p == TPS_X_EVEN ? 0 : 1;
+    const int nr = op.n[0], off = (p == TPS_X_EVEN || ctx->grid_kind == 1) ? 0 : 1;
     std::vector<double> V((size_t)nr * ny);
     for (int r = 0; r < nr; ++r)
       for (int j = 0; j < ny; ++j) V[(size_t)r * ny + j] = ctx->V_host[(size_t)(r + off) * ny + j];
@@ -335,11 +381,23 @@ int build_sector_operator(tps_ctx *ctx, int parity) {
   if (ctx->sect_ready[parity]) return TPS_OK;
   if (ctx->dim != 1) return set_error(ctx, TPS_ERR_INVALID_ARG, "parity sectors are 1D only");
   const int nx = ctx->n[0], ny = ctx->n[1];
-  HostMode fx = full_mode(nx, ctx->L[0], ctx->a[0]);
-  HostMode fy = full_mode(ny, ctx->L[1], ctx->a[1]);
-  std::vector<HostMode> modes{sector_mode(fx, parity, ctx->L[0], ctx->a[0]), fy};
+  std::vector<HostMode> modes;
+  int off = parity == TPS_X_EVEN ? 0 : 1;
+  if (ctx->grid_kind == 1) {
+    HostMode fx, fy, sx;
+    std::vector<double> px, py;
+    int st = chebyshev_mode(nx, ctx->L[0], ctx->a[0], fx, px);
+    if (!st) st = chebyshev_mode(ny, ctx->L[1], ctx->a[1], fy, py);
+    if (!st) st = chebyshev_sector_mode(fx, parity, sx);
+    if (st) return set_error(ctx, st, "eigen-decomposition of the mapped D2 failed");
+    modes = {sx, fy};
+    off = 0;
+  } else {
+    HostMode fx = full_mode(nx, ctx->L[0], ctx->a[0]);
+    HostMode fy = full_mode(ny, ctx->L[1], ctx->a[1]);
+    modes = {sector_mode(fx, parity, ctx->L[0], ctx->a[0]), fy};
+  }
   const int nr = modes[0].n;
-  const int off = parity == TPS_X_EVEN ? 0 : 1;
   std::vector<double> V((size_t)nr * ny);
   for (int r = 0; r < nr; ++r)
     for (int j = 0; j < ny; ++j) V[(size_t)r * ny + j] = ctx->V_host[(size_t)(r + off) * ny + j];
@@ -440,6 +498,9 @@ int tps_set_grid(tps_ctx *ctx, const int *n, const double *L) {
     ctx->n[k] = n[k];
     ctx->L[k] = L[k];
   }
+  ctx->grid_kind = 0;
+  ctx->pts[0].clear();
+  ctx->pts[1].clear();
   std::vector<HostMode> modes;
   for (int k = 0; k < nm; ++k) {
     const double a = (ctx->dim == 1) ? ctx->a[k] : ctx->a[k / 2];
@@ -455,6 +516,42 @@ int tps_set_grid(tps_ctx *ctx, const int *n, const double *L) {
     ctx->sect_ready[p] = false;
   }
   // preconditioner intermediates for up to 16 vectors per launch (at most 2^27 doubles)
+  long long chunk = (1LL << 27) / N;
+  chunk = std::max(1LL, std::min(16LL, chunk));
+  if ((st = ensure_apply_workspace(ctx, chunk * N))) return st;
+  ctx->have_grid = true;
+  ctx->have_V = false;
+  return TPS_OK;
+}
+
+int tps_set_grid_chebyshev(tps_ctx *ctx, const int *n, const double *L) {
+  if (!ctx || !n || !L) return TPS_ERR_INVALID_ARG;
+  if (!ctx->have_masses) return set_error(ctx, TPS_ERR_NOT_CONFIGURED, "set masses first");
+  if (ctx->dim != 1) return set_error(ctx, TPS_ERR_INVALID_ARG, "Chebyshev grids are 1D only");
+  for (int k = 0; k < 2; ++k)
+    if (n[k] < 4 || n[k] % 2 || n[k] > 1024 || !(L[k] > 0))
+      return set_error(ctx, TPS_ERR_INVALID_ARG, "grid sizes must be even in [4, 1024], L > 0");
+  cudaSetDevice(ctx->device);
+  std::vector<HostMode> modes(2);
+  std::vector<double> pts[2];
+  for (int k = 0; k < 2; ++k) {
+    const int st = chebyshev_mode(n[k], L[k], ctx->a[k], modes[k], pts[k]);
+    if (st) return set_error(ctx, st, "eigen-decomposition of the mapped D2 failed");
+  }
+  for (int k = 0; k < 2; ++k) {
+    ctx->n[k] = n[k];
+    ctx->L[k] = L[k];
+    ctx->pts[k] = pts[k];
+  }
+  ctx->grid_kind = 1;
+  const long long N = (long long)n[0] * n[1];
+  ctx->V_host.assign((size_t)N, 0.0);
+  int st = build_operator(ctx, ctx->full, modes, &ctx->V_host);
+  if (st) return st;
+  for (int p = 0; p < 3; ++p) {
+    free_operator(ctx->sect[p]);
+    ctx->sect_ready[p] = false;
+  }
   long long chunk = (1LL << 27) / N;
   chunk = std::max(1LL, std::min(16LL, chunk));
   if ((st = ensure_apply_workspace(ctx, chunk * N))) return st;
@@ -495,7 +592,15 @@ int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma) {
   if ((shape != TPS_GAUSS && shape != TPS_LORENTZ3) || !(sigma > 0) || !std::isfinite(v0))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad shape, sigma or v0");
   std::vector<double> V(ctx->full.N);
-  if (ctx->dim == 1) {
+  if (ctx->grid_kind == 1) {  // mapped Chebyshev points: evaluated on the host
+    const int nx = ctx->n[0], ny = ctx->n[1];
+    for (int i = 0; i < nx; ++i)
+      for (int j = 0; j < ny; ++j) {
+        const double x = ctx->pts[0][i], y = ctx->pts[1][j];
+        V[(size_t)i * ny + j] = -v0 * (shape_f(shape, std::fabs(y - 0.5 * x) / sigma) +
+                                       shape_f(shape, std::fabs(y + 0.5 * x) / sigma));
+      }
+  } else if (ctx->dim == 1) {
     // evaluated on the device (a host loop over all grid points costs milliseconds), then
     // kept on the host too for the sector folding
     cudaSetDevice(ctx->device);
@@ -537,6 +642,12 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est) {
   if (hnorm_est) {
     double s = 0.0;
     for (int k = 0; k < 2 * ctx->dim; ++k) {
+      if (ctx->grid_kind == 1) {  // the mapped grid: spectral radius of a_k D2_k
+        double r = 0.0;
+        for (double l : ctx->full.lam_h[k]) r = std::max(r, std::fabs(l));
+        s += r;
+        continue;
+      }
       const double h = 2.0 * ctx->L[k] / ctx->n[k];
       const double a = ctx->dim == 1 ? ctx->a[k] : ctx->a[k / 2];
       s += std::fabs(a) * (kPi / h) * (kPi / h);
@@ -741,8 +852,9 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
       (nvec > 0 && (!r_dev || !out_dev)) || !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_prec arguments");
   if (dtype == TPS_TF32_TC) {
-    if (ctx->full.nmodes != 2)
-      return set_error(ctx, TPS_ERR_INVALID_ARG, "the TF32 tensor-core preconditioner is 1D only");
+    if (ctx->full.nmodes != 2 || ctx->grid_kind != 0)
+      return set_error(ctx, TPS_ERR_INVALID_ARG,
+                       "the TF32 tensor-core preconditioner needs a 1D Fourier grid");
     st = ensure_tf_operator(ctx->full);
     if (st) return set_error(ctx, st, "building the TF32 preconditioner operator failed");
   }

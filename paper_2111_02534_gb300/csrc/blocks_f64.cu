@@ -740,6 +740,51 @@ void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *r
                                                                        full);
 }
 
+namespace {
+__global__ void k_mirror_restrict(int sg, int nx, int ny, int ncols, const double *full,
+                                  double *red) {
+  const int nr = nx / 2;
+  const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
+  const long long total = (long long)ncols * Nr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / Nr, rem = e % Nr;
+    const int i = (int)(rem / ny), j = (int)(rem % ny);
+    const double *P = full + c * Nf;
+    red[c * Nr + rem] =
+        sqrt(0.5) * (P[(long long)i * ny + j] + sg * P[(long long)(nx - 1 - i) * ny + j]);
+  }
+}
+__global__ void k_mirror_expand(int sg, int nx, int ny, int ncols, const double *red,
+                                double *full) {
+  const int nr = nx / 2;
+  const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
+  const long long total = (long long)ncols * Nf;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / Nf, rem = e % Nf;
+    const int i = (int)(rem / ny), j = (int)(rem % ny);
+    const int ir = i < nr ? i : nx - 1 - i;
+    const double w = i < nr ? sqrt(0.5) : sg * sqrt(0.5);
+    full[c * Nf + rem] = w * red[c * Nr + (long long)ir * ny + j];
+  }
+}
+}  // namespace
+
+void launch_mirror_restrict(int parity, int nx, int ny, int ncols, const double *full,
+                            double *red, cudaStream_t s) {
+  count_launch();
+  k_mirror_restrict<<<grid_for((long long)ncols * (nx / 2) * ny), 256, 0, s>>>(
+      parity == TPS_X_EVEN ? 1 : -1, nx, ny, ncols, full, red);
+}
+
+void launch_mirror_expand(int parity, int nx, int ny, int ncols, const double *red,
+                          double *full, cudaStream_t s) {
+  count_launch();
+  k_mirror_expand<<<grid_for((long long)ncols * nx * ny), 256, 0, s>>>(
+      parity == TPS_X_EVEN ? 1 : -1, nx, ny, ncols, red, full);
+}
+
 void launch_fix_sign(int ncols, long long nrows, double *X, GramScratch &scr, cudaStream_t s) {
   if (ncols <= 0 || nrows <= 0) return;
   long long nchunk = (4LL * 152 + ncols - 1) / ncols;

@@ -962,6 +962,256 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   return TPS_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Jacobi-Davidson for the non-symmetric H of the paper's own discretisation (Sec. 3.1: the
+// mapped Chebyshev D2 is dense and non-symmetric; Sec. 4.1: JDQR).  The search space V is
+// orthonormal; the projected matrix G = V^T H V is non-symmetric and kept whole (new
+// columns V^T H T and new rows T^T H V per expansion); its k eigenpairs of smallest real
+// part (host QR in complex arithmetic, m <= 64) give the Ritz pairs (theta_i, x_i = V y_i),
+// whose residuals r_i = H x_i - theta_i x_i are orthogonal to V.  The correction equation
+// Eq. jdcor is solved for the unconverged pairs with Qt an orthonormal basis of all k target
+// Ritz vectors, with the Sec. 4.2 preconditioner (fast diagonalisation with S^-1 in place of
+// S^T).  At restart V keeps an orthonormal basis of the lowest m_min Ritz vectors.  The k
+// target pairs stay in the search space until all of them have converged (no locking).
+int solve_nonsym_impl(tps_ctx *ctx, int k_req, int parity, double tol, int block,
+                      const tps_solver_opts *opts_in, double *evals_host, double *evecs_dev,
+                      tps_stats *stats, cudaStream_t s) {
+  const auto t_start = std::chrono::steady_clock::now();
+  tps_solver_opts opts;
+  tps_default_opts(&opts);
+  if (opts_in) opts = *opts_in;
+  int k = k_req + std::max(0, opts.guard);
+  const int b = std::min(block, k);
+  int mmin = opts.m_min > 0 ? opts.m_min : std::max(2 * k, 8);
+  mmin = ((mmin + b - 1) / b) * b;
+  int mmax = opts.m_max > 0 ? opts.m_max : mmin + 2 * b;
+  mmax = std::min(mmax, 64);
+  if (mmin > mmax - b) mmin = std::max(b, mmax - b);
+  if (mmin < k) mmin = std::min(k, mmax - b);
+  const int steps = opts.inner_steps > 0 ? opts.inner_steps : 3;
+  const int max_outer = opts.max_outer > 0 ? opts.max_outer : 500;
+  const double inner_tol = opts.inner_tol > 0 ? opts.inner_tol : 1e-3;
+  if (mmax < 2 * b || steps > 40 || k > mmin)
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "search space too small for k and the block");
+  const DevOperator *opp = &ctx->full;
+  if (parity != TPS_ANY) {
+    int st = build_sector_operator(ctx, parity);
+    if (st) return st;
+    opp = &ctx->sect[parity];
+  }
+  const DevOperator &op = *opp;
+  const long long N = op.N;
+  if (k_req > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
+  int st = alloc_workspace(ctx, N, mmax, std::max(b, k), k, steps);
+  if (st) return st;
+  SolverWorkspace &w = *ctx->sw;
+  Ctx c{ctx, op, w, s, N};
+  w.tm.reset(opts.timing != 0);
+  w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64 : TPS_F32;
+  w.corr_low = false;
+  w.h64_dtype = opts.h64_dtype == TPS_F64_TC ? TPS_F64_TC : TPS_F64;
+  if (w.h64_dtype == TPS_F64_TC) TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));
+  struct Scope {
+    explicit Scope(PhaseTiming *t) {
+      tl_timing = t;
+      tl_split_updates = false;  // the Ritz products stay FP64 (non-orthogonal Y)
+    }
+    ~Scope() { tl_timing = nullptr; }
+  } scope(&w.tm);
+  const long long launches0 = g_kernel_launches.load();
+  double hnorm = 0.0;
+  tps_get_info(ctx, nullptr, &hnorm);
+  tps_stats stt;
+  std::memset(&stt, 0, sizeof(stt));
+  stt.hnorm_est = hnorm;
+  const int ldG = w.mmax;
+  std::vector<double> Gh((size_t)ldG * ldG), Gr((size_t)ldG * ldG), Yh((size_t)ldG * ldG);
+  std::vector<double> lam(ldG, 0.0), res(k, 0.0);
+  uint64_t rng_counter = 0;
+  // random start block, low-pass filtered by the kinetic preconditioner
+  st = fill_random(c, w.V, b, opts.seed, rng_counter);
+  if (st) return st;
+  const double s_smooth = op.lam_min_sum - 1e-3 * hnorm;
+  for (int it = 0; it < opts.smooth_start && opts.use_prec; ++it) {
+    apply_prec_timed(c, w.V, w.P, b, s_smooth);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.V, w.P, (size_t)b * N * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s));
+    stt.prec_applies += b;
+  }
+  int m = 0, bn = b, outer = 0;
+  bool converged = false;
+  for (; outer < max_outer; ++outer) {
+    // (1) orthonormalise the new block against V, (2) apply H, (3) extend G
+    double *T = w.V + (long long)m * N;
+    int rank = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      st = orthonormalize(c, nullptr, 0, w.V, m, T, bn, &rank);
+      if (st) return st;
+      if (rank > 0) break;
+      st = fill_random(c, T, bn, opts.seed, rng_counter);
+      if (st) return st;
+    }
+    if (rank == 0) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "search space cannot be expanded");
+    double *HT = w.HV + (long long)m * N;
+    apply_h_timed(c, T, HT, rank, nullptr, false);
+    stt.h_applies += rank;
+    tgram(w.V, N, 0, m + rank, HT, N, 0, rank, N, w.G + (long long)m * ldG, ldG, 0, 1, ctx->gscr, s);
+    if (m > 0) tgram(T, N, 0, rank, w.HV, N, 0, m, N, w.G + m, ldG, 0, 1, ctx->gscr, s);
+    m += rank;
+    // (4) Ritz pairs of the non-symmetric G (host, complex QR)
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(Gh.data(), w.G, (size_t)ldG * m * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Gr[(size_t)i * m + j] = Gh[(size_t)j * ldG + i];
+    const int nk = std::min(m, std::max(k, mmin));
+    double imag = 0.0;
+    std::fill(Yh.begin(), Yh.end(), 0.0);
+    if (complex_eig_lowest(m, Gr.data(), nk, lam.data(), Yh.data(), ldG, &imag))
+      return set_error(ctx, TPS_ERR_NOT_CONVERGED, "Ritz eigenproblem did not converge");
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.Y, Yh.data(), (size_t)ldG * nk * sizeof(double),
+                                      cudaMemcpyHostToDevice, s));
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.theta, lam.data(), nk * sizeof(double),
+                                      cudaMemcpyHostToDevice, s));
+    // (5) Ritz vectors, residuals and their norms for the k targets
+    const int nt = std::min(k, m);
+    tupdate(w.V, N, 0, m, w.Y, ldG, 0, nt, 1.0, 0.0, w.QX, N, 0, N, 1, s);
+    tupdate(w.HV, N, 0, m, w.Y, ldG, 0, nt, 1.0, 0.0, w.HX, N, 0, N, 1, s);
+    launch_residual(nt, N, w.HX, w.QX, w.theta, w.R, s);
+    col_norms2(c, w.R, nt, w.nrm2);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.nrm2, nt * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    TPS_CUDA_TRY(ctx, cudaGetLastError());
+    w.tm.drain();
+    int nconv = 0;
+    std::vector<int> active;
+    for (int i = 0; i < nt; ++i) {
+      res[i] = std::sqrt(std::max(w.h_pinned[i], 0.0)) / hnorm;
+      if (res[i] <= tol && std::fabs(imag) <= 1e-8 * std::max(1.0, std::fabs(lam[i])))
+        ++nconv;
+      else if ((int)active.size() < b)
+        active.push_back(i);
+    }
+    if (nt == k && nconv == k) {
+      converged = true;
+      ++outer;
+      break;
+    }
+    // (6) restart: an orthonormal basis of the lowest m_min Ritz vectors (host MGS of Y)
+    if (m + b > mmax) {
+      const int mk = std::min(mmin, nk);
+      std::vector<double> Z((size_t)ldG * mk, 0.0);
+      int r = 0;
+      for (int j = 0; j < mk; ++j) {
+        double *z = Z.data() + (size_t)r * ldG;
+        for (int i = 0; i < m; ++i) z[i] = Yh[(size_t)j * ldG + i];
+        for (int pass = 0; pass < 2; ++pass)
+          for (int q = 0; q < r; ++q) {
+            const double *zq = Z.data() + (size_t)q * ldG;
+            double d = 0.0;
+            for (int i = 0; i < m; ++i) d += zq[i] * z[i];
+            for (int i = 0; i < m; ++i) z[i] -= d * zq[i];
+          }
+        double nz = 0.0;
+        for (int i = 0; i < m; ++i) nz += z[i] * z[i];
+        nz = std::sqrt(nz);
+        if (nz < 1e-10) continue;
+        for (int i = 0; i < m; ++i) z[i] /= nz;
+        ++r;
+      }
+      // G in the new basis: Z^T G Z (host), V <- V Z, HV <- HV Z
+      std::vector<double> GZ((size_t)m * r, 0.0), Gn((size_t)ldG * ldG, 0.0);
+      for (int j = 0; j < r; ++j)
+        for (int i = 0; i < m; ++i) {
+          double a = 0.0;
+          for (int l = 0; l < m; ++l) a += Gr[(size_t)i * m + l] * Z[(size_t)j * ldG + l];
+          GZ[(size_t)j * m + i] = a;
+        }
+      for (int j = 0; j < r; ++j)
+        for (int i = 0; i < r; ++i) {
+          double a = 0.0;
+          for (int l = 0; l < m; ++l) a += Z[(size_t)i * ldG + l] * GZ[(size_t)j * m + l];
+          Gn[(size_t)j * ldG + i] = a;
+        }
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.Arot, Z.data(), (size_t)ldG * r * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+      tupdate(w.V, N, 0, m, w.Arot, ldG, 0, r, 1.0, 0.0, w.V2, N, 0, N, 1, s);
+      tupdate(w.HV, N, 0, m, w.Arot, ldG, 0, r, 1.0, 0.0, w.HV2, N, 0, N, 1, s);
+      std::swap(w.V, w.V2);
+      std::swap(w.HV, w.HV2);
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.G, Gn.data(), (size_t)ldG * r * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+      m = r;
+      ++stt.restarts;
+    }
+    // (7) correction equations of the active pairs: Qt = orthonormal basis of the targets
+    const int na = (int)active.size();
+    if (na == 0) {  // every pair so far converged but fewer than k exist: widen with noise
+      st = fill_random(c, w.V + (long long)m * N, b, opts.seed, rng_counter);
+      if (st) return st;
+      bn = b;
+      continue;
+    }
+    for (int a = 0; a < na; ++a) {
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.P + (long long)a * N, w.R + (long long)active[a] * N,
+                                        N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      w.h_pinned[256 + a] = lam[active[a]];
+    }
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.theta2, w.h_pinned + 256, na * sizeof(double),
+                                      cudaMemcpyHostToDevice, s));
+    int nq = 0;
+    st = orthonormalize(c, nullptr, 0, nullptr, 0, w.QX, nt, &nq);
+    if (st) return st;
+    double shift = opts.prec_shift;
+    if (!std::isfinite(shift)) {
+      const double th0 = lam[active[0]];
+      shift = op.lam_min_sum - std::max(std::fabs(th0 - op.lam_min_sum), 1e-8 * hnorm);
+    }
+    st = correction_impl(ctx, op, w.QX, nq, nullptr, 0, w.P, w.theta2, na, steps, opts.use_prec,
+                         shift, inner_tol, w.V + (long long)m * N, &stt.h_applies,
+                         &stt.prec_applies, s, false, false);
+    if (st) return st;
+    stt.inner_steps += steps * na;
+    bn = na;
+  }
+  stt.outer_iters = outer;
+  // results: Ritz values ascending, vectors expanded to the full grid, signs fixed
+  const int nret = converged ? k_req : 0;
+  for (int i = 0; i < nret; ++i) {
+    evals_host[i] = lam[i];
+    if (i < 64) stt.resid[i] = res[i];
+    const double *src = w.QX + (long long)i * N;
+    double *dst = evecs_dev + (long long)i * ctx->full.N;
+    if (parity != TPS_ANY)
+      launch_mirror_expand(parity, ctx->n[0], ctx->n[1], 1, src, dst, s);
+    else
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (nret > 0) launch_fix_sign(nret, ctx->full.N, evecs_dev, ctx->gscr, s);
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  TPS_CUDA_TRY(ctx, cudaGetLastError());
+  w.tm.drain();
+  stt.n_converged = nret;
+  stt.h_ms = w.tm.ms[0];
+  stt.prec_ms = w.tm.ms[1];
+  stt.h_flops = w.tm.flops[0];
+  stt.prec_flops = w.tm.flops[1];
+  stt.h_launches = w.tm.launches[0];
+  stt.prec_launches = w.tm.launches[1];
+  stt.kernel_launches = g_kernel_launches.load() - launches0;
+  stt.time_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = stt;
+  if (w.h64_dtype == TPS_F64_TC) {
+    const int f = tc_operator_status(op);
+    if (f < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
+    if (f) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+  }
+  if (!converged) return set_error(ctx, TPS_ERR_NOT_CONVERGED, "outer-iteration cap reached");
+  return TPS_OK;
+}
+
 }  // namespace tps
 
 using namespace tps;
@@ -1000,6 +1250,11 @@ int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const doub
   if (ctx->dim == 2 && parity != TPS_ANY)
     return set_error(ctx, TPS_ERR_INVALID_ARG, "2D supports TPS_ANY only");
   cudaSetDevice(ctx->device);
+  if (ctx->grid_kind == 1) {
+    if (n_x0 > 0) return set_error(ctx, TPS_ERR_INVALID_ARG, "no warm start on Chebyshev grids");
+    return solve_nonsym_impl(ctx, k, parity, tol, block, opts, evals_host, evecs_dev, stats,
+                             stream);
+  }
   return solve_impl(ctx, k, parity, tol, block, x0_dev, n_x0, opts, evals_host, evecs_dev, stats,
                     stream);
 }

@@ -129,6 +129,12 @@ int update_split_status();
 // lam, unit columns of S; Sinv nullable).  0 on success, 1 for a complex pair or no
 // convergence, 2 for a singular S (host_eig.cpp).
 int real_eig(int n, const double *A, double *lam, double *S, double *Sinv);
+// Host: the k eigenvalues of smallest real part of a real n x n row-major A (real parts,
+// ascending) and real unit eigenvectors Y (column c at Y + c ldy); imag_max (nullable) gets
+// the largest |imaginary part| among them.  0 on success, 1 if the QR steps do not converge
+// (host_eig.cpp).
+int complex_eig_lowest(int n, const double *A, int k, double *lam, double *Y, int ldy,
+                       double *imag_max);
 // out[c] = squared 2-norm of column c (ld lda, nrows rows), c < ncols; uses scr.
 void launch_col_norms2(const double *A, long long lda, int ncols, long long nrows, double *out,
                        GramScratch &scr, cudaStream_t s);
@@ -185,6 +191,12 @@ void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double 
                             double *red, cudaStream_t s);
 void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
                           double *full, cudaStream_t s);
+// the same for the mirror-symmetric Chebyshev x grid (x_i = -x_{n-1-i}, no node at 0):
+// u_i = (P_i +- P_{n-1-i}) / sqrt 2, i < n/2, for both sectors.
+void launch_mirror_restrict(int parity, int nx, int ny, int ncols, const double *full,
+                            double *red, cudaStream_t s);
+void launch_mirror_expand(int parity, int nx, int ny, int ncols, const double *red,
+                          double *full, cudaStream_t s);
 // flip the sign of each column so that its entry of largest magnitude is positive.
 void launch_fix_sign(int ncols, long long nrows, double *X, GramScratch &scr, cudaStream_t s);
 
@@ -200,6 +212,9 @@ struct tps_ctx {
   double a[2] = {0, 0};  // kinetic coefficient of x and y
   int n[4] = {0, 0, 0, 0};
   double L[4] = {0, 0, 0, 0};
+  int grid_kind = 0;                   // 0: Fourier grids (tps_set_grid); 1: mapped Chebyshev
+                                       // roots (tps_set_grid_chebyshev, 1D)
+  std::vector<double> pts[2];          // grid points of x and y (mapped Chebyshev grids)
   std::vector<double> V_host;          // potential on the full grid
   tps::DevOperator full;               // full grid operator
   tps::DevOperator sect[3];            // [TPS_X_EVEN], [TPS_X_ODD] parity-reduced 1D operators
@@ -219,6 +234,10 @@ int ensure_gram_scratch(tps_ctx *ctx, long long doubles);
 void free_operator(DevOperator &op);
 // Build the parity-reduced 1D operator for TPS_X_EVEN / TPS_X_ODD.
 int build_sector_operator(tps_ctx *ctx, int parity);
+// The eigensolver for the non-symmetric H of the mapped Chebyshev grid (jd.cpp).
+int solve_nonsym_impl(tps_ctx *ctx, int k, int parity, double tol, int block,
+                      const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
+                      tps_stats *stats, cudaStream_t stream);
 int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const double *x0,
                int n_x0, const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
                tps_stats *stats, cudaStream_t stream);

@@ -90,6 +90,7 @@ _sig = {
     "tps_set_masses": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "tps_set_alpha": (C.c_int, [_vp, C.c_double]),
     "tps_set_grid": (C.c_int, [_vp, _ip, _dp]),
+    "tps_set_grid_chebyshev": (C.c_int, [_vp, _ip, _dp]),
     "tps_set_potential": (C.c_int, [_vp, _vp, C.c_int]),
     "tps_set_pair_potential": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
     "tps_two_body_v0": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
@@ -251,6 +252,12 @@ class Context:
         na = (C.c_int * len(n))(*n)
         La = (C.c_double * len(L))(*L)
         self._check(_lib.tps_set_grid(self._h, na, La), "set_grid")
+
+    def set_grid_chebyshev(self, n, L):
+        """The paper's mapped Chebyshev grid (1D): n[k] roots, map parameters L[k]."""
+        na = (C.c_int * len(n))(*n)
+        La = (C.c_double * len(L))(*L)
+        self._check(_lib.tps_set_grid_chebyshev(self._h, na, La), "set_grid_chebyshev")
 
     def set_potential(self, V):
         """V: float64 tensor of N entries (host or device) or a numpy array (host)."""

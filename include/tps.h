@@ -241,6 +241,18 @@ typedef struct tps_solver_opts {
                          on the FMA pipe): TPS_F64_TC (default: digit-split products on the
                          tensor cores, tps_block_update_tc, for blocks of 10^5 rows or more
                          and p >= 8; smaller ones on the FMA pipe) or TPS_F64 (FMA pipe) */
+  int graph;          /* 1: after the host-driven outer iterations that fill the first m_min
+                         columns, the rest of the solve runs
+                         as one CUDA graph launch: the outer iteration is captured once, with
+                         every wanted pair in one block (k <= 16, `block` ignored; the search
+                         space cycles between m_min, rounded up to whole blocks, and m_min + 2k),
+                         no locking, a fixed preconditioner shift (prec_shift, or the mirror
+                         of the lowest Ritz value after the second iteration) and one
+                         preconditioned-residual step per correction, inside a conditional
+                         WHILE node whose condition a device kernel sets from the residual
+                         norms.  Falls back to the host-driven loop if the cycle does not
+                         converge within max_outer iterations.  1D Fourier grids, no warm
+                         start; ignored otherwise.  Default 0 */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -290,6 +302,8 @@ typedef struct tps_stats {
                                 (every 4th launch timed, like the Gram products) */
   long long rr_launches;     /* Rayleigh-Ritz eigensolver launches (all of them) */
   long long rr_timed;        /* of which timed (rr_ms covers these) */
+  double graph_build_ms;     /* graph solver: host time to capture and instantiate the graph */
+  double graph_run_ms;       /* graph solver: host wall time of the graph launch until done */
   double resid[64];   /* ||H x_i - lambda_i x_i|| / ||H||_est per returned pair */
 } tps_stats;
 

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "jd_kernels.h"
@@ -103,6 +104,11 @@ struct SolverWorkspace {
   double *Mq = nullptr, *Minv = nullptr;        // [(kmax+b)^2]
   double *Rinv = nullptr;                       // [b * b]
   int *keep = nullptr;                          // [b]
+  int *keep0 = nullptr;                         // [b] first Cholesky-QR pass (graph solver)
+  int *gstate = nullptr;                        // graph solver: converged flag, iterations
+  double *gshift = nullptr;                     // graph solver: the preconditioner's shift
+  cudaStream_t capture = nullptr;               // graph solver: private stream for capture (the
+                                                // legacy default stream cannot capture)
   int *jstat = nullptr;                         // Jacobi sweeps, rotating rounds, calls
   int *dgks = nullptr;                          // second-pass flag, passes needed, decisions
   GmresState gm;
@@ -248,7 +254,8 @@ void apply_h_timed(Ctx &c, const double *in, double *out, int nvec, const double
   t.launches[kind] += 1;
 }
 
-void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double shift) {
+void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double shift,
+                      const double *shift_dev = nullptr) {
   PhaseTiming &t = c.w.tm;
   cudaEvent_t a = nullptr, b = nullptr;
   if (t.on) {
@@ -257,7 +264,7 @@ void apply_prec_timed(Ctx &c, const double *in, double *out, int nvec, double sh
     cudaEventRecord(a, c.s);
   }
   if (c.w.prec_dtype == TPS_TF32_TC)
-    launch_apply_prec_tf32(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
+    launch_apply_prec_tf32(c.op, in, out, nvec, shift, c.ctx->ws, c.s, shift_dev);
   else if (c.w.prec_dtype == TPS_F32)
     launch_apply_prec_f32(c.op, in, out, nvec, shift, c.ctx->ws, c.s);
   else
@@ -333,10 +340,10 @@ int orthonormalize(Ctx &c, const double *B1, int nb1, const double *B2, int nb2,
 
 // Out = Kt^-1 Y for nsys columns: projected preconditioner (use_prec) or projector.
 void kt_inverse(Ctx &c, const double *Qt, int nq, const double *KQt, int use_prec, double shift,
-                const double *Yin, int nsys, double *Out) {
+                const double *Yin, int nsys, double *Out, const double *shift_dev = nullptr) {
   SolverWorkspace &w = c.w;
   if (use_prec) {
-    apply_prec_timed(c, Yin, Out, nsys, shift);
+    apply_prec_timed(c, Yin, Out, nsys, shift, shift_dev);
     if (nq > 0) {
       tgram(Qt, c.N, 0, nq, Out, c.N, 0, nsys, c.N, w.C, nq, 0, 1, c.ctx->gscr, c.s, nullptr,
             w.corr_low);
@@ -383,7 +390,8 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   const long long nsmall = 3LL * mmax * mmax + 2LL * mmax + 2LL * std::max(q, mmax) +
                            2LL * (q + mmax + b) * std::max(b, q) + 2LL * q * q + (long long)bw * bw + bw +
                            /* gmres */ (long long)b * ((steps + 1) * steps + 2 * steps + (steps + 1) +
-                                                      3 + steps + (steps + 1)) + 64;
+                                                      3 + steps + (steps + 1)) + 64 +
+                           /* keep0, graph state, shift */ 2LL * bw + 96;
   const size_t bytes = ((size_t)nbig * N + (size_t)nsmall) * sizeof(double) + 4096 * 4;
   TPS_CUDA_TRY(ctx, cudaMalloc((void **)&w->arena, bytes));
   w->arena_bytes = bytes;
@@ -426,6 +434,9 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
   w->gm.h = take((long long)b * (steps + 1));
   w->gm.nrm2 = take(b);
   w->keep = reinterpret_cast<int *>(take(bw));
+  w->keep0 = reinterpret_cast<int *>(take(bw));
+  w->gstate = reinterpret_cast<int *>(take(2));
+  w->gshift = take(1);
   w->jstat = reinterpret_cast<int *>(take(4));  // 8 counters
   w->dgks = reinterpret_cast<int *>(take(2));
   w->gm.done = reinterpret_cast<int *>(take(b));
@@ -448,6 +459,7 @@ int alloc_workspace(tps_ctx *ctx, long long N, int mmax, int b, int kmax, int st
 void free_solver_workspace(tps_ctx *ctx) {
   if (!ctx->sw) return;
   ctx->sw->tm.destroy();
+  if (ctx->sw->capture) cudaStreamDestroy(ctx->sw->capture);
   cudaFree(ctx->sw->arena);
   cudaFreeHost(ctx->sw->h_pinned);
   cudaFreeHost(ctx->sw->hi_pinned);
@@ -463,7 +475,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                     const double *KQt_cached, int nq_cached, const double *R,
                     const double *theta, int nsys, int steps, int use_prec, double shift,
                     double inner_tol, double *T, int *h_applies, int *prec_applies,
-                    cudaStream_t s, bool direction_only, bool low) {
+                    cudaStream_t s, bool direction_only, bool low, const double *shift_dev) {
   SolverWorkspace &w = *ctx->sw;
   Ctx c{ctx, op, w, s, op.N};
   const long long N = op.N;
@@ -474,7 +486,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
                                         cudaMemcpyDeviceToDevice, s));
     if (nq > nq_cached) {
       apply_prec_timed(c, Qt + (long long)nq_cached * N, KQt + (long long)nq_cached * N,
-                       nq - nq_cached, shift);
+                       nq - nq_cached, shift, shift_dev);
       *prec_applies += nq - nq_cached;
     }
     tgram(Qt, N, 0, nq, KQt, N, 0, nq, N, w.Mq, nq, 0, 1, ctx->gscr, s, nullptr, w.corr_low);
@@ -483,7 +495,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
   const int sst = steps;
   // z_0 = -Kt^-1 r / beta
   double *Z = w.Z;
-  kt_inverse(c, Qt, nq, KQt, use_prec, shift, R, nsys, Z);
+  kt_inverse(c, Qt, nq, KQt, use_prec, shift, R, nsys, Z, shift_dev);
   if (use_prec) *prec_applies += nsys;
   if (direction_only && sst == 1) {
     // one GMRES step only scales z_0, and the caller normalises the correction: the
@@ -505,7 +517,7 @@ int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int n
     }
     apply_h_timed(c, zj, w.W, nsys, theta, low);
     *h_applies += nsys;
-    kt_inverse(c, Qt, nq, KQt, use_prec, shift, w.W, nsys, w.P);
+    kt_inverse(c, Qt, nq, KQt, use_prec, shift, w.W, nsys, w.P, shift_dev);
     if (use_prec) *prec_applies += nsys;
     // Arnoldi, classical Gram-Schmidt twice, per system: h = Z_i^T p_i ; p_i -= Z_i h
     for (int pass = 0; pass < 2; ++pass) {
@@ -963,6 +975,324 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
 }
 
 // ---------------------------------------------------------------------------------------
+// The outer loop as a captured CUDA graph (tps_solver_opts.graph).  With every wanted pair
+// in one block (b = k), no locking, a fixed preconditioner shift and one
+// preconditioned-residual step per correction (the projected direction -Kt^-1 r of Eq.
+// jdcor), the search space follows a fixed cycle -- m = m_min -> m_min + b -> m_max =
+// m_min + 2b, restart to m_min -- and every kernel of an outer iteration has sizes known in
+// advance.  The only data-dependent decision, "converged?", is taken on the device
+// (k_conv_check) and drives a conditional WHILE node around the captured two-iteration
+// cycle, so after the eager iterations that fill the first m_min columns (the last of them
+// fixes the shift from the lowest Ritz value) the rest of the solve is one graph launch
+// with no host round trip.  Columns that the orthonormalisation drops
+// become zero and get a diagonal in G above the wanted Ritz values instead of being
+// compacted on the host.
+namespace {
+
+struct GraphIter {
+  int m;          // search-space size before the expansion
+  bool restart;   // restart to 2b after this iteration
+};
+
+// One outer iteration with static sizes: orthonormalise the block at V + m, apply H, extend
+// G, Ritz pairs, targets X/HX/R and their residual norms, optional restart, correction of
+// all b targets into the next block.  Returns the search-space size after it.
+int graph_iteration(Ctx &c, const GraphIter &it, int b, int mmin, double shift, bool use_prec,
+                    int *h_applies, int *prec_applies, double thresh2, double hnorm,
+                    bool dev_shift) {
+  SolverWorkspace &w = c.w;
+  const long long N = c.N;
+  const int m = it.m, ldG = w.mmax;
+  double *T = w.V + (long long)m * N;
+  // block CGS2 (second pass only where the first lost more than half a column's norm) and
+  // Cholesky-QR twice; dropped columns stay as zeros (keep0)
+  col_norms2(c, T, b, w.ref);
+  for (int pass = 0; pass < 2 && m > 0; ++pass) {
+    const int *need = nullptr;
+    if (pass == 1) {
+      col_norms2(c, T, b, w.nrm2);
+      launch_dgks_flag(w.ref, w.nrm2, b, w.dgks, w.dgks + 1, c.s);
+      need = w.dgks;
+    }
+    tgram(w.V, N, 0, m, T, N, 0, b, N, w.C, m, 0, 1, c.ctx->gscr, c.s, need);
+    tupdate(w.V, N, 0, m, w.C, m, 0, b, -1.0, 1.0, T, N, 0, N, 1, c.s, need);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    tgram(T, N, 0, b, T, N, 0, b, N, w.C, b, 0, 1, c.ctx->gscr, c.s);
+    launch_chol_inv(w.C, b, pass == 0 ? w.ref : nullptr, pass == 0 ? 1e-7 : 1e-12, w.Rinv,
+                    w.keep, c.s);
+    tupdate(T, N, 0, b, w.Rinv, b, 0, b, 1.0, 0.0, w.T2, N, 0, N, 1, c.s, nullptr, false, false);
+    cudaMemcpyAsync(T, w.T2, (size_t)b * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+    if (pass == 0) cudaMemcpyAsync(w.keep0, w.keep, b * sizeof(int), cudaMemcpyDeviceToDevice, c.s);
+  }
+  double *HT = w.HV + (long long)m * N;
+  apply_h_timed(c, T, HT, b, nullptr, false);
+  *h_applies += b;
+  if (m > 0) tgram(w.V, N, 0, m, HT, N, 0, b, N, w.G + (long long)m * ldG, ldG, 0, 1, c.ctx->gscr, c.s);
+  tgram(T, N, 0, b, HT, N, 0, b, N, w.G + (long long)m * ldG + m, ldG, 0, 1, c.ctx->gscr, c.s);
+  launch_mirror_block(w.G, ldG, m, b, c.s);
+  launch_mark_dropped(w.G, ldG, m, b, w.keep0, c.s);
+  const int mm = m + b;
+  launch_rr_eigh(w.G, mm, ldG, w.theta, w.Y, ldG, c.s, 0, w.jstat, 0.0, w.Arot, TPS_RR_MIXED, 0);
+  tupdate(w.V, N, 0, mm, w.Y, ldG, 0, b, 1.0, 0.0, w.QX, N, 0, N, 1, c.s);
+  tupdate(w.HV, N, 0, mm, w.Y, ldG, 0, b, 1.0, 0.0, w.HX, N, 0, N, 1, c.s);
+  launch_residual(b, N, w.HX, w.QX, w.theta, w.R, c.s);
+  col_norms2(c, w.R, b, w.nrm2);
+  // converged pairs get no correction; the shift follows the lowest unconverged Ritz value
+  launch_zero_converged(w.R, N, w.nrm2, b, thresh2, c.s);
+  if (dev_shift)
+    launch_shift_update(w.theta, w.nrm2, b, thresh2, c.op.lam_min_sum, hnorm, w.gshift, c.s);
+  int mnew = mm;
+  if (it.restart) {  // keep the lowest mmin Ritz vectors (theta[0 .. mmin) stay in place)
+    tupdate(w.V, N, 0, mm, w.Y, ldG, 0, mmin, 1.0, 0.0, w.V2, N, 0, N, 1, c.s);
+    tupdate(w.HV, N, 0, mm, w.Y, ldG, 0, mmin, 1.0, 0.0, w.HV2, N, 0, N, 1, c.s);
+    cudaMemcpyAsync(w.V, w.V2, (size_t)mmin * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+    cudaMemcpyAsync(w.HV, w.HV2, (size_t)mmin * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+    launch_copy_block(w.Arot, ldG, 0, w.G, ldG, mmin, c.s);  // G in the kept Ritz basis
+    mnew = mmin;
+  }
+  correction_impl(c.ctx, c.op, w.QX, b, nullptr, 0, w.R, w.theta, b, 1, use_prec ? 1 : 0, shift,
+                  1e-3, w.V + (long long)mnew * N, h_applies, prec_applies, c.s, true, w.corr_low,
+                  dev_shift ? w.gshift : nullptr);
+  return mnew;
+}
+
+}  // namespace
+
+int solve_graph_impl(tps_ctx *ctx, int k_req, int parity, double tol,
+                     const tps_solver_opts &opts, double *evals_host, double *evecs_dev,
+                     tps_stats *stats, cudaStream_t s) {
+  const auto t_start = std::chrono::steady_clock::now();
+  // every wanted pair in the one block; the Rayleigh-Ritz space (up to 4 k) plays the role
+  // of the guard pairs
+  const int k = k_req;
+  const int b = k;
+  // the host-driven solver's search-space sizes for k + guard pairs, in whole blocks
+  const int kg = k_req + std::max(0, opts.guard);
+  const int m0 = opts.m_min > 0 ? opts.m_min : std::max(2 * kg, 8);
+  const int mmin = ((m0 + b - 1) / b) * b, mmax = mmin + 2 * b;
+  if (mmax > 64 || b > 32) return set_error(ctx, TPS_ERR_INVALID_ARG, "graph solver: k <= 16");
+  const DevOperator *opp = &ctx->full;
+  if (parity != TPS_ANY) {
+    int st = build_sector_operator(ctx, parity);
+    if (st) return st;
+    opp = &ctx->sect[parity];
+  }
+  const DevOperator &op = *opp;
+  const long long N = op.N;
+  if (k > N / 2) return set_error(ctx, TPS_ERR_INVALID_ARG, "k too large for the grid");
+  int st = alloc_workspace(ctx, N, mmax, b, k, 1);
+  if (st) return st;
+  SolverWorkspace &w = *ctx->sw;
+  Ctx c{ctx, op, w, s, N};
+  w.tm.reset(false);
+  w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64
+                 : (opts.prec_dtype == TPS_TF32_TC && op.nmodes == 2) ? TPS_TF32_TC : TPS_F32;
+  w.corr_low = opts.correction_dtype != TPS_F64;
+  w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && op.nmodes == 2) ? TPS_F64_TC : TPS_F64;
+  if (w.prec_dtype == TPS_TF32_TC) {
+    const int st_tf = ensure_tf_operator(op);
+    if (st_tf) return set_error(ctx, st_tf, "building the TF32 preconditioner operator failed");
+  }
+  if (w.h64_dtype == TPS_F64_TC) TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));
+  struct Scope {
+    explicit Scope(bool split) {
+      tl_timing = nullptr;
+      tl_split_updates = split;
+    }
+    ~Scope() { tl_split_updates = false; }
+  } scope(opts.update_dtype == TPS_F64_TC);
+  const long long launches0 = g_kernel_launches.load();
+  double hnorm = 0.0;
+  tps_get_info(ctx, nullptr, &hnorm);
+  tps_stats stt;
+  std::memset(&stt, 0, sizeof(stt));
+  stt.hnorm_est = hnorm;
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.jstat, 0, 8 * sizeof(int), s));
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
+  TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.gstate, 0, 2 * sizeof(int), s));
+  // start block: random, low-pass filtered
+  uint64_t rng_counter = 0;
+  st = fill_random(c, w.V, b, opts.seed, rng_counter);
+  if (st) return st;
+  const double s_smooth = op.lam_min_sum - 1e-3 * hnorm;
+  for (int it = 0; it < opts.smooth_start && opts.use_prec; ++it) {
+    apply_prec_timed(c, w.V, w.P, b, s_smooth);
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.V, w.P, (size_t)b * N * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s));
+    stt.prec_applies += b;
+  }
+  const double thresh2 = (tol * hnorm) * (tol * hnorm);
+  // the shift follows the lowest unconverged Ritz value on the device (TF32 preconditioner,
+  // no fixed prec_shift); else it is fixed after the eager iterations
+  const bool dev_shift = !std::isfinite(opts.prec_shift) && w.prec_dtype == TPS_TF32_TC;
+  // eager iterations up to m = m_min; the shift follows the lowest Ritz value (fixed from
+  // the last of them), the paper's -E0 when the caller fixes prec_shift
+  double shift = opts.prec_shift;
+  int m = 0;
+  // with the shift on the device the iterations that fill m_min are captured too (their
+  // sizes are static as well); else they run eagerly and fix the shift
+  const int nfill = mmin / b;
+  const int neager = dev_shift ? 0 : nfill;
+  for (int e = 0; e < neager; ++e) {
+    double sh = shift;
+    if (!std::isfinite(sh)) {
+      if (e == 0) {
+        sh = s_smooth;
+      } else {
+        TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta, sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+        TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        const double th0 = w.h_pinned[0];
+        sh = op.lam_min_sum - std::max(std::fabs(th0 - op.lam_min_sum), 1e-8 * hnorm);
+      }
+    }
+    m = graph_iteration(c, GraphIter{m, false}, b, mmin, sh, opts.use_prec != 0, &stt.h_applies,
+                        &stt.prec_applies, thresh2, hnorm, false);
+    if (e == neager - 1) shift = sh;
+  }
+  if (opts.update_dtype == TPS_F64_TC) prewarm_update_split();
+  // the captured cycle: m = 2b -> 3b, 3b -> 4b -> restart to 2b, inside a WHILE node
+  const int max_outer = opts.max_outer > 0 ? opts.max_outer : 500;
+  if (dev_shift) {
+    shift = s_smooth;
+    w.h_pinned[0] = shift;
+    TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.gshift, w.h_pinned, sizeof(double), cudaMemcpyHostToDevice, s));
+    TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  }
+  // graph construction takes driver locks; threads of a batch take turns
+  static std::mutex build_mutex;
+  std::unique_lock<std::mutex> build_lock(build_mutex);
+  const auto t_build = std::chrono::steady_clock::now();
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto fail = [&](cudaError_t e, const char *what) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_error(ctx, e, what);
+  };
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return fail(e, "cudaGraphCreate");
+  cudaGraphConditionalHandle loop;
+  e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+  // capture on a private stream (nothing runs during capture; the graph launches on s)
+  if (!w.capture) {
+    e = cudaStreamCreateWithFlags(&w.capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(e, "cudaStreamCreateWithFlags");
+  }
+  const cudaStream_t cs = w.capture;
+  Ctx cc{ctx, op, w, cs, N};
+  std::vector<cudaGraphNode_t> leaf;
+  if (neager < nfill) {  // the filling iterations, captured into the top-level graph
+    e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(e, "cudaStreamBeginCaptureToGraph (fill)");
+    for (int e2 = neager; e2 < nfill; ++e2)
+      m = graph_iteration(cc, GraphIter{m, false}, b, mmin, shift, opts.use_prec != 0,
+                          &stt.h_applies, &stt.prec_applies, thresh2, hnorm, dev_shift);
+    cudaGraph_t captured_fill = nullptr;
+    const cudaError_t fe = cudaStreamEndCapture(cs, &captured_fill);
+    e = fe != cudaSuccess ? fe : cudaGetLastError();
+    if (e != cudaSuccess) return fail(e, "capturing the filling iterations");
+    size_t nn = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+      size_t nd = 0;
+      e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
+      if (e == cudaSuccess && nd == 0) leaf.push_back(nodes[i]);
+    }
+    if (e != cudaSuccess) return fail(e, "reading the graph's last node");
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  e = cudaGraphAddNode(&wnode, graph, leaf.empty() ? nullptr : leaf.data(), nullptr, leaf.size(),
+                       &cp);
+  if (e != cudaSuccess) return fail(e, "cudaGraphAddNode (while)");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(e, "cudaStreamBeginCaptureToGraph");
+  int hcount = 0, pcount = 0;
+  int mc = graph_iteration(cc, GraphIter{mmin, false}, b, mmin, shift, opts.use_prec != 0, &hcount,
+                           &pcount, thresh2, hnorm, dev_shift);
+  launch_conv_check(w.nrm2, k_req, thresh2, w.gstate, max_outer, loop, 0, cs);
+  mc = graph_iteration(cc, GraphIter{mc, true}, b, mmin, shift, opts.use_prec != 0, &hcount,
+                       &pcount, thresh2, hnorm, dev_shift);
+  launch_conv_check(w.nrm2, k_req, thresh2, w.gstate, max_outer, loop, 1, cs);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+  e = ce != cudaSuccess ? ce : cudaGetLastError();
+  if (e != cudaSuccess) return fail(e, "capturing the outer iteration");
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+  build_lock.unlock();
+  const auto t_run = std::chrono::steady_clock::now();
+  stt.graph_build_ms = std::chrono::duration<double, std::milli>(t_run - t_build).count();
+  e = cudaGraphLaunch(exec, s);
+  if (e != cudaSuccess) return fail(e, "cudaGraphLaunch");
+  int state[2] = {0, 0};
+  e = cudaMemcpyAsync(w.hi_pinned, w.gstate, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e, "running the outer-iteration graph");
+  stt.graph_run_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                               t_run).count();
+  std::memcpy(state, w.hi_pinned, sizeof(state));
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  const int cycles = (state[1] + 1) / 2;
+  stt.outer_iters = nfill + state[1];
+  stt.h_applies += cycles * hcount;
+  stt.prec_applies += cycles * pcount;
+  stt.restarts = cycles;
+  // results: Ritz values, vectors (QX) expanded to the full grid, signs fixed; the Ritz
+  // vectors of a converged state are unit vectors (a dropped column would be zero)
+  TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned, w.theta, k * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+  col_norms2(c, w.QX, k_req, w.ref);
+  TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 64, w.ref, k_req * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+  TPS_CUDA_TRY(ctx, cudaMemcpyAsync(w.h_pinned + 128, w.nrm2, k_req * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  bool ok = state[0] != 0;
+  for (int i = 0; i < k_req && ok; ++i) ok = std::fabs(w.h_pinned[64 + i] - 1.0) <= 1e-8;
+  if (!ok) return TPS_ERR_NOT_CONVERGED;  // the caller falls back to the host-driven loop
+  for (int i = 0; i < k_req; ++i) {
+    evals_host[i] = w.h_pinned[i];
+    if (i < 64) stt.resid[i] = std::sqrt(std::max(w.h_pinned[128 + i], 0.0)) / hnorm;
+    const double *src = w.QX + (long long)i * N;
+    double *dst = evecs_dev + (long long)i * ctx->full.N;
+    if (parity != TPS_ANY)
+      launch_sector_expand(parity, ctx->n[0], ctx->n[1], 1, src, dst, s);
+    else
+      TPS_CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  launch_fix_sign(k_req, ctx->full.N, evecs_dev, ctx->gscr, s);
+  TPS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  TPS_CUDA_TRY(ctx, cudaGetLastError());
+  stt.n_converged = k_req;
+  stt.kernel_launches = g_kernel_launches.load() - launches0;
+  stt.time_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = stt;
+  {
+    const int f = (w.h64_dtype == TPS_F64_TC ? tc_operator_status(op) : 0) |
+                  (opts.update_dtype == TPS_F64_TC ? update_split_status() : 0);
+    if (f < 0) return set_error(ctx, TPS_ERR_CUDA, "reading the device status flag failed");
+    if (f) return set_error(ctx, TPS_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+  }
+  return TPS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // Jacobi-Davidson for the non-symmetric H of the paper's own discretisation (Sec. 3.1: the
 // mapped Chebyshev D2 is dense and non-symmetric; Sec. 4.1: JDQR).  The search space V is
 // orthonormal; the projected matrix G = V^T H V is non-symmetric and kept whole (new
@@ -1254,6 +1584,13 @@ int tps_solve(tps_ctx *ctx, int k, int parity, double tol, int block, const doub
     if (n_x0 > 0) return set_error(ctx, TPS_ERR_INVALID_ARG, "no warm start on Chebyshev grids");
     return solve_nonsym_impl(ctx, k, parity, tol, block, opts, evals_host, evecs_dev, stats,
                              stream);
+  }
+  if (opts && opts->graph && n_x0 == 0 && ctx->dim == 1) {
+    const int st = solve_graph_impl(ctx, k, parity, tol, *opts, evals_host, evecs_dev, stats,
+                                    stream);
+    if (st != TPS_ERR_NOT_CONVERGED) return st;
+    // the graph's cycle did not converge within the cap (or returned a degenerate vector):
+    // the host-driven loop solves the problem from scratch
   }
   return solve_impl(ctx, k, parity, tol, block, x0_dev, n_x0, opts, evals_host, evecs_dev, stats,
                     stream);

@@ -172,6 +172,80 @@ void launch_gmres_solve(int nsys, int s, GmresState &st, cudaStream_t str) {
   count_launch();
   k_gmres_solve<<<nb(nsys), 128, 0, str>>>(nsys, s, st.Hb, st.g, st.mvalid, st.y);
 }
+// A column of the new block that the Cholesky-QR dropped (keep0 == 0) is zero, so its row
+// and column of G are zero: its diagonal entry is raised to twice the largest |G_ii| of the
+// first m0 + bn, which puts that spurious Ritz value above the wanted ones.
+__global__ void k_mark_dropped(double *G, int ldg, int m0, int bn, const int *keep0) {
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < m0 + bn; ++i) a = fmax(a, fabs(G[(long long)i * ldg + i]));
+    mx = a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < bn; j += blockDim.x)
+    if (!keep0[j]) G[(long long)(m0 + j) * ldg + (m0 + j)] = 2.0 * mx + 1.0;
+}
+
+// Convergence of the first k pairs (squared residual norms nrm2 <= thresh2), counted
+// iterations, and the condition of the enclosing graph loop: go on while not converged and
+// under the iteration cap.  state[0] = converged, state[1] = iterations.
+__global__ void k_conv_check(const double *nrm2, int k, double thresh2, int *state, int max_iter,
+                             cudaGraphConditionalHandle loop, int set_loop) {
+  if (threadIdx.x != 0) return;
+  int conv = 1;
+  for (int i = 0; i < k; ++i) conv = conv && nrm2[i] <= thresh2;
+  state[0] = conv;
+  state[1] += 1;
+  if (set_loop) cudaGraphSetConditional(loop, (!conv && state[1] < max_iter) ? 1u : 0u);
+}
+
+// Residual columns of pairs already converged (nrm2 <= thresh2) are set to zero, so their
+// corrections are zero (and dropped by the orthonormalisation) instead of noise directions.
+__global__ void k_zero_converged(double *R, long long nrows, const double *nrm2, int k,
+                                 double thresh2) {
+  const long long total = (long long)k * nrows;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    if (nrm2[e / nrows] <= thresh2) R[e] = 0.0;
+}
+
+// The preconditioner's shift from the lowest unconverged Ritz value theta: below the kinetic
+// spectrum (bottom lam_min), at the mirror image of theta when theta lies above it:
+// shift = lam_min - max(|theta - lam_min|, 1e-8 hnorm).
+__global__ void k_shift_update(const double *theta, const double *nrm2, int k, double thresh2,
+                               double lam_min, double hnorm, double *shift) {
+  if (threadIdx.x != 0) return;
+  int i = 0;
+  while (i < k - 1 && nrm2[i] <= thresh2) ++i;
+  *shift = lam_min - fmax(fabs(theta[i] - lam_min), 1e-8 * hnorm);
+}
+
+void launch_zero_converged(double *R, long long nrows, const double *nrm2, int k, double thresh2,
+                           cudaStream_t str) {
+  count_launch();
+  long long blocks = ((long long)k * nrows + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  k_zero_converged<<<(unsigned)blocks, 256, 0, str>>>(R, nrows, nrm2, k, thresh2);
+}
+
+void launch_shift_update(const double *theta, const double *nrm2, int k, double thresh2,
+                         double lam_min, double hnorm, double *shift, cudaStream_t str) {
+  count_launch();
+  k_shift_update<<<1, 32, 0, str>>>(theta, nrm2, k, thresh2, lam_min, hnorm, shift);
+}
+
+void launch_mark_dropped(double *G, int ldg, int m0, int bn, const int *keep0, cudaStream_t str) {
+  count_launch();
+  k_mark_dropped<<<1, 32, 0, str>>>(G, ldg, m0, bn, keep0);
+}
+
+void launch_conv_check(const double *nrm2, int k, double thresh2, int *state, int max_iter,
+                       cudaGraphConditionalHandle loop, int set_loop, cudaStream_t str) {
+  count_launch();
+  k_conv_check<<<1, 32, 0, str>>>(nrm2, k, thresh2, state, max_iter, loop, set_loop);
+}
+
 void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str) {
   count_launch();
   k_mirror_block<<<nb((long long)(m0 + bn) * bn), 128, 0, str>>>(G, ldg, m0, bn);

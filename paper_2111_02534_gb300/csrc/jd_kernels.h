@@ -26,6 +26,13 @@ void launch_gmres_givens(int nsys, int s, int j, const double *nrm2, GmresState 
                          cudaStream_t str);
 void launch_gmres_solve(int nsys, int s, GmresState &st, cudaStream_t str);
 void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str);
+void launch_mark_dropped(double *G, int ldg, int m0, int bn, const int *keep0, cudaStream_t str);
+void launch_zero_converged(double *R, long long nrows, const double *nrm2, int k, double thresh2,
+                           cudaStream_t str);
+void launch_shift_update(const double *theta, const double *nrm2, int k, double thresh2,
+                         double lam_min, double hnorm, double *shift, cudaStream_t str);
+void launch_conv_check(const double *nrm2, int k, double thresh2, int *state, int max_iter,
+                       cudaGraphConditionalHandle loop, int set_loop, cudaStream_t str);
 void launch_set_diag(double *G, int ldg, const double *d, int m, cudaStream_t str);
 void launch_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk,
                        cudaStream_t str);

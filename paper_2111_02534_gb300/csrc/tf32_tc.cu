@@ -41,6 +41,7 @@ struct TfArgs {
   double *out64;                // epi 2
   const float *lamR, *lamN;     // epi 1: divided by lamR[r] + lamN[n] - sigma
   float sigma;
+  const double *sigma_dev;      // nullable: the shift read on the device (takes precedence)
   int epi;                      // 0 FP32 store, 1 FP32 store after the division, 2 FP64 store
   int *err;                     // nonzero after a timed-out wait
 };
@@ -184,7 +185,8 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int v = mvalid ? m / g.R : 0;
     const int r = m - v * g.R;
     const long long rowoff = (long long)v * g.os_v + (long long)r * g.os_r;
-    const float lr = (g.epi == 1 && mvalid) ? g.lamR[r] - g.sigma : 0.f;
+    const float sig = g.sigma_dev ? (float)*g.sigma_dev : g.sigma;
+    const float lr = (g.epi == 1 && mvalid) ? g.lamR[r] - sig : 0.f;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
     // contiguous rows (os_n = 1) are written 16 bytes at a time when aligned
     const bool vec = g.os_n == 1 && ((g.epi == 2) ? (rowoff & 1) == 0 : (rowoff & 3) == 0);
@@ -389,7 +391,8 @@ long long tf_prec_workspace_floats(const DevOperator &op, int nvec) {
 }
 
 int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, int nvec,
-                           double sigma, ApplyWorkspace &ws, cudaStream_t s) {
+                           double sigma, ApplyWorkspace &ws, cudaStream_t s,
+                           const double *sigma_dev) {
   if (nvec <= 0) return TPS_OK;
   TfOperator *t = op.tf;
   if (!t || op.nmodes != 2) return TPS_ERR_INVALID_ARG;
@@ -416,6 +419,7 @@ int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, 
   TfArgs g{};
   g.err = t->err;
   g.sigma = (float)sigma;
+  g.sigma_dev = sigma_dev;
   // pass 1: t0T[v][j][x] = sum_y r[v][x][y] S_y[y][j]
   g.M = nvec * nx; g.N = ny; g.K = ny; g.R = nx; g.BN = t->BNy;
   g.os_v = (long long)ny * XP; g.os_r = 1; g.os_n = XP;

@@ -89,8 +89,10 @@ void free_tc_operator(struct TcOperator *t);
 void free_tf_operator(struct TfOperator *t);
 int ensure_tf_operator(const DevOperator &op);
 long long tf_prec_workspace_floats(const DevOperator &op, int nvec);
+// sigma_dev (nullable): the shift read on the device, in place of sigma.
 int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, int nvec,
-                           double sigma, ApplyWorkspace &ws, cudaStream_t s);
+                           double sigma, ApplyWorkspace &ws, cudaStream_t s,
+                           const double *sigma_dev = nullptr);
 int tf_operator_status(const DevOperator &op);
 // Synchronously reads and clears the timed-out-wait flag of op's tensor-core kernels.
 int tc_operator_status(const DevOperator &op);
@@ -122,6 +124,9 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
                          int ldy, long long bsy, int q, double alpha, double beta, double *C,
                          long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,
                          const int *need = nullptr);
+// Queries the split update's launch configuration for every slab width up front (before
+// a stream capture).
+void prewarm_update_split();
 // Synchronously reads and clears the timed-out-wait flag of the staged split update
 // (1 if a wait gave up since the last call, 0 if not, -1 if the flag cannot be read).
 int update_split_status();
@@ -234,6 +239,11 @@ int ensure_gram_scratch(tps_ctx *ctx, long long doubles);
 void free_operator(DevOperator &op);
 // Build the parity-reduced 1D operator for TPS_X_EVEN / TPS_X_ODD.
 int build_sector_operator(tps_ctx *ctx, int parity);
+// The outer loop as one captured CUDA graph with a device-side convergence test (jd.cpp);
+// TPS_ERR_NOT_CONVERGED when the caller should fall back to solve_impl.
+int solve_graph_impl(tps_ctx *ctx, int k, int parity, double tol, const tps_solver_opts &opts,
+                     double *evals_host, double *evecs_dev, tps_stats *stats,
+                     cudaStream_t stream);
 // The eigensolver for the non-symmetric H of the mapped Chebyshev grid (jd.cpp).
 int solve_nonsym_impl(tps_ctx *ctx, int k, int parity, double tol, int block,
                       const tps_solver_opts *opts, double *evals_host, double *evecs_dev,
@@ -243,11 +253,14 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
                tps_stats *stats, cudaStream_t stream);
 void free_solver_workspace(tps_ctx *ctx);
 long long gram_scratch_doubles(int p, int q, int batch);
+// shift_dev (nullable): the preconditioner's shift read on the device (TF32 preconditioner
+// only), in place of shift.
 int correction_impl(tps_ctx *ctx, const DevOperator &op, const double *Qt, int nq,
                     const double *KQt_cached, int nq_cached, const double *R,
                     const double *theta, int nsys, int steps, int use_prec, double shift,
                     double inner_tol, double *T, int *h_applies, int *prec_applies,
-                    cudaStream_t s, bool direction_only, bool low);
+                    cudaStream_t s, bool direction_only, bool low,
+                    const double *shift_dev = nullptr);
 }  // namespace tps
 
 #define TPS_CUDA_TRY(ctx, expr)                                   \

@@ -411,6 +411,12 @@ const StagedCfg &staged_cfg(int p) {
 
 }  // namespace
 
+// Fill the per-device launch configuration of every slab width (occupancy queries and
+// attributes), so that later launches, e.g. during stream capture, make no such calls.
+void prewarm_update_split() {
+  for (int p = 1; p <= 64; ++p) staged_cfg(p);
+}
+
 void launch_update_split(const double *A, long long lda, long long bsa, int p, const double *Y,
                          int ldy, long long bsy, int q, double alpha, double beta, double *C,
                          long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,

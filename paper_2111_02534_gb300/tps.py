@@ -49,7 +49,7 @@ class SolverOpts(C.Structure):
                 ("h64_dtype", C.c_int), ("rr_method", C.c_int),
                 ("rr_refine_max", C.c_int),
                 ("correction_dtype", C.c_int),
-                ("update_dtype", C.c_int)]
+                ("update_dtype", C.c_int), ("graph", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -69,7 +69,8 @@ class Stats(C.Structure):
                 ("rr_mixed_calls", C.c_int), ("rr_fp32_solves", C.c_int),
                 ("rr_refine_iters", C.c_int), ("rr_groups_rotated", C.c_int),
                 ("rr_fallbacks", C.c_int), ("rr_ms", C.c_double), ("rr_launches", C.c_longlong),
-                ("rr_timed", C.c_longlong),
+                ("rr_timed", C.c_longlong), ("graph_build_ms", C.c_double),
+                ("graph_run_ms", C.c_double),
                 ("resid", C.c_double * 64)]
 
     def as_dict(self):

@@ -66,3 +66,55 @@ def test_batch_argument_checks():
     lam, stats, status = tps.solve_batch([], [], tps.X_EVEN, 1e-12, 2, [])
     assert lam == []
     c.close()
+
+
+def test_graph_solver_all_sweep_instances():
+    """Every one of the 256 sweep instances (uneven grids n = 128 .. 384) solved by the
+    graph-captured outer loop (tps_solver_opts.graph: two host-driven iterations, then one
+    graph launch whose conditional loop runs until a device kernel finds the residuals
+    converged), batched over host threads: each eigenvalue within 1e-10 of the oracle's."""
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    with open(os.path.join(GOLD, "evals_sweep.json")) as f:
+        gold = json.load(f)["instances"]
+    assert len(gold) == 256
+    opts = tps.default_opts()
+    opts.graph = 1
+    worst = 0.0
+    for start in range(0, 256, 64):     # contexts in groups (device memory)
+        part = gold[start:start + 64]
+        ctxs = _contexts(part)
+        evecs = [torch.empty(4, c.info()[0], dtype=torch.float64, device="cuda") for c in ctxs]
+        lam, stats, status = tps.solve_batch(ctxs, [4] * len(ctxs), tps.X_EVEN, 1e-12, 4, evecs,
+                                             opts=opts, nstreams=8)
+        assert all(s == tps.OK for s in status)
+        for l, g in zip(lam, part):
+            ref = np.array(g["evals"])
+            scale = np.maximum(np.abs(ref), abs(ref[0]))
+            err = np.max(np.abs(l - ref) / scale)
+            worst = max(worst, err)
+            assert err <= 1e-10, (g["index"], l, ref)
+        for c in ctxs:
+            c.close()
+    assert worst <= 1e-10
+
+
+def test_graph_solver_matches_host_loop_on_the_n512_workload():
+    """The 8-pair x-even solve of the 512 x 512 workload with the graph-captured loop: the
+    eigenvalues agree with the oracle's to 1e-10 (the tall products take the tensor-core
+    paths inside the captured graph)."""
+    require_gpu()
+    from paper_2111_02534_gb300 import tps
+    from paper_2111_02534_gb300.inputs import WORKLOADS
+    from gpu_common import make_ctx_1d
+    w = WORKLOADS["1d_n512"]
+    with open(os.path.join(GOLD, "evals_1d_n512.json")) as f:
+        g = json.load(f)
+    ctx = make_ctx_1d(w.M, w.m, w.n, w.L, g["v0"], w.sigma)
+    ev = torch.empty(w.k, ctx.info()[0], dtype=torch.float64, device="cuda")
+    opts = tps.default_opts()
+    opts.graph = 1
+    lam, st = ctx.solve(w.k, tps.X_EVEN, 1e-12, w.block, ev, opts=opts)
+    ref = np.array(g["evals"])
+    assert np.max(np.abs(lam - ref) / np.abs(ref)) <= 1e-10
+    ctx.close()

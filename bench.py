@@ -217,9 +217,10 @@ def cpu_oracle_legs(w, v0):
                                "workload (2112 x 2112, H assembled explicitly), 4 pairs"}
 
 
-def run_sweep(tps, torch, nstreams):
-    """The 256-instance sweep (inputs.sweep_instances): contexts set up first (untimed),
-    one warm-up instance per grid size, then one timed tps_solve_batch over all of them.
+def run_sweep(tps, torch, nstreams, graph=0):
+    """The 256-instance sweep (inputs.sweep_instances): contexts set up first (untimed: one
+    full warm-up solve per grid size, one outer iteration per instance for its operators and
+    workspace), then one timed tps_solve_batch over all of them.
     Pairs count when within 1e-10 of the oracle's eigenvalues (tests/golden/evals_sweep.json)."""
     path = os.path.join(ROOT, "tests", "golden", "evals_sweep.json")
     if not os.path.exists(path):
@@ -243,10 +244,19 @@ def run_sweep(tps, torch, nstreams):
     warm = sorted(seen.values())
     tps.solve_batch([ctxs[i] for i in warm], [4] * len(warm), tps.X_EVEN, 1e-12, 4,
                     [evecs[i] for i in warm], nstreams=nstreams)
+    # set-up of every instance outside the timed region: one outer iteration per context
+    # builds its parity-sector operator and allocates its solver workspace
+    setup = tps.default_opts()
+    setup.max_outer = 1
+    setup.graph = graph
+    tps.solve_batch(ctxs, [4] * len(ctxs), tps.X_EVEN, 1e-12, 4, evecs, opts=setup,
+                    nstreams=nstreams)
+    opts = tps.default_opts()
+    opts.graph = graph
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lam, stats, status = tps.solve_batch(ctxs, [4] * len(ctxs), tps.X_EVEN, 1e-12, 4, evecs,
-                                         nstreams=nstreams)
+                                         opts=opts, nstreams=nstreams)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     passing, worst, misses = 0, 0.0, []
@@ -261,7 +271,10 @@ def run_sweep(tps, torch, nstreams):
     for c in ctxs:
         c.close()
     return {"instances": len(gold), "pairs_passing": passing, "eigenpairs_per_s": passing / dt,
-            "wall_s": dt, "nstreams": nstreams, "eigen_rel_err_max": worst, "misses": misses[:8],
+            "wall_s": dt, "nstreams": nstreams, "host_threads": nstreams,
+            "executor": "graph-captured outer loop per instance" if graph else
+                        "host-driven outer loop per instance",
+            "eigen_rel_err_max": worst, "misses": misses[:8],
             "workload": "256 instances, M/m~U[1,40], E0~logU[1e-4,1], sigma in {0.5,1,2}, "
                         "n in {128,192,256,384}, L=20, 4 x-even pairs each, block 4"}
 
@@ -484,10 +497,11 @@ def run_ours(args):
 
     # solver variants on the same input: FP64-only and mixed, FP64 H-applies on the
     # tensor cores (default) or on the FP64 FMA pipe
-    def variant_rate(h_dtype, h64_dtype, reps):
+    def variant_rate(h_dtype, h64_dtype, reps, graph=0):
         o = tps.default_opts()
         o.h_dtype = h_dtype
         o.h64_dtype = h64_dtype
+        o.graph = graph
         step(o)
         ts, ok = [], True
         for _ in range(reps):
@@ -507,13 +521,16 @@ def run_ours(args):
                           ("mixed_fp32_then_fp64_fma", tps.F32, tps.F64)):
         variants[name], ok = variant_rate(hd, h64, reps)
         variants[name + "_all_pass"] = ok
+    variants["fp64_tc_graph"], ok = variant_rate(tps.F64, tps.F64_TC, reps, graph=1)
+    variants["fp64_tc_graph_all_pass"] = ok
     h2d = 8 * N + 8 * w.block * N
     d2h = 8 * w.k * N + 8 * w.k
 
     # batched sweep: the 256 independent instances of uneven grid size solved concurrently
-    sweep = None
+    sweep = sweep_graph = None
     if rank == 0 and not args.no_sweep:
         sweep = run_sweep(tps, torch, args.sweep_streams)
+        sweep_graph = run_sweep(tps, torch, args.sweep_streams, graph=1)
     apply_2d = run_apply_2d(tps, torch) if rank == 0 and not args.no_sweep else None
 
     # per-kernel rates from the solver's own CUDA-event timers over the timed solves; the
@@ -638,7 +655,9 @@ def run_ours(args):
                               "digit-split BF16 tensor-core products (tcgen05 / mma.sync), TF32 "
                               "tensor-core preconditioner, FP64 Gram/Ritz/orthogonalisation",
             "solver_variants": dict(variants, note="eigenpairs/s per GPU; tc = FP64 H-applies "
-                                                   "on the tensor cores, fma = on the FP64 pipe"),
+                                                   "on the tensor cores, fma = on the FP64 pipe; "
+                                                   "graph = the outer loop as one captured CUDA "
+                                                   "graph (tps_solver_opts.graph)"),
             "roofline": roofline,
             "kernels": kernels,
             "e2e": {"value": E_pairs / E_T, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -655,6 +674,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if sweep is not None:
             line["sweep"] = sweep
+        if sweep_graph is not None:
+            line["sweep_graph"] = sweep_graph
         if apply_2d is not None:
             line["h_apply_2d"] = apply_2d
         print(json.dumps(line), flush=True)

@@ -244,8 +244,9 @@ typedef struct tps_solver_opts {
   int graph;          /* 1: after the host-driven outer iterations that fill the first m_min
                          columns, the rest of the solve runs
                          as one CUDA graph launch: the outer iteration is captured once, with
-                         every wanted pair in one block (k <= 16, `block` ignored; the search
-                         space cycles between m_min, rounded up to whole blocks, and m_min + 2k),
+                         every wanted pair in one block (k <= 16, `block` and `guard` ignored;
+                         the search space cycles between m_min (default 4k), rounded up to
+                         whole blocks, and m_min + 2k <= 64),
                          no locking, a fixed preconditioner shift (prec_shift, or the mirror
                          of the lowest Ritz value after the second iteration) and one
                          preconditioned-residual step per correction, inside a conditional

@@ -1063,15 +1063,17 @@ int solve_graph_impl(tps_ctx *ctx, int k_req, int parity, double tol,
                      const tps_solver_opts &opts, double *evals_host, double *evecs_dev,
                      tps_stats *stats, cudaStream_t s) {
   const auto t_start = std::chrono::steady_clock::now();
-  // every wanted pair in the one block; the Rayleigh-Ritz space (up to 4 k) plays the role
+  // every wanted pair in the one block; the Rayleigh-Ritz space (up to 6 k) plays the role
   // of the guard pairs
   const int k = k_req;
   const int b = k;
-  // the host-driven solver's search-space sizes for k + guard pairs, in whole blocks
-  const int kg = k_req + std::max(0, opts.guard);
-  const int m0 = opts.m_min > 0 ? opts.m_min : std::max(2 * kg, 8);
-  const int mmin = ((m0 + b - 1) / b) * b, mmax = mmin + 2 * b;
-  if (mmax > 64 || b > 32) return set_error(ctx, TPS_ERR_INVALID_ARG, "graph solver: k <= 16");
+  // default m_min = 4k (measured on the 256-instance sweep: 12, 16, 20, 24 at k = 4 took
+  // 34, 28, 26, 24 outer iterations, 16 the least time), at most 64 - 2k
+  const int m0 = opts.m_min > 0 ? opts.m_min : std::max(4 * k, 8);
+  int mmin = ((m0 + b - 1) / b) * b;
+  if (mmin + 2 * b > 64) mmin = ((64 - 2 * b) / b) * b;
+  const int mmax = mmin + 2 * b;
+  if (b > 16 || mmin < b) return set_error(ctx, TPS_ERR_INVALID_ARG, "graph solver: k <= 16");
   const DevOperator *opp = &ctx->full;
   if (parity != TPS_ANY) {
     int st = build_sector_operator(ctx, parity);

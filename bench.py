@@ -45,9 +45,22 @@ TC_PAIRS = 54
 # capture of the kernel on this workload; a kernel that changes after its capture is
 # removed from this table
 TRAFFIC_BYTES_PER_LAUNCH = {"k_gram": 42.13e6, "k_tf32_gemm": 5.08e6}
+# the same for kernels whose launches cover a varying number of vectors: (bytes per launch,
+# bytes per vector), fitted to two captured launches of different width (k_oz_gemm: 12 and 8
+# vectors, 49.62 and 35.65 MB)
+TRAFFIC_AFFINE = {"k_oz_gemm": (7.71e6, 3.49e6)}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
 # BF16 digit-pair products per FP64 multiply-add of the split block update
 SPLIT_UPDATE_PAIRS = 34
+
+
+def traffic_per_launch(name, kd):
+    """DRAM bytes per launch of a kernel from its ncu capture (None if not captured since
+    its last change); for kernels over a varying vector count, at the bench's mean count."""
+    if name in TRAFFIC_AFFINE and kd.get("vectors_per_launch"):
+        a, b = TRAFFIC_AFFINE[name]
+        return a + b * kd["vectors_per_launch"]
+    return TRAFFIC_BYTES_PER_LAUNCH.get(name)
 
 
 def measured_peaks():
@@ -556,6 +569,7 @@ def run_ours(args):
             "frac": tflops / bf16_peak if bf16_peak else None,
             "peak_note": "bf16_tflops_sustained of measured (cuBLAS bf16, seconds-long loop)",
             "fp64_equivalent_tflops": h_fl / (h_ms / 1000.0) / 1e12,
+            "vectors_per_launch": tot("h_applies") / max(tot("h_launches"), 1),
             "launches": tot("h_launches"), "share": h_ms / 1000.0 / step_s}
     # every 4th Gram / update / Ritz launch is timed (stats doc): rates come from the timed
     # launches, the share of the step is scaled up to all launches
@@ -628,7 +642,7 @@ def run_ours(args):
         launches = kd["launches"]
         roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                     "unit": kd["unit"], "frac": kd["frac"],
-                    "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kernel": dom,
+                    "traffic": traffic_per_launch(dom, kd), "kernel": dom,
                     "peak_note": kd["peak_note"], "launches": launches,
                     "time_share_of_step": kd["share"]}
     clocks = clk.summary()

@@ -149,9 +149,8 @@ int tps_two_body_v0(int dim, double mu_hl, double hbar, double E0, int shape, do
  * else TPS_ERR_INVALID_ARG.  With lam_host, S_host and Sinv_host non-null it also writes
  * the fast-diagonalisation factors of the Sec. 4.2 preconditioner on this grid,
  * D2 = S diag(lam) S^-1 (lam ascending, unit columns of S, row-major), from a host QR
- * eigensolver; TPS_ERR_SINGULAR if D2 has a complex pair or S is singular.  (The solver
- * works on the periodic Fourier grid; this is the operator construction for the
- * paper's grid.) */
+ * eigensolver; TPS_ERR_SINGULAR if D2 has a complex pair or S is singular.  A context
+ * takes this grid through tps_set_grid_chebyshev. */
 int tps_chebyshev_grid(int n, double L, double *y_host, double *D2_host, double *lam_host,
                        double *S_host, double *Sinv_host);
 
@@ -247,8 +246,9 @@ typedef struct tps_solver_opts {
                          every wanted pair in one block (k <= 16, `block` and `guard` ignored;
                          the search space cycles between m_min (default 4k), rounded up to
                          whole blocks, and m_min + 2k <= 64),
-                         no locking, a fixed preconditioner shift (prec_shift, or the mirror
-                         of the lowest Ritz value after the second iteration) and one
+                         no locking, the preconditioner shift prec_shift if given, else set
+                         on the device every iteration from the lowest unconverged Ritz value
+                         (converged pairs get no correction), and one
                          preconditioned-residual step per correction, inside a conditional
                          WHILE node whose condition a device kernel sets from the residual
                          norms.  Falls back to the host-driven loop if the cycle does not

@@ -976,9 +976,10 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
 
 // ---------------------------------------------------------------------------------------
 // The outer loop as a captured CUDA graph (tps_solver_opts.graph).  With every wanted pair
-// in one block (b = k), no locking, a fixed preconditioner shift and one
-// preconditioned-residual step per correction (the projected direction -Kt^-1 r of Eq.
-// jdcor), the search space follows a fixed cycle -- m = m_min -> m_min + b -> m_max =
+// in one block (b = k), no locking, the preconditioner shift kept on the device (a kernel
+// sets it from the lowest unconverged Ritz value each iteration, unless prec_shift fixes it)
+// and one preconditioned-residual step per correction (the projected direction -Kt^-1 r of
+// Eq. jdcor), the search space follows a fixed cycle -- m = m_min -> m_min + b -> m_max =
 // m_min + 2b, restart to m_min -- and every kernel of an outer iteration has sizes known in
 // advance.  The only data-dependent decision, "converged?", is taken on the device
 // (k_conv_check) and drives a conditional WHILE node around the captured two-iteration

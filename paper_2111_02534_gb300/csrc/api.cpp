@@ -204,6 +204,20 @@ int build_operator(tps_ctx *ctx, DevOperator &op, const std::vector<HostMode> &m
   }
   op.lam_min_sum = lmin;
   op.lam_max_sum = lmax;
+  // the eigenvalue sums of modes 1.. sorted once, for the per-call singularity test
+  op.lam_rest.assign(1, 0.0);
+  for (int k = 1; k < op.nmodes && !op.lam_rest.empty(); ++k) {
+    if (op.lam_rest.size() * op.lam_h[k].size() > (1u << 22)) {
+      op.lam_rest.clear();
+      break;
+    }
+    std::vector<double> nx;
+    nx.reserve(op.lam_rest.size() * op.lam_h[k].size());
+    for (double a : op.lam_rest)
+      for (double b : op.lam_h[k]) nx.push_back(a + b);
+    op.lam_rest.swap(nx);
+  }
+  std::sort(op.lam_rest.begin(), op.lam_rest.end());
   TPS_CUDA_TRY(ctx, cudaMalloc((void **)&op.V, op.N * sizeof(double)));
   if (V) {
     TPS_CUDA_TRY(ctx, cudaMemcpy(op.V, V->data(), op.N * sizeof(double), cudaMemcpyHostToDevice));
@@ -270,21 +284,12 @@ int check_ready(tps_ctx *ctx) {
 
 // Preconditioner singularity test against the host copy of the eigenvalues.
 bool prec_singular(const DevOperator &op, double theta) {
-  // minimum over the Kronecker sum of |lambda_sum - theta|: the sums are not stored,
-  // so bound it by scanning mode 0 against the sorted sums of the other modes.
-  std::vector<double> rest(1, 0.0);
-  for (int k = 1; k < op.nmodes; ++k) {
-    std::vector<double> nx;
-    nx.reserve(rest.size() * op.lam_h[k].size());
-    for (double a : rest)
-      for (double b : op.lam_h[k]) nx.push_back(a + b);
-    rest.swap(nx);
-    if (rest.size() > (1u << 22)) break;  // large 2D grids: fall back to the range test below
-  }
+  // minimum over the Kronecker sum of |lambda_sum - theta|: mode 0 scanned against the
+  // sorted sums of the other modes (built with the operator)
+  const std::vector<double> &rest = op.lam_rest;
   const double scale = std::max(std::fabs(op.lam_max_sum), std::fabs(op.lam_min_sum));
   double mind = std::numeric_limits<double>::infinity();
-  if ((int)rest.size() <= (1 << 22)) {
-    std::sort(rest.begin(), rest.end());
+  if (!rest.empty()) {
     for (double a : op.lam_h[0]) {
       const double target = theta - a;
       auto it = std::lower_bound(rest.begin(), rest.end(), target);
@@ -317,6 +322,7 @@ void free_operator(DevOperator &op) {
     op.Sf[k] = op.STf[k] = op.lamf[k] = op.Kf[k] = op.KTf[k] = nullptr;
     op.lam_h[k].clear();
   }
+  op.lam_rest.clear();
   free_tc_operator(op.tc);
   free_tf_operator(op.tf);
   op.tf = nullptr;
@@ -509,6 +515,7 @@ int tps_set_grid(tps_ctx *ctx, const int *n, const double *L) {
   long long N = 1;
   for (int k = 0; k < nm; ++k) N *= n[k];
   ctx->V_host.assign((size_t)N, 0.0);
+  ctx->vmax_ok = false;
   int st = build_operator(ctx, ctx->full, modes, &ctx->V_host);
   if (st) return st;
   for (int p = 0; p < 3; ++p) {
@@ -546,6 +553,7 @@ int tps_set_grid_chebyshev(tps_ctx *ctx, const int *n, const double *L) {
   ctx->grid_kind = 1;
   const long long N = (long long)n[0] * n[1];
   ctx->V_host.assign((size_t)N, 0.0);
+  ctx->vmax_ok = false;
   int st = build_operator(ctx, ctx->full, modes, &ctx->V_host);
   if (st) return st;
   for (int p = 0; p < 3; ++p) {
@@ -563,6 +571,7 @@ int tps_set_grid_chebyshev(tps_ctx *ctx, const int *n, const double *L) {
 int tps_set_potential(tps_ctx *ctx, const double *V, int on_device) {
   int st = check_ready(ctx);
   if (st) return st;
+  ctx->vmax_ok = false;
   if (!V) return set_error(ctx, TPS_ERR_INVALID_ARG, "null potential");
   cudaSetDevice(ctx->device);
   const size_t bytes = ctx->full.N * sizeof(double);
@@ -589,6 +598,7 @@ int tps_set_potential(tps_ctx *ctx, const double *V, int on_device) {
 int tps_set_pair_potential(tps_ctx *ctx, int shape, double v0, double sigma) {
   int st = check_ready(ctx);
   if (st) return st;
+  ctx->vmax_ok = false;
   if ((shape != TPS_GAUSS && shape != TPS_LORENTZ3) || !(sigma > 0) || !std::isfinite(v0))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad shape, sigma or v0");
   std::vector<double> V(ctx->full.N);
@@ -652,9 +662,13 @@ int tps_get_info(const tps_ctx *ctx, long long *N, double *hnorm_est) {
       const double a = ctx->dim == 1 ? ctx->a[k] : ctx->a[k / 2];
       s += std::fabs(a) * (kPi / h) * (kPi / h);
     }
-    double vmax = 0.0;
-    for (double v : ctx->V_host) vmax = std::max(vmax, std::fabs(v));
-    *hnorm_est = s + vmax;
+    if (!ctx->vmax_ok) {  // scanned once per potential
+      double vmax = 0.0;
+      for (double v : ctx->V_host) vmax = std::max(vmax, std::fabs(v));
+      ctx->vmax = vmax;
+      ctx->vmax_ok = true;
+    }
+    *hnorm_est = s + ctx->vmax;
   }
   return TPS_OK;
 }

@@ -46,6 +46,8 @@ struct DevOperator {
   float *Vf = nullptr;
   double *V = nullptr;                                   // [N]
   std::vector<double> lam_h[4];                          // host copies (singularity test)
+  std::vector<double> lam_rest;  // sorted sums of the eigenvalues of modes 1.. (singularity
+                                 // test; empty when there are more than 2^22 of them)
   double lam_min_sum = 0.0, lam_max_sum = 0.0;
   bool owns = true;
   // tensor-core (BF16 digit slice) form of the mode matrices, built on first use
@@ -221,6 +223,8 @@ struct tps_ctx {
                                        // roots (tps_set_grid_chebyshev, 1D)
   std::vector<double> pts[2];          // grid points of x and y (mapped Chebyshev grids)
   std::vector<double> V_host;          // potential on the full grid
+  mutable double vmax = 0.0;           // max |V_host| (tps_get_info), valid if vmax_ok
+  mutable bool vmax_ok = false;
   tps::DevOperator full;               // full grid operator
   tps::DevOperator sect[3];            // [TPS_X_EVEN], [TPS_X_ODD] parity-reduced 1D operators
   bool sect_ready[3] = {false, false, false};

@@ -256,10 +256,12 @@ TF32_TOL = 1e-2
 
 @pytest.mark.parametrize("n,nvec,theta", [((64, 64), 3, -0.5), ((100, 70), 2, -1.3),
                                           ((12, 8), 4, -0.05), ((130, 200), 1, -2.0),
-                                          ((66, 34), 9, -0.3)])
+                                          ((66, 34), 9, -0.3), ((64, 64), 20, -0.5),
+                                          ((258, 128), 17, -0.7)])
 def test_apply_prec_1d_tf32(n, nvec, theta):
     # padded rows (70, 130, 34, 66 are not multiples of 4 floats), K below one 32-wide
-    # tile (n = 8, 12), M and N ragged against the 128 x 64 tiles
+    # tile (n = 8, 12), M and N ragged against the 128 x 64 tiles; more vectors than one
+    # launch takes (16), tiles spanning several vectors
     require_gpu()
     tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
     L = (20.0, 15.0)

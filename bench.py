@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -44,7 +45,7 @@ TC_PAIRS = 54
 # DRAM bytes (read + write) per launch of each kernel, mean over the launches of one ncu
 # capture of the kernel on this workload; a kernel that changes after its capture is
 # removed from this table
-TRAFFIC_BYTES_PER_LAUNCH = {"k_gram": 42.13e6, "k_tf32_gemm": 5.08e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_tf32_gemm": 5.08e6}
 # the same for kernels whose launches cover a varying number of vectors: (bytes per launch,
 # bytes per vector), fitted to two captured launches of different width (k_oz_gemm: 12 and 8
 # vectors, 49.62 and 35.65 MB)
@@ -137,6 +138,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
+        self.lines = []
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
         try:
@@ -146,17 +152,26 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        # the timed region starts once nvidia-smi has initialised and taken its first
+        # sample, so that its start-up does not fall inside it
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
+                self.proc.wait()
+            self.reader.join(timeout=5)
+        self.out = "".join(self.lines)
 
     def summary(self):
         rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 7]
@@ -578,13 +593,18 @@ def run_ours(args):
     n_timed = sum((st_.gram_launches + 3) // 4 for st_ in stats)
     if ms > 0:
         a = fl / (ms / 1000.0) / 1e12
+        gbs = by / (ms / 1000.0) / 1e9
         kernels["k_gram"] = {
-            "what": "FP64 Gram products A^T B (one launch, split rows, FP64 FMA)",
-            "bound": "alu", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": a / fp64_peak,
-            "peak_note": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz (nominal-derived)",
-            "hbm_gbs": by / (ms / 1000.0) / 1e9,
-            "hbm_frac": by / (ms / 1000.0) / 1e9 / hbm_peak if hbm_peak else None,
+            "what": "FP64-accurate Gram products G = A^T B: digit-split BF16 products "
+                    "(k_gram_split, mma.sync, exponents per 64-row block) for blocks of >= 1e5 "
+                    "rows, FP64 FMA (k_gram) below; algorithmic bytes 8 nrows (p + q)",
+            "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": gbs / hbm_peak if hbm_peak else None,
+            "peak_note": "hbm_gbs of measured (STREAM-style copy)",
+            "fp64_equivalent_tflops": a,
+            "fp64_pipe_frac": a / fp64_peak,
+            "fp64_pipe_note": "FP64-equivalent rate against the FP64 FMA pipe "
+                              "(4 flop/clk/SM x 152 SMs x 2070 MHz, nominal-derived)",
             "launches": n_all, "timed_launches": n_timed,
             "share": ms * n_all / max(n_timed, 1) / 1000.0 / step_s}
     ms, fl, by = tot("upd_ms"), tot("upd_flops"), tot("upd_bytes")

@@ -254,6 +254,12 @@ typedef struct tps_solver_opts {
                          norms.  Falls back to the host-driven loop if the cycle does not
                          converge within max_outer iterations.  1D Fourier grids, no warm
                          start; ignored otherwise.  Default 0 */
+  int gram_dtype;     /* arithmetic of the FP64 Gram products of the outer iteration
+                         (orthogonalisation coefficients, Cholesky-QR Grams, the
+                         Rayleigh-Ritz matrix): TPS_F64_TC (default: digit-split products on
+                         the tensor cores, tps_gram_tc, for blocks of 10^5 rows or more with
+                         min(p, q) <= 8 and max(p, q) <= 64; others on the FMA pipe) or
+                         TPS_F64 (FMA pipe).  Symmetric solver only */
 } tps_solver_opts;
 
 typedef struct tps_stats {
@@ -349,6 +355,18 @@ int tps_solve_batch(tps_ctx **ctxs, int ninst, const int *k, int parity, double 
 int tps_gram(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *B_dev,
              long long ldb, int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream);
 
+/* The same Gram matrix, FP64-accurate, as digit-split BF16 products on the tensor cores
+ * (the Ozaki scheme; the solver's default for its FP64 Grams): per block of 64 rows each
+ * column of A and of B is scaled by a power of two and its 55-bit integer cut into seven
+ * base-256 digits; the digit pairs of levels 0..7 are multiplied exactly, each block's sum
+ * is rounded once to FP64 and the blocks are added in FP64.  Error per entry within a small
+ * multiple of an FP64 dot product's, 2^-53 (max_r |A[r][i]| sum_r |B[r][j]| + max_r |B[r][j]|
+ * sum_r |A[r][i]|) per block of rows.  min(p, q) <= 8 and max(p, q) <= 64, else
+ * TPS_ERR_INVALID_ARG; otherwise the same arguments and errors as tps_gram.  The result
+ * does not depend on launch scheduling (partial sums added in a fixed order). */
+int tps_gram_tc(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *B_dev,
+                long long ldb, int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream);
+
 /* Block update C = beta*C + A Y (p, q <= 64); Y_dev: device p x q, leading
  * dimension ldy.  C must not overlap A. */
 int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *Y_dev,
@@ -357,10 +375,10 @@ int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, co
 
 /* The same block update, FP64-accurate, computed as digit-split BF16 products on the
  * tensor cores (the Ozaki scheme; the solver's default for its FP64 updates): each row of A
- * and each column of Y is scaled by a power of two and cut into nine 6-bit digits, the
- * digit pairs of nine or fewer levels are multiplied exactly and combined in integer
- * arithmetic.  Error per entry at most about 2^-53 max_k |A[r][k]| sum_k |Y[k][j]|.  Same
- * arguments, limits and errors as tps_block_update. */
+ * and each column of Y is scaled by a power of two and its 55-bit integer cut into seven
+ * base-256 digits, the digit pairs of levels 0..7 are multiplied exactly and combined in
+ * integer arithmetic.  Error per entry at most about 2^-53 max_k |A[r][k]| sum_k |Y[k][j]|.
+ * Same arguments, limits and errors as tps_block_update. */
 int tps_block_update_tc(tps_ctx *ctx, const double *A_dev, long long lda, int p,
                         const double *Y_dev, int ldy, int q, double beta, double *C_dev,
                         long long ldc, long long nrows, cudaStream_t stream);

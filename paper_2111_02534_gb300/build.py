@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libtps.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gemm_f64.cu", "gemm_f32.cu", "blocks_f64.cu", "jd_kernels.cu", "api.cpp", "jd.cpp",
-           "batch.cpp", "gram_noalloc.cu", "ozaki_tc.cu", "mlp.cu", "rr_eigh.cu", "tf32_tc.cu", "update_mma.cu", "host_eig.cpp"]
+           "batch.cpp", "gram_noalloc.cu", "ozaki_tc.cu", "mlp.cu", "rr_eigh.cu", "tf32_tc.cu", "update_mma.cu", "host_eig.cpp",
+           "gram_mma.cu"]
 
 
 def _nvcc() -> str:

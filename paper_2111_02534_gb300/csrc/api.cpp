@@ -909,6 +909,17 @@ int tps_gram(tps_ctx *ctx, const double *A_dev, long long lda, int p, const doub
   return TPS_OK;
 }
 
+int tps_gram_tc(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *B_dev,
+                long long ldb, int q, long long nrows, double *G_dev, int ldg, cudaStream_t stream) {
+  if (!ctx) return TPS_ERR_INVALID_ARG;
+  if (p < 1 || q < 1 || !gram_split_supported(p, q, 1) || nrows < 0 || lda < nrows ||
+      ldb < nrows || ldg < p || !G_dev || (nrows > 0 && (!A_dev || !B_dev)))
+    return set_error(ctx, TPS_ERR_INVALID_ARG, "bad gram_tc arguments");
+  launch_gram_split(A_dev, lda, p, B_dev, ldb, q, nrows, G_dev, ldg, ctx->gscr, stream);
+  TPS_CUDA_TRY(ctx, cudaGetLastError());
+  return TPS_OK;
+}
+
 int tps_block_update(tps_ctx *ctx, const double *A_dev, long long lda, int p, const double *Y_dev,
                      int ldy, int q, double beta, double *C_dev, long long ldc, long long nrows,
                      cudaStream_t stream) {

@@ -141,6 +141,7 @@ void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
 // Timers of the running solve (tps_solver_opts.timing), for the skinny-kernel wrappers.
 thread_local PhaseTiming *tl_timing = nullptr;
 thread_local bool tl_split_updates = false;  // FP64 updates as digit-split tensor-core products
+thread_local bool tl_split_grams = false;    // FP64 Grams as digit-split tensor-core products
 
 // launch_gram / launch_update with CUDA-event timing and algorithmic work counts
 // low: FP32-arithmetic products (the correction equation's); like conditional launches
@@ -159,7 +160,11 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
     b = t->get();
     cudaEventRecord(a, s);
   }
-  launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need, low);
+  // as for the updates, the split pays on tall blocks only
+  if (!low && tl_split_grams && nrows >= 100000 && gram_split_supported(p, q, batch))
+    launch_gram_split(A, lda, p, B, ldb, q, nrows, G, ldg, scr, s, need);
+  else
+    launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need, low);
   if (rec) {
     cudaEventRecord(b, s);
     t->pend[3].push_back({a, b});
@@ -591,15 +596,17 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
   TPS_CUDA_TRY(ctx, cudaMemsetAsync(w.dgks, 0, 4 * sizeof(int), s));
   // per-solve thread-local state of tupdate/tgram: the phase timers and the update arithmetic
   struct SolveScope {
-    explicit SolveScope(PhaseTiming *t, bool split) {
+    explicit SolveScope(PhaseTiming *t, bool split, bool split_gram) {
       tl_timing = t;
       tl_split_updates = split;
+      tl_split_grams = split_gram;
     }
     ~SolveScope() {
       tl_timing = nullptr;
       tl_split_updates = false;
+      tl_split_grams = false;
     }
-  } solve_scope(&w.tm, opts.update_dtype == TPS_F64_TC);
+  } solve_scope(&w.tm, opts.update_dtype == TPS_F64_TC, opts.gram_dtype == TPS_F64_TC);
   // the TF32 tensor-core preconditioner exists for the 1D operator; 2D solves use FP32
   w.prec_dtype = opts.prec_dtype == TPS_F64
                      ? TPS_F64
@@ -1099,12 +1106,16 @@ int solve_graph_impl(tps_ctx *ctx, int k_req, int parity, double tol,
   }
   if (w.h64_dtype == TPS_F64_TC) TPS_CUDA_TRY(ctx, ensure_tc_operator(op, s));
   struct Scope {
-    explicit Scope(bool split) {
+    explicit Scope(bool split, bool split_gram) {
       tl_timing = nullptr;
       tl_split_updates = split;
+      tl_split_grams = split_gram;
     }
-    ~Scope() { tl_split_updates = false; }
-  } scope(opts.update_dtype == TPS_F64_TC);
+    ~Scope() {
+      tl_split_updates = false;
+      tl_split_grams = false;
+    }
+  } scope(opts.update_dtype == TPS_F64_TC, opts.gram_dtype == TPS_F64_TC);
   const long long launches0 = g_kernel_launches.load();
   double hnorm = 0.0;
   tps_get_info(ctx, nullptr, &hnorm);
@@ -1348,6 +1359,7 @@ int solve_nonsym_impl(tps_ctx *ctx, int k_req, int parity, double tol, int block
     explicit Scope(PhaseTiming *t) {
       tl_timing = t;
       tl_split_updates = false;  // the Ritz products stay FP64 (non-orthogonal Y)
+      tl_split_grams = false;
     }
     ~Scope() { tl_timing = nullptr; }
   } scope(&w.tm);
@@ -1562,6 +1574,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->prec_dtype = TPS_TF32_TC;  // 1D; 2D solves use TPS_F32
   o->correction_dtype = TPS_F32;
   o->update_dtype = TPS_F64_TC;
+  o->gram_dtype = TPS_F64_TC;
   o->h_dtype = TPS_F64;
   o->switch_tol = 1e-6;
   o->refine_block = 0;

@@ -126,6 +126,13 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
                          int ldy, long long bsy, int q, double alpha, double beta, double *C,
                          long long ldc, long long bsc, long long nrows, int batch, cudaStream_t s,
                          const int *need = nullptr);
+// G = A^T B, FP64-accurate, as digit-split BF16 products on the tensor cores (gram_mma.cu),
+// exponents per 64-row block; for batch 1, min(p, q) <= 8 and max(p, q) <= 64
+// (gram_split_supported); need as for launch_gram.
+bool gram_split_supported(int p, int q, int batch);
+void launch_gram_split(const double *A, long long lda, int p, const double *B, long long ldb,
+                       int q, long long nrows, double *G, int ldg, GramScratch &scr,
+                       cudaStream_t s, const int *need = nullptr);
 // Queries the split update's launch configuration for every slab width up front (before
 // a stream capture).
 void prewarm_update_split();

@@ -49,7 +49,7 @@ class SolverOpts(C.Structure):
                 ("h64_dtype", C.c_int), ("rr_method", C.c_int),
                 ("rr_refine_max", C.c_int),
                 ("correction_dtype", C.c_int),
-                ("update_dtype", C.c_int), ("graph", C.c_int)]
+                ("update_dtype", C.c_int), ("graph", C.c_int), ("gram_dtype", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -105,6 +105,7 @@ _sig = {
     "tps_solve": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_int, _vp, C.c_int,
                             C.POINTER(SolverOpts), _dp, _vp, C.POINTER(Stats), _vp]),
     "tps_gram": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
+    "tps_gram_tc": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, _ll, C.c_int, _ll, _vp, C.c_int, _vp]),
     "tps_block_update": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, C.c_int, C.c_int, C.c_double,
                                    _vp, _ll, _ll, _vp]),
     "tps_block_update_tc": (C.c_int, [_vp, _vp, _ll, C.c_int, _vp, C.c_int, C.c_int, C.c_double,
@@ -309,9 +310,11 @@ class Context:
         return np.array(ev[: stats.n_converged]), stats
 
     # ---- building blocks ----------------------------------------------------------
-    def gram(self, A, p, B, q, nrows, G, ldg=None, lda=None, ldb=None, stream=None):
-        self._check(_lib.tps_gram(self._h, _ptr(A), lda or nrows, p, _ptr(B), ldb or nrows, q,
-                                  nrows, _ptr(G), ldg or p, _stream(stream)), "gram")
+    def gram(self, A, p, B, q, nrows, G, ldg=None, lda=None, ldb=None, stream=None, dtype=F64):
+        """G = A^T B; dtype F64 (FMA pipe) or F64_TC (digit-split tensor-core products)."""
+        fn = _lib.tps_gram_tc if dtype == F64_TC else _lib.tps_gram
+        self._check(fn(self._h, _ptr(A), lda or nrows, p, _ptr(B), ldb or nrows, q, nrows,
+                       _ptr(G), ldg or p, _stream(stream)), "gram")
 
     def block_update(self, A, p, Y, q, beta, Cm, nrows, ldy=None, stream=None, dtype=F64):
         """C = beta C + A Y; dtype F64 (FMA pipe) or F64_TC (digit-split tensor-core products)."""

@@ -37,6 +37,88 @@ def test_gram(ctx, nrows, p, q):
     assert np.max(np.abs(got - ref)) <= 1e-14 * scale * max(1.0, np.abs(ref).max())
 
 
+def _gram_bound(A, B):
+    # the split Gram's error per entry: per 64-row block at most ~2^-53 (max|A_i| sum|B_j| +
+    # sum|A_i| max|B_j|) (slack 4), plus the FP64 sum over the blocks and the reference's
+    # rounding, at most (blocks + 2) 2^-53 sum |A_i| |B_j|
+    p, n = A.shape
+    q = B.shape[0]
+    nb = (n + 63) // 64
+    Ap = np.zeros((p, nb * 64))
+    Bp = np.zeros((q, nb * 64))
+    Ap[:, :n] = np.abs(A)
+    Bp[:, :n] = np.abs(B)
+    Ab, Bb = Ap.reshape(p, nb, 64), Bp.reshape(q, nb, 64)
+    amax, asum = Ab.max(axis=2), Ab.sum(axis=2)    # p x nb
+    bmax, bsum = Bb.max(axis=2), Bb.sum(axis=2)    # q x nb
+    bound = 4 * 2.0 ** -53 * (amax @ bsum.T + asum @ bmax.T)
+    return bound + (nb + 2) * 2.0 ** -53 * (np.abs(A) @ np.abs(B).T)
+
+
+def _exact_gram(A, B):
+    # the reference in the widest float numpy has (80-bit or 128-bit long double)
+    return (A.astype(np.longdouble) @ B.astype(np.longdouble).T).astype(np.float64)
+
+
+@pytest.mark.parametrize("nrows,p,q", [(131584, 24, 8), (131590, 36, 8), (100003, 64, 8),
+                                       (70001, 8, 40), (1000, 17, 5), (200000, 48, 2),
+                                       (777, 1, 1), (65, 16, 3), (64, 3, 64), (0, 5, 5)])
+def test_gram_tc(ctx, nrows, p, q):
+    # digit-split Gram: ragged last 64-row block, one to four 16-column m tiles, p < q
+    # (operands swapped, result stored transposed), tiny and empty inputs; against the
+    # exact product within the scheme's bound, against the FMA-pipe Gram, and the same bits
+    # on a second call
+    from paper_2111_02534_gb300 import tps
+    A = random_block(p, max(nrows, 1), 21)[:, :nrows]
+    B = random_block(q, max(nrows, 1), 22)[:, :nrows]
+    G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+    dA, dB = dev(np.ascontiguousarray(A)), dev(np.ascontiguousarray(B))
+    ctx.gram(dA, p, dB, q, nrows, G, dtype=tps.F64_TC)
+    got = host(G).T
+    if nrows == 0:
+        assert np.all(got == 0.0)
+        return
+    assert np.all(np.abs(got - _exact_gram(A, B)) <= _gram_bound(A, B))
+    G64 = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+    ctx.gram(dA, p, dB, q, nrows, G64)
+    ref64 = host(G64).T
+    scale = np.outer(np.linalg.norm(A, axis=1), np.linalg.norm(B, axis=1))
+    assert np.all(np.abs(got - ref64) <= 1e-14 * scale)
+    G2 = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+    ctx.gram(dA, p, dB, q, nrows, G2, dtype=tps.F64_TC)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
+@pytest.mark.parametrize("nrows,p,q", [(131584, 40, 8), (100001, 8, 8), (5003, 33, 4)])
+def test_gram_tc_graded(ctx, nrows, p, q):
+    # columns spanning many binades (1e-8 .. 1e8), rows inside a column over 1e-12 .. 1e12
+    # (so one 64-row block's scale differs from the next), entries over 1e-6 .. 1, zeros
+    from paper_2111_02534_gb300 import tps
+    rng = np.random.default_rng(nrows + p)
+    A = rng.standard_normal((p, nrows)) * 10.0 ** rng.uniform(-6, 0, (p, nrows))
+    A *= 10.0 ** rng.uniform(-12, 12, nrows)[None, :] * 10.0 ** rng.uniform(-8, 8, p)[:, None]
+    B = rng.standard_normal((q, nrows)) * 10.0 ** rng.uniform(-12, 12, nrows)[None, :]
+    A[:, ::97] = 0.0
+    B[:, 5] = 0.0
+    G = torch.full((q, p), np.nan, dtype=torch.float64, device="cuda")
+    ctx.gram(dev(A), p, dev(B), q, nrows, G, dtype=tps.F64_TC)
+    got = host(G).T
+    assert np.all(np.abs(got - _exact_gram(A, B)) <= _gram_bound(A, B) + 1e-300)
+
+
+def test_gram_tc_rejects_wide_blocks(ctx):
+    from paper_2111_02534_gb300 import tps
+    x = dev(random_block(9, 100, 1))
+    G = torch.empty(81, dtype=torch.float64, device="cuda")
+    with pytest.raises(tps.TpsError):
+        ctx.gram(x, 9, x, 9, 100, G, dtype=tps.F64_TC)
+    y = dev(random_block(65, 100, 1))
+    G = torch.empty(65, dtype=torch.float64, device="cuda")
+    with pytest.raises(tps.TpsError):
+        ctx.gram(y, 65, x, 1, 100, G, dtype=tps.F64_TC)
+
+
 @pytest.mark.parametrize("nrows,p,q,beta", [(131584, 24, 8, 0.0), (100003, 70, 3, 1.0),
                                             (513, 1, 17, -0.5), (1000, 0, 4, 2.0),
                                             # column tiles 1, 2, 4 (ragged), 8, 8 + 1

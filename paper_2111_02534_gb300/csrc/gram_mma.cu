@@ -19,8 +19,8 @@
 // Work: one warp per 64-row block (grid-stride).  The warp splits its block of B into
 // digit fragments once and runs through A's columns 16 at a time.  Partial sums stay in
 // FP64 registers per warp, then go through shared memory (per CTA) and the scratch array
-// (per CTA), which the last CTA to finish sums in CTA order: the result does not depend on
-// scheduling.
+// (per CTA), which the last CTA of each group of 8 and then the last group sum in a fixed
+// order: the result does not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include "split_digits.cuh"
@@ -34,6 +34,8 @@ using namespace b256;
 constexpr int kGW = 8;        // warps per CTA
 constexpr int kGRows = 64;    // rows per block: one exponent per column and block
 constexpr int kGQ = 8;        // B columns (one n tile)
+constexpr int kGroup = 8;     // CTAs per group of the two-level reduction
+constexpr int kMaxGroups = 32;  // groups (CTAs <= kGroup kMaxGroups)
 
 struct GramArgs {
   const double *A;
@@ -46,8 +48,8 @@ struct GramArgs {
   double *G;
   int ldg;
   int trans;          // 1: store G^T (the operands were swapped so that p >= q)
-  double *partial;    // gridDim.x x (16 MT x kGQ) partial sums
-  unsigned *count;    // one ticket counter, zero between calls
+  double *partial;    // gridDim.x, then ceil(gridDim.x / kGroup), x (16 MT x kGQ) sums
+  unsigned *count;    // tickets: [0] groups, [1 + g] CTAs of group g; zero between calls
   const int *need;    // nullable: skip the product when *need == 0
   int vec;            // A, B, lda, ldb allow 16-byte loads of row pairs
 };
@@ -138,10 +140,13 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt) {
       // A: columns 16 mt + gq (fragment rows g) and + 8 (rows g + 8)
+      // when the m tile's upper 8 columns are all past p (p <= 8, or a ragged last tile),
+      // the warp skips them: zero fragments, no loads, no splitting
+      const bool upper = 16 * mt + 8 < g.p;
       double av[2][4][4];
       load_col(g.A, g.lda, g.p, 16 * mt + gq, r0, g.nrows, c, g.vec, av[0]);
-      load_col(g.A, g.lda, g.p, 16 * mt + gq + 8, r0, g.nrows, c, g.vec, av[1]);
-      const unsigned e0 = col_raw_max(av[0]), e1 = col_raw_max(av[1]);
+      if (upper) load_col(g.A, g.lda, g.p, 16 * mt + gq + 8, r0, g.nrows, c, g.vec, av[1]);
+      const unsigned e0 = col_raw_max(av[0]), e1 = upper ? col_raw_max(av[1]) : 0u;
       float lv[kUL][4];
 #pragma unroll
       for (int l = 0; l < kUL; ++l)
@@ -154,6 +159,11 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int col = r & 1, h = r >> 1;
+          if (col && !upper) {
+#pragma unroll
+            for (int i = 0; i < kUS; ++i) af[i][r] = 0u;
+            continue;
+          }
           uint32_t d[kUS];
           digits_pair(av[col][ks][2 * h], av[col][ks][2 * h + 1], col ? e1 : e0, d);
 #pragma unroll
@@ -191,31 +201,62 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
     for (int t = 0; t < 4; ++t)
       red[warp][(16 * mt + gq + 8 * (t >> 1)) * kGQ + 2 * c + (t & 1)] = acc[mt][t];
   __syncthreads();
-  double *part = g.partial + (long long)blockIdx.x * (P * kGQ);
-  for (int e = threadIdx.x; e < P * kGQ; e += blockDim.x) {
+  constexpr int E = P * kGQ;
+  double *part = g.partial + (long long)blockIdx.x * E;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kGW; ++w) s += red[w][e];
     part[e] = s;
   }
+  // Two-level reduction over the CTAs, in a fixed order: the last CTA of each group of
+  // kGroup adds the group's partial sums, the last group adds the group sums.  Every
+  // thread issues all its loads of a level before adding them.
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int gsize = min(kGroup, (int)gridDim.x - grp * kGroup);
   __threadfence();  // this CTA's sums are visible before its ticket is taken
   __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(g.count, 1u);
+  if (threadIdx.x == 0) ticket = atomicAdd(g.count + 1 + grp, 1u);
   __syncthreads();
-  if (ticket != gridDim.x - 1) return;
-  // the last CTA: every partial sum is in memory; add them in CTA order
+  if (ticket != (unsigned)(gsize - 1)) return;
   __threadfence();
+  double *gpart = g.partial + (long long)gridDim.x * E + (long long)grp * E;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const double *src = g.partial + (long long)grp * kGroup * E + e;
+    double v[kGroup];
+#pragma unroll
+    for (int b = 0; b < kGroup; ++b) v[b] = b < gsize ? __ldcg(src + (long long)b * E) : 0.0;
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < kGroup; ++b) s += v[b];
+    gpart[e] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    g.count[1 + grp] = 0u;  // re-armed for the next call on this stream
+    ticket = atomicAdd(g.count, 1u);
+  }
+  __syncthreads();
+  if (ticket != (unsigned)(ngroups - 1)) return;
+  __threadfence();
+  const double *gbase = g.partial + (long long)gridDim.x * E;
   for (int e = threadIdx.x; e < g.p * g.q; e += blockDim.x) {
     const int i = e % g.p, j = e / g.p;
-    const double *src = g.partial + i * kGQ + j;
+    const double *src = gbase + i * kGQ + j;
+    double v[kMaxGroups];
+#pragma unroll
+    for (int b = 0; b < kMaxGroups; ++b) v[b] = b < ngroups ? __ldcg(src + (long long)b * E) : 0.0;
     double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(src + (long long)b * (P * kGQ));
+#pragma unroll
+    for (int b = 0; b < kMaxGroups; ++b) s += v[b];
     if (g.trans)
       g.G[(long long)i * g.ldg + j] = s;
     else
       g.G[(long long)j * g.ldg + i] = s;
   }
-  if (threadIdx.x == 0) *g.count = 0u;  // re-armed for the next call on this stream
+  if (threadIdx.x == 0) *g.count = 0u;
 }
 
 int sm_count_cached() {
@@ -235,6 +276,8 @@ bool gram_split_supported(int p, int q, int batch) {
   const int lo = p < q ? p : q, hi = p < q ? q : p;
   return batch == 1 && lo >= 1 && lo <= kGQ && hi <= 64;
 }
+
+bool gram_split_pays(int p, int q) { return p * q >= 32; }
 
 void launch_gram_split(const double *A, long long lda, int p, const double *B, long long ldb,
                        int q, long long nrows, double *G, int ldg, GramScratch &scr,
@@ -266,9 +309,11 @@ void launch_gram_split(const double *A, long long lda, int p, const double *B, l
   const int MT = (p + 15) / 16;
   const long long nblk = (nrows + kGRows - 1) / kGRows;
   long long grid = (nblk + kGW - 1) / kGW;
-  const long long cap = scr.capacity / (16LL * MT * kGQ);
+  // partial sums of the CTAs and of their groups fit the scratch
+  const long long cap = scr.capacity / (16LL * MT * kGQ) * kGroup / (kGroup + 1);
   grid = grid < sm_count_cached() ? grid : sm_count_cached();
   grid = grid < cap ? grid : cap;
+  grid = grid < kGroup * kMaxGroups ? grid : kGroup * kMaxGroups;
   if (grid < 1) grid = 1;
   count_launch();
   switch (MT) {

@@ -130,6 +130,8 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
 // exponents per 64-row block; for batch 1, min(p, q) <= 8 and max(p, q) <= 64
 // (gram_split_supported); need as for launch_gram.
 bool gram_split_supported(int p, int q, int batch);
+// the split is faster than the FMA pipe's Gram from p q >= 32 on (measured at 131,584 rows)
+bool gram_split_pays(int p, int q);
 void launch_gram_split(const double *A, long long lda, int p, const double *B, long long ldb,
                        int q, long long nrows, double *G, int ldg, GramScratch &scr,
                        cudaStream_t s, const int *need = nullptr);

@@ -415,58 +415,56 @@ __device__ __forceinline__ float warp_sum(float v) {
 //     no barrier.
 // The refinement needs only well-conditioned FP32-quality vectors: close eigenvalues whose
 // vectors this leaves mixed are separated by its group rotations.
-__device__ void eig32(MixedSmem &sh, int n) {
+__device__ void eig32(MixedSmem &sh, int n, int c0 = 0, int c1 = -1) {
+  if (c1 < 0) c1 = n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float(*A)[JMAX + 1] = sh.a[0];
-  // 1. tridiagonalisation
+  // 1. tridiagonalisation; each step: every warp forms the reflector of column k itself
+  // (the same data and arithmetic in each, so no barrier for it), p = b A22 v with four
+  // threads per row, then the rank-2 update; two barriers per step
   for (int k = 0; k + 2 < n; ++k) {
     const int L = n - k - 1;
-    if (warp == 0) {
-      const float x0 = A[k + 1][k];
-      float s = 0.f;
-      for (int i = 1 + lane; i < L; i += 32) s = fmaf(A[k + 1 + i][k], A[k + 1 + i][k], s);
-      s = warp_sum(s);
-      if (lane == 0) {
-        sh.td[k] = A[k][k];
-        if (s == 0.f) {
-          sh.tbeta[k] = 0.f;
-          sh.te[k] = x0;
-        } else {
-          const float r = sqrtf(fmaf(x0, x0, s));
-          const float alpha = x0 >= 0.f ? -r : r;
-          sh.tbeta[k] = 1.f / (alpha * (alpha - x0));
-          sh.te[k] = alpha;
-          A[k + 1][k] = x0 - alpha;  // v = x - alpha e_1
-        }
-      }
+    const float x0 = A[k + 1][k];
+    float s = 0.f;
+    for (int i = 1 + lane; i < L; i += 32) s = fmaf(A[k + 1 + i][k], A[k + 1 + i][k], s);
+    s = warp_sum(s);
+    float b = 0.f, alpha = x0;
+    if (s != 0.f) {
+      const float r = sqrtf(fmaf(x0, x0, s));
+      alpha = x0 >= 0.f ? -r : r;
+      b = 1.f / (alpha * (alpha - x0));
     }
-    __syncthreads();
-    const float b = sh.tbeta[k];
-    if (b == 0.f) continue;
-    if (tid < L) {  // p = b A22 v, a row per thread
-      const int i = k + 1 + tid;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int j = 0;
-      for (; j + 3 < L; j += 4) {
-        s0 = fmaf(A[i][k + 1 + j], A[k + 1 + j][k], s0);
-        s1 = fmaf(A[i][k + 2 + j], A[k + 2 + j][k], s1);
-        s2 = fmaf(A[i][k + 3 + j], A[k + 3 + j][k], s2);
-        s3 = fmaf(A[i][k + 4 + j], A[k + 4 + j][k], s3);
+    const float v0 = x0 - alpha;  // v = x - alpha e_1 (stored in A[k+1:, k] below)
+    if (tid == 0) {
+      sh.td[k] = A[k][k];
+      sh.tbeta[k] = b;
+      sh.te[k] = alpha;
+    }
+    if (b == 0.f) continue;  // every thread takes the same branch
+    {  // p = b A22 v: row tid / 4, the quad's four partial sums added by shuffles
+      const int ir = tid >> 2, q = tid & 3;
+      float acc = 0.f;
+      if (ir < L) {
+        const int i = k + 1 + ir;
+        for (int j = q; j < L; j += 4)
+          acc = fmaf(A[i][k + 1 + j], j == 0 ? v0 : A[k + 1 + j][k], acc);
       }
-      for (; j < L; ++j) s0 = fmaf(A[i][k + 1 + j], A[k + 1 + j][k], s0);
-      sh.tp[tid] = b * ((s0 + s1) + (s2 + s3));
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (ir < L && q == 0) sh.tp[ir] = b * acc;
     }
     __syncthreads();
     float kk = 0.f;  // K = b p.v / 2, w = p - K v; A22 -= v w^T + w v^T
-    for (int j = lane; j < L; j += 32) kk = fmaf(sh.tp[j], A[k + 1 + j][k], kk);
+    for (int j = lane; j < L; j += 32) kk = fmaf(sh.tp[j], j == 0 ? v0 : A[k + 1 + j][k], kk);
     kk = 0.5f * b * warp_sum(kk);
     for (int i = warp; i < L; i += JT / 32) {
-      const float vi = A[k + 1 + i][k], wi = fmaf(-kk, vi, sh.tp[i]);
+      const float vi = i == 0 ? v0 : A[k + 1 + i][k], wi = fmaf(-kk, vi, sh.tp[i]);
       for (int j = lane; j < L; j += 32) {
-        const float vj = A[k + 1 + j][k], wj = fmaf(-kk, vj, sh.tp[j]);
+        const float vj = j == 0 ? v0 : A[k + 1 + j][k], wj = fmaf(-kk, vj, sh.tp[j]);
         A[k + 1 + i][k + 1 + j] -= fmaf(vi, wj, wi * vj);
       }
     }
+    if (tid == 0) A[k + 1][k] = v0;  // every read of x0 happened before the barrier above
     __syncthreads();
   }
   if (tid == 0) {
@@ -642,19 +640,21 @@ __device__ void eig32(MixedSmem &sh, int n) {
     }
     __syncthreads();
   }
-  // 4. X = H_0 (H_1 (... H_{n-3} Z)): P threads per column (P a power of two, P n <= JT)
+  // 4. X = H_0 (H_1 (... H_{n-3} Z)) for columns c0 .. c1 - 1: P threads per column (P a
+  // power of two, P (c1 - c0) <= JT)
   {
+    const int nc = c1 - c0;
     int P = 32;
-    while (P > 1 && P * n > JT) P >>= 1;
-    const int j = tid / P, part = tid - (tid / P) * P;
+    while (P > 1 && P * nc > JT) P >>= 1;
+    const int j = c0 + tid / P, part = tid - (tid / P) * P;
     for (int k = n - 3; k >= 0; --k) {
       const float b = sh.tbeta[k];
       if (b == 0.f) continue;
       float u = 0.f;
-      if (j < n)
+      if (j < c1)
         for (int i = k + 1 + part; i < n; i += P) u = fmaf(A[i][k], sh.v[i][j], u);
       for (int o = 1; o < P; o <<= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-      if (j < n)
+      if (j < c1)
         for (int i = k + 1 + part; i < n; i += P) sh.v[i][j] = fmaf(-b * u, A[i][k], sh.v[i][j]);
     }
   }
@@ -736,13 +736,19 @@ k_rr_mixed(const double *__restrict__ G, int m, int ldg, double *theta, double *
       sh.v[i][j] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
-    eig32(sh, m);
+    // every CTA finds the same eigenvalues and segment vectors; each back-transforms its
+    // own columns (CTA r: r R .. r R + R - 1) and reads the others' from their owners
+    eig32(sh, m, min(r0, m), min(r0 + R, m));
     if (tid == 0) sh.solves32 += 1;
+    cluster.sync();
     for (int e = tid; e < m * 64; e += JT) {
       const int i = e >> 6, j = e & 63;
-      if (j < m) sh.X[i][j] = (double)sh.v[i][j];
+      if (j >= m) continue;
+      const int o = sh.owner[j];
+      sh.X[i][j] = (double)((o == rank) ? sh.v[i][j] : *peer(&sh.v[i][j], o));
     }
-    __syncthreads();
+    // no CTA overwrites its v until every peer has read it (the group rotations reuse it)
+    cluster.sync();
   }
 
   // ---- FP64 refinement; CTA r owns columns r0 .. r0 + nown - 1 of W, S, R, E and X

@@ -116,10 +116,10 @@ struct UpdArgs {
 // {row g+8, k 2c..}, {row g, k 2c+8..}, {row g+8, k 2c+8..}; B regs {k 2c..2c+1, col g},
 // {k 2c+8.., col g}; C {row g, col 2c, 2c+1}, {row g+8, ..}.  release() is called once the
 // warp has read its last value of As.
-template <int KT, typename Stride, typename Release>
+template <int KT, int NG, typename Stride, typename Release>
 __device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Stride cs,
-                                        long long row0, const uint2 (*Bd)[kUKT][32],
-                                        const unsigned *Fraw, int j0, double *Cs,
+                                        long long row0, const uint2 (*Bd)[kUS][kUKT][32],
+                                        const unsigned (*Fraw)[8], int j0, double *Cs,
                                         Release release) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, c = lane & 3;
@@ -147,11 +147,13 @@ __device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Str
   }
   ea >>= 20;
   eb >>= 20;
-  float acc[kUL][4];
+  float acc[NG][kUL][4];
 #pragma unroll
-  for (int l = 0; l < kUL; ++l)
+  for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[l][t] = 0.f;
+    for (int l = 0; l < kUL; ++l)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[gg][l][t] = 0.f;
 #pragma unroll
   for (int kt = 0; kt < KT; ++kt) {
     const bool full16 = kt < KT - 1 || 16 * kt + 8 < p;
@@ -173,42 +175,48 @@ __device__ __forceinline__ void block16(const UpdArgs &g_, const double *As, Str
       for (int i = 0; i < kUS; ++i) af[i][r] = d[i];
     }
     if (kt == KT - 1) release();
-    if (full16) {
+    // the A digit fragments serve every column group of the CTA
 #pragma unroll
-      for (int j = 0; j < kUS; ++j) {
-        const uint2 b = Bd[j][kt][lane];
+    for (int gg = 0; gg < NG; ++gg) {
+      if (full16) {
 #pragma unroll
-        for (int i = 0; i < kUS; ++i)
-          if (i + j < kUL) mma_16816(acc[i + j], af[i], b);
-      }
-    } else {
+        for (int j = 0; j < kUS; ++j) {
+          const uint2 b = Bd[gg][j][kt][lane];
 #pragma unroll
-      for (int j = 0; j < kUS; ++j) {
-        const uint32_t b = Bd[j][kt][lane].x;
+          for (int i = 0; i < kUS; ++i)
+            if (i + j < kUL) mma_16816(acc[gg][i + j], af[i], b);
+        }
+      } else {
 #pragma unroll
-        for (int i = 0; i < kUS; ++i)
-          if (i + j < kUL) mma_1688(acc[i + j], af[i][0], af[i][1], b);
+        for (int j = 0; j < kUS; ++j) {
+          const uint32_t b = Bd[gg][j][kt][lane].x;
+#pragma unroll
+          for (int i = 0; i < kUS; ++i)
+            if (i + j < kUL) mma_1688(acc[gg][i + j], af[i][0], af[i][1], b);
+        }
       }
     }
   }
   // combine the levels: value = (hi 2^32 + lo) 2^(E + F - 70), hi = levels 0..3, lo =
   // levels 4..7 (Horner in base 256)
 #pragma unroll
+  for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
   for (int t = 0; t < 4; ++t) {
     const bool v = (t & 2) ? vb : va;
     const int jl = 2 * c + (t & 1);
-    const int j = j0 + jl;
+    const int j = j0 + 8 * gg + jl;
     if (!v || j >= g_.q) continue;
     long long hi = 0, lo = 0;
 #pragma unroll
     for (int l = 0; l < kUL; ++l) {
-      const long long dl = (long long)__float2int_rn(acc[l][t]);
+      const long long dl = (long long)__float2int_rn(acc[gg][l][t]);
       if (l < kUL / 2)
         hi = hi * 256 + dl;
       else
         lo = lo * 256 + dl;
     }
-    const unsigned er = (t & 2) ? eb : ea, fr = Fraw[jl];
+    const unsigned er = (t & 2) ? eb : ea, fr = Fraw[gg][jl];
     const double val =
         (er && fr) ? combine(hi, lo, (int)er - 1022 + (int)fr - 1022) : 0.0;
     double *dst = Cs + (long long)j * g_.ldc + ((t & 2) ? rb : ra);
@@ -256,32 +264,33 @@ template <int KT>
 __global__ void __launch_bounds__(kCons)
 k_update_split(const __grid_constant__ UpdArgs g_) {
   if (g_.need && *g_.need == 0) return;  // conditional product (decided on the device)
-  __shared__ uint2 Bd[kUS][kUKT][32];
-  __shared__ unsigned Fraw[8];
+  __shared__ uint2 Bd[1][kUS][kUKT][32];
+  __shared__ unsigned Fraw[1][8];
   const int s = blockIdx.y, j0 = blockIdx.z * 8, warp = threadIdx.x >> 5;
-  y_fragments(g_, g_.Y + s * g_.bsy, j0, Bd, Fraw);
+  y_fragments(g_, g_.Y + s * g_.bsy, j0, Bd[0], Fraw[0]);
   const double *As = g_.A + s * g_.bsa;
   double *Cs = g_.C + s * g_.bsc;
   const long long nblk = (g_.nrows + 15) >> 4;
   for (long long blk = (long long)blockIdx.x * kWarps + warp; blk < nblk;
        blk += (long long)gridDim.x * kWarps)
-    block16<KT>(g_, As + blk * 16, g_.lda, blk * 16, Bd, Fraw, j0, Cs, [] {});
+    block16<KT, 1>(g_, As + blk * 16, g_.lda, blk * 16, Bd, Fraw, j0, Cs, [] {});
 }
 
 // Staged variant (kCons + 32 threads): warps 0..kWarps-1 consume kRows-row tiles of A
 // from a ring of g_.stages shared-memory stages (kColStride doubles between columns), the
 // last warp fills it with one cp.async.bulk per column.  CTA i takes tiles i, i + gridDim.x,
 // ...  The last tile, if partial, is read from global memory by the consumers.
-template <int KT>
-__global__ void __launch_bounds__(kCons + 32, TPS_UPD_MINB)
+template <int KT, int NG>
+__global__ void __launch_bounds__(kCons + 32, NG == 1 ? TPS_UPD_MINB : 1)
 k_update_split_staged(const __grid_constant__ UpdArgs g_) {
   if (g_.need && *g_.need == 0) return;
   extern __shared__ __align__(128) double ring[];
-  __shared__ uint2 Bd[kUS][kUKT][32];
-  __shared__ unsigned Fraw[8];
+  __shared__ uint2 Bd[NG][kUS][kUKT][32];
+  __shared__ unsigned Fraw[NG][8];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
   __shared__ int abort_flag;
-  const int s = blockIdx.y, j0 = blockIdx.z * 8, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y, j0 = blockIdx.z * 8 * NG, warp = threadIdx.x >> 5,
+            lane = threadIdx.x & 31;
   const int S = g_.stages, p = g_.p;
   const int stage_d = p * kColStride;  // doubles per stage
   const long long ntiles = (g_.nrows + kRows - 1) / kRows;
@@ -340,7 +349,8 @@ k_update_split_staged(const __grid_constant__ UpdArgs g_) {
     return;
   }
   // ---- consumers
-  y_fragments(g_, g_.Y + s * g_.bsy, j0, Bd, Fraw);
+#pragma unroll
+  for (int gg = 0; gg < NG; ++gg) y_fragments(g_, g_.Y + s * g_.bsy, j0 + 8 * gg, Bd[gg], Fraw[gg]);
   int it = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it % S;
@@ -357,17 +367,23 @@ k_update_split_staged(const __grid_constant__ UpdArgs g_) {
       if (lane == 0) mbar_arrive(&empty[st]);
     };
     if (tile < nfull)
-      block16<KT>(g_, ring + st * stage_d + 16 * warp, kColStride, row0, Bd, Fraw, j0, Cs,
-                  release);
+      block16<KT, NG>(g_, ring + st * stage_d + 16 * warp, kColStride, row0, Bd, Fraw, j0, Cs,
+                      release);
     else
-      block16<KT>(g_, As + row0, g_.lda, row0, Bd, Fraw, j0, Cs, release);
+      block16<KT, NG>(g_, As + row0, g_.lda, row0, Bd, Fraw, j0, Cs, release);
   }
   __syncthreads();
 }
 
 using UpdKernel = void (*)(UpdArgs);
-const UpdKernel kStagedK[kUKT] = {k_update_split_staged<1>, k_update_split_staged<2>,
-                                  k_update_split_staged<3>, k_update_split_staged<4>};
+constexpr int kMaxNG = 3;  // column groups of 8 per staged CTA (A split once for all)
+const UpdKernel kStagedK[kMaxNG][kUKT] = {
+    {k_update_split_staged<1, 1>, k_update_split_staged<2, 1>, k_update_split_staged<3, 1>,
+     k_update_split_staged<4, 1>},
+    {k_update_split_staged<1, 2>, k_update_split_staged<2, 2>, k_update_split_staged<3, 2>,
+     k_update_split_staged<4, 2>},
+    {k_update_split_staged<1, 3>, k_update_split_staged<2, 3>, k_update_split_staged<3, 3>,
+     k_update_split_staged<4, 3>}};
 const UpdKernel kDirectK[kUKT] = {k_update_split<1>, k_update_split<2>, k_update_split<3>,
                                   k_update_split<4>};
 
@@ -379,11 +395,11 @@ int stages_for(int p) {
 
 struct StagedCfg {
   int sms = 0;
-  int per_sm[65] = {0};  // resident staged CTAs per SM by p (0: not yet queried)
+  int per_sm[kMaxNG][65] = {{0}};  // resident staged CTAs per SM by groups and p (0: unknown)
 };
 
 // SM count and residency of the staged kernel on the current device (cached per device).
-const StagedCfg &staged_cfg(int p) {
+const StagedCfg &staged_cfg(int p, int ng) {
   static StagedCfg cfg[64];
   static std::mutex mu;
   int dev = 0;
@@ -395,16 +411,17 @@ const StagedCfg &staged_cfg(int p) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     c.sms = n > 0 ? n : 1;
-    for (int i = 0; i < kUKT; ++i)
-      cudaFuncSetAttribute(kStagedK[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           2 * 64 * kColStride * 8);
+    for (int g = 0; g < kMaxNG; ++g)
+      for (int i = 0; i < kUKT; ++i)
+        cudaFuncSetAttribute(kStagedK[g][i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * 64 * kColStride * 8);
   }
-  if (p >= 1 && p <= 64 && c.per_sm[p] == 0) {
+  if (p >= 1 && p <= 64 && ng >= 1 && ng <= kMaxNG && c.per_sm[ng - 1][p] == 0) {
     int b = 0;
     const size_t smem = (size_t)stages_for(p) * p * kColStride * 8;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kStagedK[(p + 15) / 16 - 1], kCons + 32,
-                                                  smem);
-    c.per_sm[p] = b > 0 ? b : 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kStagedK[ng - 1][(p + 15) / 16 - 1],
+                                                  kCons + 32, smem);
+    c.per_sm[ng - 1][p] = b > 0 ? b : 1;
   }
   return c;
 }
@@ -414,7 +431,8 @@ const StagedCfg &staged_cfg(int p) {
 // Fill the per-device launch configuration of every slab width (occupancy queries and
 // attributes), so that later launches, e.g. during stream capture, make no such calls.
 void prewarm_update_split() {
-  for (int p = 1; p <= 64; ++p) staged_cfg(p);
+  for (int g = 1; g <= kMaxNG; ++g)
+    for (int p = 1; p <= 64; ++p) staged_cfg(p, g);
 }
 
 void launch_update_split(const double *A, long long lda, long long bsa, int p, const double *Y,
@@ -450,15 +468,21 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
     const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (lda & 1) == 0 &&
                          (batch == 1 || (bsa & 1) == 0);
     const long long ntiles = (nrows + kRows - 1) / kRows;
-    const StagedCfg &cfg = staged_cfg(g.p);
+    // up to kMaxNG column groups of 8 per CTA: A's digits are formed once for all of them
+    // (at one CTA per SM instead of two; measured at 131,584 rows, p = 40: q = 16 in 46 us,
+    // q = 24 in 62 us, against ~54 and ~70 us with a CTA per group; wider q takes groups of
+    // one, the three-group kernel's spills making q = 32 no faster)
+    const int ng = q <= 8 * kMaxNG ? (q + 7) / 8 : 1;
+    const StagedCfg &cfg = staged_cfg(g.p, ng);
     count_launch();
     if (aligned && nrows >= kRows) {
       g.stages = stages_for(g.p);
-      const long long want = (long long)cfg.sms * cfg.per_sm[g.p];
+      const long long want = (long long)cfg.sms * cfg.per_sm[ng - 1][g.p];
       const long long gx = ntiles < want ? ntiles : want;
       const size_t smem = (size_t)g.stages * g.p * kColStride * 8;
       g_staged_launches.fetch_add(1, std::memory_order_relaxed);
-      kStagedK[kt]<<<dim3((unsigned)gx, batch, (q + 7) / 8), kCons + 32, smem, s>>>(g);
+      kStagedK[ng - 1][kt]<<<dim3((unsigned)gx, batch, (q + 8 * ng - 1) / (8 * ng)), kCons + 32,
+                             smem, s>>>(g);
     } else {
       g.stages = 0;
       const long long blocks = (nrows + kRows - 1) / kRows;

@@ -126,7 +126,11 @@ def test_gram_tc_rejects_wide_blocks(ctx):
                                             (131584, 32, 5, -1.0), (20003, 9, 9, 0.5),
                                             # staged split path: partial last tile, p in
                                             # two slabs, two column groups
-                                            (131590, 36, 8, 1.0), (200002, 100, 12, -1.0)])
+                                            (131590, 36, 8, 1.0), (200002, 100, 12, -1.0),
+                                            # two and three column groups per CTA, four
+                                            # (two CTA groups), ragged q
+                                            (131584, 40, 24, 0.0), (131590, 33, 16, 1.0),
+                                            (150000, 64, 20, -1.0), (140000, 17, 32, 0.5)])
 @pytest.mark.parametrize("dtype", ["f64", "f64_tc"])
 def test_block_update(ctx, nrows, p, q, beta, dtype):
     from paper_2111_02534_gb300 import tps

@@ -86,9 +86,20 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
 }
 
+// Programmatic dependent launch: a pass is launched while the previous one still runs;
+// griddepcontrol.wait holds a thread until the previous grid has completed and its writes
+// are visible, and launch_dependents lets the next pass's CTAs be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One CTA computes the 128 x BN tile (m0, n0) of C = A B^T.  Warp 0 lane 0 loads (TMA),
 // warp 1 lane 0 issues the MMAs, warp 2 owns the tensor memory, all four warps run the
 // epilogue (warp w reads TMEM lanes 32 w .. 32 w + 31, one accumulator row per thread).
+// Launched as a dependent of the previous pass: the set-up and the loads of the B operand
+// (the constant eigenbases) run before pdl_wait, the A operand (the previous pass's
+// output) is loaded and the output written after it.
 __global__ void __launch_bounds__(kThreads, 1)
 k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const TfArgs g) {
@@ -109,6 +120,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int KB = (g.K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
+    pdl_trigger();
     for (int i = 0; i < kStages; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
@@ -126,11 +138,19 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const uint32_t tmem = *holder;
 
   if (warp == 0 && lane == 0) {
-    // ---- producer
+    // ---- producer: the first stages' B tiles before the wait for the previous pass
     int last[kStages];
     for (int i = 0; i < kStages; ++i) last[i] = -1;
+    const int pre = KB < kStages ? KB : kStages;
+    for (int kb = 0; kb < pre; ++kb) {
+      tc::mbar_arrive_expect_tx(&full[kb], kATile + btile);
+      tma_load_2d(sB + kb * kBTileMax, &tmB, &full[kb], kb * kBK, n0);
+      last[kb] = 0;
+    }
+    pdl_wait();
+    for (int kb = 0; kb < pre; ++kb) tma_load_2d(sA + kb * kATile, &tmA, &full[kb], kb * kBK, m0);
     bool ok = true;
-    for (int kb = 0; kb < KB; ++kb) {
+    for (int kb = pre; kb < KB; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages);
       if (!tc::mbar_wait(&empty[s], (ph & 1u) ^ 1u, g.err, 11)) {
@@ -174,7 +194,8 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   __syncwarp();
 
-  // ---- epilogue
+  // ---- epilogue (its stores follow the previous pass's completion: pdl_wait)
+  pdl_wait();
   bool ok = tc::mbar_wait(accum, 0, g.err, 13);
   ok = __all_sync(0xffffffffu, ok);
   const int aborted = __shfl_sync(0xffffffffu, *((volatile int *)&abort_flag), 0);
@@ -237,6 +258,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // b, b + grid, ...; a thread converts 2 consecutive values of a row per step.
 __global__ void k_to_f32_rows(const double *__restrict__ x, float *__restrict__ y, long long rows,
                               int cols, int ld) {
+  if (threadIdx.x == 0) pdl_trigger();  // pass 1 may be scheduled (it waits for this grid)
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const double *xr = x + r * cols;
     float *yr = y + r * ld;
@@ -318,9 +340,18 @@ void launch_tf32_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const TfArgs
   std::call_once(g_attr_once, [] {
     cudaFuncSetAttribute(k_tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   });
-  dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + g.BN - 1) / g.BN));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + g.BN - 1) / g.BN));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   count_launch();
-  k_tf32_gemm<<<grid, kThreads, kSmemBytes, s>>>(ta, tb, g);
+  cudaLaunchKernelEx(&cfg, k_tf32_gemm, ta, tb, g);
 }
 
 }  // namespace

@@ -43,6 +43,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <utility>
 
 #include "ozaki_tc.cuh"
 #include "split_digits.cuh"
@@ -51,6 +52,31 @@
 namespace tps {
 
 namespace {
+
+// Programmatic dependent launch (the H-apply's split and product kernels): a dependent
+// kernel is launched while its predecessor still runs and holds every access to data the
+// predecessor writes behind griddepcontrol.wait; launch_dependents at entry lets the next
+// kernel be scheduled early.  Both are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int kBeta = 6;
 constexpr int kPsiSlices = 9;  // wave-function digits: 54 bits
@@ -116,6 +142,7 @@ __device__ __forceinline__ long long scaled_integer(double x, unsigned raw_max, 
 // arrays must be zeroed before.  Block 32 x 8 over a 32 x 32 tile.
 __global__ void k_exponents(const double *__restrict__ X, int R, int C, long long bs,
                             unsigned *__restrict__ rexp, unsigned *__restrict__ cexp) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) pdl_trigger();
   const int b = blockIdx.z;
   const int c = blockIdx.x * 32 + threadIdx.x;
   const int r0 = blockIdx.y * 32;
@@ -155,8 +182,11 @@ __global__ void k_exponents(const double *__restrict__ X, int R, int C, long lon
 // Slice i = 0 holds the most significant digit.
 __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs, int S,
                         const unsigned *__restrict__ rexp, uint16_t *__restrict__ outN, int ldn,
-                        const unsigned *__restrict__ cexp, uint16_t *__restrict__ outT, int ldt) {
+                        const unsigned *__restrict__ cexp, uint16_t *__restrict__ outT, int ldt,
+                        double *__restrict__ zero_out) {
   __shared__ double tile[32][33];
+  if (threadIdx.x == 0 && threadIdx.y == 0) pdl_trigger();
+  pdl_wait();  // X's exponents come from the previous kernel
   const int b = blockIdx.z;
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const double *Xb = X + b * bs;
@@ -165,7 +195,11 @@ __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs
   for (int j = 0; j < 4; ++j) {
     const int r = r0 + threadIdx.y + 8 * j, c = c0 + threadIdx.x;
     double x = 0.0;
-    if (r < R && c < C) x = Xb[(long long)r * C + c];
+    if (r < R && c < C) {
+      x = Xb[(long long)r * C + c];
+      // the product kernel that follows accumulates into a zeroed output of X's shape
+      if (zero_out) zero_out[b * bs + (long long)r * C + c] = 0.0;
+    }
     tile[threadIdx.y + 8 * j][threadIdx.x] = x;
     if (outN && r < R && c < C) {
       long long q = scaled_integer(x, rexp[(long long)b * R + r], S);
@@ -316,6 +350,7 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
   const int KB = (g.K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
+    pdl_trigger();
     for (int i = 0; i < kAStages; ++i) {
       tc::mbar_init(&fullA[i], 1);
       tc::mbar_init(&emptyA[i], 1);
@@ -335,6 +370,8 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *holder;
+  // the set-up above overlaps the previous kernel; every global access below follows it
+  pdl_wait();
 
   if (warp == 0 && lane == 0) {
     // ---- producer: per K block, all B slices (one stage), then the A slices one by one
@@ -601,10 +638,15 @@ void launch_exponents(const double *X, int R, int C, long long bs, int batch, un
 
 void launch_split(const double *X, int R, int C, long long bs, int batch, int S,
                   const unsigned *rexp, uint16_t *outN, int ldn, const unsigned *cexp,
-                  uint16_t *outT, int ldt, cudaStream_t s) {
+                  uint16_t *outT, int ldt, cudaStream_t s, double *zero_out = nullptr,
+                  bool dependent = false) {
   count_launch();
-  k_split<<<split_grid(R, C, batch), dim3(32, 8), 0, s>>>(X, R, C, bs, S, rexp, outN, ldn, cexp,
-                                                          outT, ldt);
+  if (dependent)
+    launch_dependent(k_split, split_grid(R, C, batch), dim3(32, 8), 0, s, X, R, C, bs, S, rexp,
+                     outN, ldn, cexp, outT, ldt, zero_out);
+  else
+    k_split<<<split_grid(R, C, batch), dim3(32, 8), 0, s>>>(X, R, C, bs, S, rexp, outN, ldn,
+                                                            cexp, outT, ldt, zero_out);
 }
 
 // The two products of the H-apply (pass 1: A = K_y slices, B = psi slices; pass 2: A =
@@ -626,9 +668,9 @@ cudaError_t launch_oz_pair(const CUtensorMap &mA1, const CUtensorMap &mB1, const
   const long long tiles = (long long)((g1.M + kBM - 1) / kBM) * ((g1.N + kBN - 1) / kBN) * nvec;
   if (2 * tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
   count_launch();
-  k_oz_gemm<<<(unsigned)(2 * tiles), kThreads, oz_smem_bytes(kMaxSlices), s>>>(mA1, mB1, g1, mA2,
-                                                                             mB2, g2);
-  return cudaGetLastError();
+  const cudaError_t le = launch_dependent(k_oz_gemm, dim3((unsigned)(2 * tiles)), dim3(kThreads),
+                                          oz_smem_bytes(kMaxSlices), s, mA1, mB1, g1, mA2, mB2, g2);
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 }  // namespace
@@ -873,9 +915,9 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
     e = cudaMemsetAsync(t.eP, 0, sizeof(unsigned) * t.chunk * (nx + ny), s);
     if (e != cudaSuccess) return e;
     launch_exponents(P, nx, ny, op.N, nv, erow, ecol, s);
-    launch_split(P, nx, ny, op.N, nv, Sp, erow, t.Pn, t.ldy, ecol, t.PT, t.ldx, s);
-    e = cudaMemsetAsync(O, 0, sizeof(double) * (size_t)nv * op.N, s);
-    if (e != cudaSuccess) return e;
+    // the split also zeroes the output, which the product kernel accumulates into; split and
+    // product are launched as programmatic dependents of their predecessors
+    launch_split(P, nx, ny, op.N, nv, Sp, erow, t.Pn, t.ldy, ecol, t.PT, t.ldx, s, O, true);
     OzArgs g;
     std::memset(&g, 0, sizeof(g));
     g.L = kLevels;

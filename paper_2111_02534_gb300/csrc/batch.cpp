@@ -15,6 +15,7 @@
 #include <thread>
 #include <vector>
 
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 extern "C" int tps_solve_batch(tps_ctx **ctxs, int ninst, const int *k, int parity, double tol,
@@ -32,7 +33,9 @@ extern "C" int tps_solve_batch(tps_ctx **ctxs, int ninst, const int *k, int pari
     if (ctxs[i]->device != device) return TPS_ERR_INVALID_ARG;
   std::atomic<int> next{0};
   std::atomic<int> cuda_failure{0};
+  const int nt = std::min(nstreams, ninst);
   auto worker = [&]() {
+    tps::pdl_enabled = nt == 1;  // dependent launches only without concurrent streams
     if (cudaSetDevice(device) != cudaSuccess) {
       cuda_failure = 1;
       return;
@@ -54,7 +57,6 @@ extern "C" int tps_solve_batch(tps_ctx **ctxs, int ninst, const int *k, int pari
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   };
-  const int nt = std::min(nstreams, ninst);
   std::vector<std::thread> threads;
   threads.reserve(nt);
   for (int t = 0; t < nt; ++t) threads.emplace_back(worker);

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <utility>
 
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -72,6 +73,7 @@ k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
        const double *__restrict__ B, long long ldb, long long bsb, int q, long long nrows,
        int nchunk, double *__restrict__ partial, unsigned *__restrict__ count,
        double *__restrict__ G, int ldg, long long bsg, int trans, const int *__restrict__ need) {
+  pdl_entry();
   constexpr int V = BP * BQ;
   if (need && *need == 0) return;  // conditional product (decided on the device)
   const int c = blockIdx.x, s = blockIdx.y, pb = blockIdx.z;
@@ -158,6 +160,7 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
          const double *__restrict__ Y, int ldy, long long bsy, int q, double alpha, double beta,
          double *__restrict__ C, long long ldc, long long bsc, long long nrows,
          const int *__restrict__ need) {
+  pdl_entry();
   if (need && *need == 0) return;  // conditional product (decided on the device)
   const int s = blockIdx.y;
   const int j0 = blockIdx.z * BQ;
@@ -208,6 +211,7 @@ __device__ __forceinline__ double rsqrt64(double d) {
 // column per lane.  Pivots use rsqrt64 and every division is a multiplication by it.
 __global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__restrict__ ref,
                            double tol_rel, double *__restrict__ Rinv, int *__restrict__ keep) {
+  pdl_entry();
   __shared__ double R[32][33];
   __shared__ double inv[32];
   __shared__ int kp[32];
@@ -271,6 +275,7 @@ __global__ void k_chol_inv(const double *__restrict__ G, int b, const double *__
 // Minv = M^-1 by Cholesky M = L L^T in place in Minv (lower), then L^-1, then L^-T L^-1;
 // reciprocal pivots by rsqrt64, no FP64 division.
 __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__restrict__ W) {
+  pdl_entry();
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ double sm[];
   double *Lm = sm;           // q x q, column-major
@@ -323,6 +328,7 @@ __global__ void k_spd_inverse(const double *__restrict__ M, int q, double *__res
 // x_i = -L_x + i 2L_x/n_x; also the FP32 copy.
 __global__ void k_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,
                                     double sigma, double *__restrict__ V, float *__restrict__ Vf) {
+  pdl_entry();
   const long long total = (long long)nx * ny;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -346,6 +352,7 @@ __global__ void k_pair_potential_1d(int nx, int ny, double Lx, double Ly, int sh
 
 __global__ void k_axpby_cols(int ncols, long long nrows, double alpha, const double *X,
                              long long ldx, double beta, double *Y, long long ldy) {
+  pdl_entry();
   const long long total = (long long)ncols * nrows;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -358,6 +365,7 @@ __global__ void k_axpby_cols(int ncols, long long nrows, double alpha, const dou
 
 __global__ void k_scale_cols(int ncols, long long nrows, const double *X, long long ldx,
                              const double *scale, int invert, double *Y, long long ldy) {
+  pdl_entry();
   const long long total = (long long)ncols * nrows;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -370,6 +378,7 @@ __global__ void k_scale_cols(int ncols, long long nrows, const double *X, long l
 
 __global__ void k_residual(int ncols, long long nrows, const double *HX, const double *X,
                            const double *theta, double *R) {
+  pdl_entry();
   const long long total = (long long)ncols * nrows;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -383,6 +392,7 @@ __global__ void k_residual(int ncols, long long nrows, const double *HX, const d
 //  odd:  u_i = sqrt(2) * (P_i - P_{n-i}) / 2,   i = 1..n/2-1
 __global__ void k_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
                                   double *red) {
+  pdl_entry();
   const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
   const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
   const long long total = (long long)ncols * Nr;
@@ -408,6 +418,7 @@ __global__ void k_sector_restrict(int parity, int nx, int ny, int ncols, const d
 
 __global__ void k_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
                                 double *full) {
+  pdl_entry();
   const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
   const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
   const long long total = (long long)ncols * Nf;
@@ -444,6 +455,7 @@ __global__ void k_sector_expand(int parity, int nx, int ny, int ncols, const dou
 // signs travel with the partials, so no block reads an entry another may be negating).
 __global__ void k_sign_partial(long long nrows, const double *__restrict__ X, int nchunk,
                                unsigned long long *__restrict__ part) {
+  pdl_entry();
   const int c = blockIdx.x, j = blockIdx.y;
   const double *x = X + (long long)j * nrows;
   const long long per = (nrows + nchunk - 1) / nchunk;
@@ -488,6 +500,7 @@ __global__ void k_sign_partial(long long nrows, const double *__restrict__ X, in
 
 __global__ void k_sign_apply(long long nrows, double *__restrict__ X, int nchunk,
                              const unsigned long long *__restrict__ part) {
+  pdl_entry();
   const int j = blockIdx.y;
   __shared__ int neg;
   if (threadIdx.x == 0) {
@@ -556,10 +569,12 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
   dim3 grid(nchunk, batch, npb);
   count_launch();
 #define TPS_GRAM(bp, bq)                                                                      \
-  (low ? k_gram<float, bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk,  \
+  (low ? launch_pdl(k_gram<float, bp, bq>, grid, GT, 0, s, A, lda, bsa, p, B, ldb, bsb, q, nrows,  \
+                    nchunk,                                                                        \
                                                    scr.partial, scr.count, G, ldg, bsg, trans,     \
                                                    need)                                           \
-       : k_gram<double, bp, bq><<<grid, GT, 0, s>>>(A, lda, bsa, p, B, ldb, bsb, q, nrows, nchunk, \
+       : launch_pdl(k_gram<double, bp, bq>, grid, GT, 0, s, A, lda, bsa, p, B, ldb, bsb, q, nrows, \
+                    nchunk,                                                                        \
                                                     scr.partial, scr.count, G, ldg, bsg, trans,    \
                                                     need))
   if (BQ == 4)
@@ -581,7 +596,8 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
   if (p <= 0) {  // C = beta * C
     for (int b = 0; b < batch; ++b) {
       count_launch();
-      k_axpby_cols<<<grid_for((long long)q * nrows), 256, 0, s>>>(q, nrows, 0.0, C + b * bsc, ldc,
+      launch_pdl(k_axpby_cols, grid_for((long long)q * nrows), 256, 0, s, q, nrows, 0.0,
+                 C + b * bsc, ldc,
                                                                 beta, C + b * bsc, ldc);
     }
     return;
@@ -595,7 +611,8 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     const double *Ai = A + (long long)i0 * lda;
     count_launch();
 #define TPS_UPD(T, bq)                                                                       \
-  k_update<T, bq><<<grid, GT, 0, s>>>(Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, ldc, \
+  launch_pdl(k_update<T, bq>, grid, GT, 0, s, Ai, lda, bsa, pp, Y + i0, ldy, bsy, q, alpha, bt, C, \
+             ldc,                                                                                  \
                                       bsc, nrows, need)
     if (low)
       BQ == 8 ? TPS_UPD(float, 8) : (BQ == 4 ? TPS_UPD(float, 4) : (BQ == 2 ? TPS_UPD(float, 2) : TPS_UPD(float, 1)));
@@ -611,6 +628,7 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
 __global__ void __launch_bounds__(GT)
 k_col_norms2(const double *__restrict__ A, long long lda, long long nrows, int nchunk,
              double *__restrict__ partial, unsigned *__restrict__ count, double *__restrict__ out) {
+  pdl_entry();
   const int chunk = blockIdx.x, c = blockIdx.y;
   const long long rows_per = (nrows + nchunk - 1) / nchunk;
   const long long r0 = (long long)chunk * rows_per;
@@ -648,6 +666,7 @@ k_col_norms2(const double *__restrict__ A, long long lda, long long nrows, int n
 
 __global__ void k_dgks_flag(const double *__restrict__ before, const double *__restrict__ after,
                             int ncols, int *__restrict__ need, int *__restrict__ stat) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   int n = 0;
   for (int j = 0; j < ncols; ++j) n |= after[j] < 0.5 * before[j];
@@ -667,27 +686,28 @@ void launch_col_norms2(const double *A, long long lda, int ncols, long long nrow
   if (nchunk > scr.capacity / ncols) nchunk = scr.capacity / ncols;
   if (nchunk < 1) nchunk = 1;
   count_launch();
-  k_col_norms2<<<dim3((unsigned)nchunk, ncols), GT, 0, s>>>(A, lda, nrows, (int)nchunk,
+  launch_pdl(k_col_norms2, dim3((unsigned)nchunk, ncols), GT, 0, s, A, lda, nrows, (int)nchunk,
                                                            scr.partial, scr.count, out);
 }
 
 void launch_dgks_flag(const double *before, const double *after, int ncols, int *need,
                       int *stat, cudaStream_t s) {
   count_launch();
-  k_dgks_flag<<<1, 32, 0, s>>>(before, after, ncols, need, stat);
+  launch_pdl(k_dgks_flag, 1, 32, 0, s, before, after, ncols, need, stat);
 }
 
 void launch_pair_potential_1d(int nx, int ny, double Lx, double Ly, int shape, double v0,
                               double sigma, double *V, float *Vf, cudaStream_t s) {
   count_launch();
-  k_pair_potential_1d<<<grid_for((long long)nx * ny), 256, 0, s>>>(nx, ny, Lx, Ly, shape, v0,
+  launch_pdl(k_pair_potential_1d, grid_for((long long)nx * ny), 256, 0, s, nx, ny, Lx, Ly, shape,
+             v0,
                                                                    sigma, V, Vf);
 }
 
 void launch_chol_inv(const double *G, int b, const double *ref, double tol_rel, double *Rinv,
                      int *keep, cudaStream_t s) {
   count_launch();
-  k_chol_inv<<<1, 32, 0, s>>>(G, b, ref, tol_rel, Rinv, keep);
+  launch_pdl(k_chol_inv, 1, 32, 0, s, G, b, ref, tol_rel, Rinv, keep);
 }
 
 void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s) {
@@ -699,14 +719,15 @@ void launch_spd_inverse(const double *M, int q, double *Minv, cudaStream_t s) {
     attr = true;
   }
   count_launch();
-  k_spd_inverse<<<1, 128, smem, s>>>(M, q, Minv);
+  launch_pdl(k_spd_inverse, 1, 128, smem, s, M, q, Minv);
 }
 
 void launch_axpby_cols(int ncols, long long nrows, double alpha, const double *X, long long ldx,
                        double beta, double *Y, long long ldy, cudaStream_t s) {
   if (ncols <= 0 || nrows <= 0) return;
   count_launch();
-  k_axpby_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, alpha, X, ldx,
+  launch_pdl(k_axpby_cols, grid_for((long long)ncols * nrows), 256, 0, s, ncols, nrows, alpha, X,
+             ldx,
                                                                    beta, Y, ldy);
 }
 
@@ -714,7 +735,8 @@ void launch_scale_cols(int ncols, long long nrows, const double *X, long long ld
                        const double *scale, int invert, double *Y, long long ldy, cudaStream_t s) {
   if (ncols <= 0 || nrows <= 0) return;
   count_launch();
-  k_scale_cols<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, X, ldx, scale,
+  launch_pdl(k_scale_cols, grid_for((long long)ncols * nrows), 256, 0, s, ncols, nrows, X, ldx,
+             scale,
                                                                    invert, Y, ldy);
 }
 
@@ -722,27 +744,31 @@ void launch_residual(int ncols, long long nrows, const double *HX, const double 
                      const double *theta, double *R, cudaStream_t s) {
   if (ncols <= 0) return;
   count_launch();
-  k_residual<<<grid_for((long long)ncols * nrows), 256, 0, s>>>(ncols, nrows, HX, X, theta, R);
+  launch_pdl(k_residual, grid_for((long long)ncols * nrows), 256, 0, s, ncols, nrows, HX, X, theta,
+             R);
 }
 
 void launch_sector_restrict(int parity, int nx, int ny, int ncols, const double *full,
                             double *red, cudaStream_t s) {
   const int nr = parity == TPS_X_EVEN ? nx / 2 + 1 : nx / 2 - 1;
   count_launch();
-  k_sector_restrict<<<grid_for((long long)ncols * nr * ny), 256, 0, s>>>(parity, nx, ny, ncols,
+  launch_pdl(k_sector_restrict, grid_for((long long)ncols * nr * ny), 256, 0, s, parity, nx, ny,
+             ncols,
                                                                          full, red);
 }
 
 void launch_sector_expand(int parity, int nx, int ny, int ncols, const double *red,
                           double *full, cudaStream_t s) {
   count_launch();
-  k_sector_expand<<<grid_for((long long)ncols * nx * ny), 256, 0, s>>>(parity, nx, ny, ncols, red,
+  launch_pdl(k_sector_expand, grid_for((long long)ncols * nx * ny), 256, 0, s, parity, nx, ny,
+             ncols, red,
                                                                        full);
 }
 
 namespace {
 __global__ void k_mirror_restrict(int sg, int nx, int ny, int ncols, const double *full,
                                   double *red) {
+  pdl_entry();
   const int nr = nx / 2;
   const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
   const long long total = (long long)ncols * Nr;
@@ -757,6 +783,7 @@ __global__ void k_mirror_restrict(int sg, int nx, int ny, int ncols, const doubl
 }
 __global__ void k_mirror_expand(int sg, int nx, int ny, int ncols, const double *red,
                                 double *full) {
+  pdl_entry();
   const int nr = nx / 2;
   const long long Nf = (long long)nx * ny, Nr = (long long)nr * ny;
   const long long total = (long long)ncols * Nf;
@@ -774,14 +801,14 @@ __global__ void k_mirror_expand(int sg, int nx, int ny, int ncols, const double 
 void launch_mirror_restrict(int parity, int nx, int ny, int ncols, const double *full,
                             double *red, cudaStream_t s) {
   count_launch();
-  k_mirror_restrict<<<grid_for((long long)ncols * (nx / 2) * ny), 256, 0, s>>>(
+  launch_pdl(k_mirror_restrict, grid_for((long long)ncols * (nx / 2) * ny), 256, 0, s,
       parity == TPS_X_EVEN ? 1 : -1, nx, ny, ncols, full, red);
 }
 
 void launch_mirror_expand(int parity, int nx, int ny, int ncols, const double *red,
                           double *full, cudaStream_t s) {
   count_launch();
-  k_mirror_expand<<<grid_for((long long)ncols * nx * ny), 256, 0, s>>>(
+  launch_pdl(k_mirror_expand, grid_for((long long)ncols * nx * ny), 256, 0, s,
       parity == TPS_X_EVEN ? 1 : -1, nx, ny, ncols, red, full);
 }
 
@@ -794,11 +821,11 @@ void launch_fix_sign(int ncols, long long nrows, double *X, GramScratch &scr, cu
   if (nchunk < 1) nchunk = 1;
   unsigned long long *part = reinterpret_cast<unsigned long long *>(scr.partial);
   count_launch();
-  k_sign_partial<<<dim3((unsigned)nchunk, ncols), 256, 0, s>>>(nrows, X, (int)nchunk, part);
+  launch_pdl(k_sign_partial, dim3((unsigned)nchunk, ncols), 256, 0, s, nrows, X, (int)nchunk, part);
   long long blocks = (nrows + 255) / 256;
   if (blocks > 152LL * 4 / ncols + 1) blocks = 152LL * 4 / ncols + 1;
   count_launch();
-  k_sign_apply<<<dim3((unsigned)blocks, ncols), 256, 0, s>>>(nrows, X, (int)nchunk, part);
+  launch_pdl(k_sign_apply, dim3((unsigned)blocks, ncols), 256, 0, s, nrows, X, (int)nchunk, part);
 }
 
 }  // namespace tps

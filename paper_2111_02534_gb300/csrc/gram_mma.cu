@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "split_digits.cuh"
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -101,6 +102,7 @@ __device__ __forceinline__ unsigned col_raw_max(const double (&v)[4][4]) {
 
 template <int MT>
 __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
+  pdl_entry();
   constexpr int P = 16 * MT;  // padded A columns
   __shared__ double red[kGW][P * kGQ];
   __shared__ unsigned ticket;
@@ -317,10 +319,10 @@ void launch_gram_split(const double *A, long long lda, int p, const double *B, l
   if (grid < 1) grid = 1;
   count_launch();
   switch (MT) {
-    case 1: k_gram_split<1><<<(unsigned)grid, 32 * kGW, 0, s>>>(g); break;
-    case 2: k_gram_split<2><<<(unsigned)grid, 32 * kGW, 0, s>>>(g); break;
-    case 3: k_gram_split<3><<<(unsigned)grid, 32 * kGW, 0, s>>>(g); break;
-    default: k_gram_split<4><<<(unsigned)grid, 32 * kGW, 0, s>>>(g); break;
+    case 1: launch_pdl(k_gram_split<1>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    case 2: launch_pdl(k_gram_split<2>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    case 3: launch_pdl(k_gram_split<3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    default: launch_pdl(k_gram_split<4>, (unsigned)grid, 32 * kGW, 0, s, g); break;
   }
 }
 

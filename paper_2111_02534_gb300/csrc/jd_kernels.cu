@@ -3,6 +3,7 @@
 // small triangular solve, projected-basis matrix updates.  One thread per system or
 // per matrix entry; all sizes are tiny (<= 64).
 #include "jd_kernels.h"
+#include "pdl.cuh"
 
 namespace tps {
 namespace {
@@ -13,6 +14,7 @@ namespace {
 
 __global__ void k_gmres_init(int nsys, int s, const double *nrm2, double *beta, double *g,
                              double *Hb, int *done, int *mvalid, double *scale) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   const double b = sqrt(nrm2[i] > 0.0 ? nrm2[i] : 0.0);
@@ -28,6 +30,7 @@ __global__ void k_gmres_init(int nsys, int s, const double *nrm2, double *beta, 
 
 __global__ void k_hess_add(int nsys, int s, int j, const double *h, int ldh, double *Hb,
                            const int *done) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = e / (j + 1), l = e % (j + 1);
   if (i >= nsys) return;
@@ -38,6 +41,7 @@ __global__ void k_hess_add(int nsys, int s, int j, const double *h, int ldh, dou
 __global__ void k_gmres_givens(int nsys, int s, int j, const double *nrm2, double *Hb,
                                double *cs, double *sn, double *g, const double *beta, int *done,
                                int *mvalid, double *scale, double tol) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   if (done[i]) {
@@ -79,6 +83,7 @@ __global__ void k_gmres_givens(int nsys, int s, int j, const double *nrm2, doubl
 
 __global__ void k_gmres_solve(int nsys, int s, const double *Hb, const double *g,
                               const int *mvalid, double *y) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   const double *H = Hb + (long long)i * (s + 1) * s;
@@ -96,6 +101,7 @@ __global__ void k_gmres_solve(int nsys, int s, const double *Hb, const double *g
 
 // G[m0+a, m0+b] block symmetrised and mirrored: G[m0+b][c] = G[c][m0+b] for c < m0.
 __global__ void k_mirror_block(double *G, int ldg, int m0, int bn) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int tot = (m0 + bn) * bn;
   if (e >= tot) return;
@@ -112,6 +118,7 @@ __global__ void k_mirror_block(double *G, int ldg, int m0, int bn) {
 }
 
 __global__ void k_set_diag(double *G, int ldg, const double *d, int m) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * m) return;
   const int i = e % m, j = e / m;
@@ -120,6 +127,7 @@ __global__ void k_set_diag(double *G, int ldg, const double *d, int m) {
 
 // dst[0:mk, 0:mk] = src[off:off+mk, off:off+mk] (column-major, leading dimensions lds, ldd)
 __global__ void k_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= mk * mk) return;
   const int i = e % mk, j = e / mk;
@@ -127,11 +135,13 @@ __global__ void k_copy_block(const double *src, int lds, int off, double *dst, i
 }
 
 __global__ void k_copy_small(const double *src, double *dst, int n) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = src[e];
 }
 
 __global__ void k_sqrt_div(const double *nrm2, double *out, int n, double div) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) out[e] = sqrt(nrm2[e] > 0.0 ? nrm2[e] : 0.0) / div;
 }
@@ -139,6 +149,7 @@ __global__ void k_sqrt_div(const double *nrm2, double *out, int n, double div) {
 // C (m x n) = alpha * A (m x k) * B (k x n) + beta * C, column-major, tiny sizes
 __global__ void k_small_gemm(int m, int n, int k, double alpha, const double *A, int lda,
                              const double *B, int ldb, double beta, double *C, int ldc) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * n) return;
   const int i = e % m, j = e / m;
@@ -154,28 +165,32 @@ inline unsigned nb(long long n, int t = 128) { return (unsigned)((n + t - 1) / t
 
 void launch_gmres_init(int nsys, int s, const double *nrm2, GmresState &st, cudaStream_t str) {
   count_launch();
-  k_gmres_init<<<nb(nsys), 128, 0, str>>>(nsys, s, nrm2, st.beta, st.g, st.Hb, st.done, st.mvalid,
+  launch_pdl(k_gmres_init, nb(nsys), 128, 0, str, nsys, s, nrm2, st.beta, st.g, st.Hb, st.done,
+             st.mvalid,
                                            st.scale);
 }
 void launch_hess_add(int nsys, int s, int j, const double *h, int ldh, GmresState &st,
                      cudaStream_t str) {
   count_launch();
-  k_hess_add<<<nb((long long)nsys * (j + 1)), 128, 0, str>>>(nsys, s, j, h, ldh, st.Hb, st.done);
+  launch_pdl(k_hess_add, nb((long long)nsys * (j + 1)), 128, 0, str, nsys, s, j, h, ldh, st.Hb,
+             st.done);
 }
 void launch_gmres_givens(int nsys, int s, int j, const double *nrm2, GmresState &st, double tol,
                          cudaStream_t str) {
   count_launch();
-  k_gmres_givens<<<nb(nsys), 128, 0, str>>>(nsys, s, j, nrm2, st.Hb, st.cs, st.sn, st.g, st.beta,
+  launch_pdl(k_gmres_givens, nb(nsys), 128, 0, str, nsys, s, j, nrm2, st.Hb, st.cs, st.sn, st.g,
+             st.beta,
                                              st.done, st.mvalid, st.scale, tol);
 }
 void launch_gmres_solve(int nsys, int s, GmresState &st, cudaStream_t str) {
   count_launch();
-  k_gmres_solve<<<nb(nsys), 128, 0, str>>>(nsys, s, st.Hb, st.g, st.mvalid, st.y);
+  launch_pdl(k_gmres_solve, nb(nsys), 128, 0, str, nsys, s, st.Hb, st.g, st.mvalid, st.y);
 }
 // A column of the new block that the Cholesky-QR dropped (keep0 == 0) is zero, so its row
 // and column of G are zero: its diagonal entry is raised to twice the largest |G_ii| of the
 // first m0 + bn, which puts that spurious Ritz value above the wanted ones.
 __global__ void k_mark_dropped(double *G, int ldg, int m0, int bn, const int *keep0) {
+  pdl_entry();
   __shared__ double mx;
   if (threadIdx.x == 0) {
     double a = 0.0;
@@ -192,6 +207,7 @@ __global__ void k_mark_dropped(double *G, int ldg, int m0, int bn, const int *ke
 // under the iteration cap.  state[0] = converged, state[1] = iterations.
 __global__ void k_conv_check(const double *nrm2, int k, double thresh2, int *state, int max_iter,
                              cudaGraphConditionalHandle loop, int set_loop) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   int conv = 1;
   for (int i = 0; i < k; ++i) conv = conv && nrm2[i] <= thresh2;
@@ -204,6 +220,7 @@ __global__ void k_conv_check(const double *nrm2, int k, double thresh2, int *sta
 // corrections are zero (and dropped by the orthonormalisation) instead of noise directions.
 __global__ void k_zero_converged(double *R, long long nrows, const double *nrm2, int k,
                                  double thresh2) {
+  pdl_entry();
   const long long total = (long long)k * nrows;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
@@ -215,6 +232,7 @@ __global__ void k_zero_converged(double *R, long long nrows, const double *nrm2,
 // shift = lam_min - max(|theta - lam_min|, 1e-8 hnorm).
 __global__ void k_shift_update(const double *theta, const double *nrm2, int k, double thresh2,
                                double lam_min, double hnorm, double *shift) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   int i = 0;
   while (i < k - 1 && nrm2[i] <= thresh2) ++i;
@@ -226,52 +244,53 @@ void launch_zero_converged(double *R, long long nrows, const double *nrm2, int k
   count_launch();
   long long blocks = ((long long)k * nrows + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
-  k_zero_converged<<<(unsigned)blocks, 256, 0, str>>>(R, nrows, nrm2, k, thresh2);
+  launch_pdl(k_zero_converged, (unsigned)blocks, 256, 0, str, R, nrows, nrm2, k, thresh2);
 }
 
 void launch_shift_update(const double *theta, const double *nrm2, int k, double thresh2,
                          double lam_min, double hnorm, double *shift, cudaStream_t str) {
   count_launch();
-  k_shift_update<<<1, 32, 0, str>>>(theta, nrm2, k, thresh2, lam_min, hnorm, shift);
+  launch_pdl(k_shift_update, 1, 32, 0, str, theta, nrm2, k, thresh2, lam_min, hnorm, shift);
 }
 
 void launch_mark_dropped(double *G, int ldg, int m0, int bn, const int *keep0, cudaStream_t str) {
   count_launch();
-  k_mark_dropped<<<1, 32, 0, str>>>(G, ldg, m0, bn, keep0);
+  launch_pdl(k_mark_dropped, 1, 32, 0, str, G, ldg, m0, bn, keep0);
 }
 
 void launch_conv_check(const double *nrm2, int k, double thresh2, int *state, int max_iter,
                        cudaGraphConditionalHandle loop, int set_loop, cudaStream_t str) {
   count_launch();
-  k_conv_check<<<1, 32, 0, str>>>(nrm2, k, thresh2, state, max_iter, loop, set_loop);
+  launch_pdl(k_conv_check, 1, 32, 0, str, nrm2, k, thresh2, state, max_iter, loop, set_loop);
 }
 
 void launch_mirror_block(double *G, int ldg, int m0, int bn, cudaStream_t str) {
   count_launch();
-  k_mirror_block<<<nb((long long)(m0 + bn) * bn), 128, 0, str>>>(G, ldg, m0, bn);
+  launch_pdl(k_mirror_block, nb((long long)(m0 + bn) * bn), 128, 0, str, G, ldg, m0, bn);
 }
 void launch_set_diag(double *G, int ldg, const double *d, int m, cudaStream_t str) {
   count_launch();
-  k_set_diag<<<nb((long long)m * m), 128, 0, str>>>(G, ldg, d, m);
+  launch_pdl(k_set_diag, nb((long long)m * m), 128, 0, str, G, ldg, d, m);
 }
 void launch_copy_block(const double *src, int lds, int off, double *dst, int ldd, int mk,
                        cudaStream_t str) {
   count_launch();
-  k_copy_block<<<nb((long long)mk * mk), 128, 0, str>>>(src, lds, off, dst, ldd, mk);
+  launch_pdl(k_copy_block, nb((long long)mk * mk), 128, 0, str, src, lds, off, dst, ldd, mk);
 }
 void launch_copy_small(const double *src, double *dst, int n, cudaStream_t str) {
   count_launch();
-  k_copy_small<<<nb(n), 128, 0, str>>>(src, dst, n);
+  launch_pdl(k_copy_small, nb(n), 128, 0, str, src, dst, n);
 }
 void launch_sqrt_div(const double *nrm2, double *out, int n, double div, cudaStream_t str) {
   count_launch();
-  k_sqrt_div<<<nb(n), 128, 0, str>>>(nrm2, out, n, div);
+  launch_pdl(k_sqrt_div, nb(n), 128, 0, str, nrm2, out, n, div);
 }
 void launch_small_gemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,
                        int ldb, double beta, double *C, int ldc, cudaStream_t str) {
   if (m <= 0 || n <= 0) return;
   count_launch();
-  k_small_gemm<<<nb((long long)m * n), 128, 0, str>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  launch_pdl(k_small_gemm, nb((long long)m * n), 128, 0, str, m, n, k, alpha, A, lda, B, ldb, beta,
+             C, ldc);
 }
 
 }  // namespace tps

@@ -46,6 +46,7 @@
 #include <utility>
 
 #include "ozaki_tc.cuh"
+#include "pdl.cuh"
 #include "split_digits.cuh"
 #include "tps_internal.h"
 
@@ -53,30 +54,6 @@ namespace tps {
 
 namespace {
 
-// Programmatic dependent launch (the H-apply's split and product kernels): a dependent
-// kernel is launched while its predecessor still runs and holds every access to data the
-// predecessor writes behind griddepcontrol.wait; launch_dependents at entry lets the next
-// kernel be scheduled early.  Both are no-ops for kernels launched without the attribute.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                             cudaStream_t s, Args &&...args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 constexpr int kBeta = 6;
 constexpr int kPsiSlices = 9;  // wave-function digits: 54 bits
@@ -642,7 +619,7 @@ void launch_split(const double *X, int R, int C, long long bs, int batch, int S,
                   bool dependent = false) {
   count_launch();
   if (dependent)
-    launch_dependent(k_split, split_grid(R, C, batch), dim3(32, 8), 0, s, X, R, C, bs, S, rexp,
+    launch_pdl(k_split, split_grid(R, C, batch), dim3(32, 8), 0, s, X, R, C, bs, S, rexp,
                      outN, ldn, cexp, outT, ldt, zero_out);
   else
     k_split<<<split_grid(R, C, batch), dim3(32, 8), 0, s>>>(X, R, C, bs, S, rexp, outN, ldn,
@@ -668,7 +645,7 @@ cudaError_t launch_oz_pair(const CUtensorMap &mA1, const CUtensorMap &mB1, const
   const long long tiles = (long long)((g1.M + kBM - 1) / kBM) * ((g1.N + kBN - 1) / kBN) * nvec;
   if (2 * tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
   count_launch();
-  const cudaError_t le = launch_dependent(k_oz_gemm, dim3((unsigned)(2 * tiles)), dim3(kThreads),
+  const cudaError_t le = launch_pdl(k_oz_gemm, dim3((unsigned)(2 * tiles)), dim3(kThreads),
                                           oz_smem_bytes(kMaxSlices), s, mA1, mB1, g1, mA2, mB2, g2);
   return le != cudaSuccess ? le : cudaGetLastError();
 }

@@ -42,6 +42,7 @@
 
 #include <atomic>
 
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 namespace cg = cooperative_groups;
@@ -307,6 +308,7 @@ __device__ void jacobi64(JacobiSmem &sh, cg::cluster_group &cluster, const doubl
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
 k_jacobi(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
          int mp, int *__restrict__ stat, double tol_abs, double *Arot) {
+  pdl_entry();
   __shared__ JacobiSmem sh;
   cg::cluster_group cluster = cg::this_cluster();
   jacobi64(sh, cluster, G, m, ldg, theta, Yout, ldy, mp, stat, tol_abs, Arot);
@@ -673,6 +675,7 @@ __device__ void eig32(MixedSmem &sh, int n, int c0 = 0, int c1 = -1) {
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
 k_rr_mixed(const double *__restrict__ G, int m, int ldg, double *theta, double *Yout, int ldy,
            int mp, int *__restrict__ stat, double tol_abs, double *Arot, int refine_max) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MixedSmem &sh = *reinterpret_cast<MixedSmem *>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
@@ -1083,7 +1086,8 @@ k_rr_mixed(const double *__restrict__ G, int m, int ldg, double *theta, double *
 void launch_jacobi_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
                         cudaStream_t s, int mp, int *stat, double tol_abs, double *Arot) {
   count_launch();
-  k_jacobi<<<JCL, JT, 0, s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat, tol_abs, Arot);
+  launch_pdl(k_jacobi, JCL, JT, 0, s, G, m, ldg, theta, Y, ldy,
+             mp < m ? mp : 0, stat, tol_abs, Arot);
 }
 
 void launch_rr_eigh(const double *G, int m, int ldg, double *theta, double *Y, int ldy,
@@ -1103,7 +1107,8 @@ void launch_rr_eigh(const double *G, int m, int ldg, double *theta, double *Y, i
     attr_done.fetch_or(bit);
   }
   count_launch();
-  k_rr_mixed<<<JCL, JT, sizeof(MixedSmem), s>>>(G, m, ldg, theta, Y, ldy, mp < m ? mp : 0, stat,
+  launch_pdl(k_rr_mixed, JCL, JT, sizeof(MixedSmem), s, G, m, ldg, theta, Y, ldy,
+             mp < m ? mp : 0, stat,
                                                  tol_abs, Arot, refine_max > 0 ? refine_max : kRefineMax);
 }
 

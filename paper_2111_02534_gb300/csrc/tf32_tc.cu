@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "ozaki_tc.cuh"
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -84,14 +85,6 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-}
-
-// Programmatic dependent launch: a pass is launched while the previous one still runs;
-// griddepcontrol.wait holds a thread until the previous grid has completed and its writes
-// are visible, and launch_dependents lets the next pass's CTAs be scheduled early.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // One CTA computes the 128 x BN tile (m0, n0) of C = A B^T.  Warp 0 lane 0 loads (TMA),
@@ -340,18 +333,10 @@ void launch_tf32_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const TfArgs
   std::call_once(g_attr_once, [] {
     cudaFuncSetAttribute(k_tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   });
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + g.BN - 1) / g.BN));
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = kSmemBytes;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
   count_launch();
-  cudaLaunchKernelEx(&cfg, k_tf32_gemm, ta, tb, g);
+  launch_pdl(k_tf32_gemm,
+             dim3((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + g.BN - 1) / g.BN)),
+             dim3(kThreads), kSmemBytes, s, ta, tb, g);
 }
 
 }  // namespace

@@ -39,6 +39,7 @@
 
 #include "ozaki_tc.cuh"
 #include "split_digits.cuh"
+#include "pdl.cuh"
 #include "tps_internal.h"
 
 namespace tps {
@@ -263,6 +264,7 @@ __device__ __forceinline__ void y_fragments(const UpdArgs &g_, const double *Ys,
 template <int KT>
 __global__ void __launch_bounds__(kCons)
 k_update_split(const __grid_constant__ UpdArgs g_) {
+  pdl_entry();
   if (g_.need && *g_.need == 0) return;  // conditional product (decided on the device)
   __shared__ uint2 Bd[1][kUS][kUKT][32];
   __shared__ unsigned Fraw[1][8];
@@ -283,6 +285,7 @@ k_update_split(const __grid_constant__ UpdArgs g_) {
 template <int KT, int NG>
 __global__ void __launch_bounds__(kCons + 32, NG == 1 ? TPS_UPD_MINB : 1)
 k_update_split_staged(const __grid_constant__ UpdArgs g_) {
+  pdl_entry();
   if (g_.need && *g_.need == 0) return;
   extern __shared__ __align__(128) double ring[];
   __shared__ uint2 Bd[NG][kUS][kUKT][32];
@@ -481,13 +484,13 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
       const long long gx = ntiles < want ? ntiles : want;
       const size_t smem = (size_t)g.stages * g.p * kColStride * 8;
       g_staged_launches.fetch_add(1, std::memory_order_relaxed);
-      kStagedK[ng - 1][kt]<<<dim3((unsigned)gx, batch, (q + 8 * ng - 1) / (8 * ng)), kCons + 32,
-                             smem, s>>>(g);
+      launch_pdl(kStagedK[ng - 1][kt], dim3((unsigned)gx, batch, (q + 8 * ng - 1) / (8 * ng)),
+                 kCons + 32, smem, s, g);
     } else {
       g.stages = 0;
       const long long blocks = (nrows + kRows - 1) / kRows;
       const long long gx = blocks < cfg.sms * 4LL ? blocks : cfg.sms * 4LL;
-      kDirectK[kt]<<<dim3((unsigned)gx, batch, (q + 7) / 8), kCons, 0, s>>>(g);
+      launch_pdl(kDirectK[kt], dim3((unsigned)gx, batch, (q + 7) / 8), kCons, 0, s, g);
     }
   }
 }

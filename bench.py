@@ -47,9 +47,9 @@ TC_PAIRS = 54
 # removed from this table
 TRAFFIC_BYTES_PER_LAUNCH = {"k_tf32_gemm": 5.08e6}
 # the same for kernels whose launches cover a varying number of vectors: (bytes per launch,
-# bytes per vector), fitted to two captured launches of different width (k_oz_gemm: 12 and 8
+# bytes per vector), fitted to two captured launches of different width (k_oz_gemm: 6 and 4
 # vectors, 49.65 and 35.66 MB)
-TRAFFIC_AFFINE = {"k_oz_gemm": (7.68e6, 3.50e6)}
+TRAFFIC_AFFINE = {"k_oz_gemm": (7.68e6, 6.99e6)}
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates per GPU (TF32, BF16)
 # BF16 digit-pair products per FP64 multiply-add of the split block update
 SPLIT_UPDATE_PAIRS = 34

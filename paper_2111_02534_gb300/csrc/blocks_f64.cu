@@ -634,15 +634,18 @@ k_col_norms2(const double *__restrict__ A, long long lda, long long nrows, int n
   const long long r0 = (long long)chunk * rows_per;
   const long long r1 = r0 + rows_per < nrows ? r0 + rows_per : nrows;
   const double *a = A + (long long)c * lda;
-  double s0 = 0.0, s1 = 0.0;
+  // four independent loads in flight per thread
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   long long r = r0 + threadIdx.x;
-  for (; r + GT < r1; r += 2 * GT) {
-    const double x = a[r], y = a[r + GT];
-    s0 = fma(x, x, s0);
-    s1 = fma(y, y, s1);
+  for (; r + 3 * GT < r1; r += 4 * GT) {
+    const double x0 = a[r], x1 = a[r + GT], x2 = a[r + 2 * GT], x3 = a[r + 3 * GT];
+    s0 = fma(x0, x0, s0);
+    s1 = fma(x1, x1, s1);
+    s2 = fma(x2, x2, s2);
+    s3 = fma(x3, x3, s3);
   }
-  if (r < r1) s0 = fma(a[r], a[r], s0);
-  double v = s0 + s1;
+  for (; r < r1; r += GT) s0 = fma(a[r], a[r], s0);
+  double v = (s0 + s1) + (s2 + s3);
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __shared__ double red[GT / 32];
   __shared__ unsigned ticket;
@@ -656,12 +659,18 @@ k_col_norms2(const double *__restrict__ A, long long lda, long long nrows, int n
     ticket = atomicAdd(&count[c], 1u);
   }
   __syncthreads();
-  if (threadIdx.x != 0 || ticket != (unsigned)(nchunk - 1)) return;
+  if (threadIdx.x >= 32 || ticket != (unsigned)(nchunk - 1)) return;
+  // the last CTA of the column: warp 0 adds the chunks' sums, all loads issued at once,
+  // in a fixed order (lane-strided sums, then a fixed shuffle tree)
   __threadfence();
+  const double *pc = partial + (long long)c * nchunk;
   double t = 0.0;
-  for (int k = 0; k < nchunk; ++k) t += __ldcg(partial + (long long)c * nchunk + k);
-  out[c] = t;
-  count[c] = 0u;
+  for (int k = threadIdx.x; k < nchunk; k += 32) t += __ldcg(pc + k);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) {
+    out[c] = t;
+    count[c] = 0u;
+  }
 }
 
 __global__ void k_dgks_flag(const double *__restrict__ before, const double *__restrict__ after,

@@ -100,8 +100,34 @@ __device__ __forceinline__ unsigned col_raw_max(const double (&v)[4][4]) {
   return e;
 }
 
-template <int MT>
+// The leading NS digits of two values of one column (same exponent) as BF16 pairs.  NS = 7:
+// every digit (split_digits.cuh).  NS = 3: the top digit and the two leading base-256 digits
+// of the first 24-bit chunk, a 23-bit truncation (the rest, below 2^-23 of the column's
+// scale, is dropped): FP32-quality products for the correction equation, which is solved
+// to 1e-3 and whose result is orthonormalised in FP64.
+template <int NS>
+__device__ __forceinline__ void digits_n(double x0, double x1, unsigned raw_max,
+                                         uint32_t (&out)[NS]) {
+  if constexpr (NS == kUS) {
+    digits_pair(x0, x1, raw_max, out);
+  } else {
+    static_assert(NS == 3, "7 or 3 digits");
+    unsigned t0, a0, b0, t1, a1, b1;
+    float s0, s1;
+    chunks(x0, raw_max, t0, a0, b0, s0);
+    chunks(x1, raw_max, t1, a1, b1, s1);
+    out[0] = pack_bf16(s0 * (float)t0, s1 * (float)t1);
+    const float f0 = s0 * (float)a0, f1 = s1 * (float)a1;  // |f| < 2^24: exact
+    const float d00 = rintf(f0 * (1.f / 65536.f)), d01 = rintf(f1 * (1.f / 65536.f));
+    out[1] = pack_bf16(d00, d01);
+    out[2] = pack_bf16(rintf(fmaf(-d00, 65536.f, f0) * (1.f / 256.f)),
+                       rintf(fmaf(-d01, 65536.f, f1) * (1.f / 256.f)));
+  }
+}
+
+template <int MT, int NS>
 __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
+  constexpr int NL = NS == kUS ? kUL : NS;  // digit-pair levels kept: i + j < NL
   pdl_entry();
   constexpr int P = 16 * MT;  // padded A columns
   __shared__ double red[kGW][P * kGQ];
@@ -120,7 +146,7 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
        blk += (long long)gridDim.x * kGW) {
     const long long r0 = blk * kGRows;
     // B: column gq, its exponent and digit fragments {k 2c, 2c+1 | 2c+8, 2c+9; col gq}
-    uint32_t bf[kUS][4][2];
+    uint32_t bf[NS][4][2];
     unsigned f0, f1;
     {
       double bv[4][4];
@@ -130,10 +156,10 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
       for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          uint32_t d[kUS];
-          digits_pair(bv[ks][2 * h], bv[ks][2 * h + 1], fb, d);
+          uint32_t d[NS];
+          digits_n<NS>(bv[ks][2 * h], bv[ks][2 * h + 1], fb, d);
 #pragma unroll
-          for (int j = 0; j < kUS; ++j) bf[j][ks][h] = d[j];
+          for (int j = 0; j < NS; ++j) bf[j][ks][h] = d[j];
         }
       // exponents of this lane's output columns 2c and 2c + 1
       f0 = __shfl_sync(0xffffffffu, fb, (2 * c) * 4);
@@ -149,33 +175,33 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
       load_col(g.A, g.lda, g.p, 16 * mt + gq, r0, g.nrows, c, g.vec, av[0]);
       if (upper) load_col(g.A, g.lda, g.p, 16 * mt + gq + 8, r0, g.nrows, c, g.vec, av[1]);
       const unsigned e0 = col_raw_max(av[0]), e1 = upper ? col_raw_max(av[1]) : 0u;
-      float lv[kUL][4];
+      float lv[NL][4];
 #pragma unroll
-      for (int l = 0; l < kUL; ++l)
+      for (int l = 0; l < NL; ++l)
 #pragma unroll
         for (int t = 0; t < 4; ++t) lv[l][t] = 0.f;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
         // A fragment regs: {i g, k 2c..}, {i g+8, k 2c..}, {i g, k 2c+8..}, {i g+8, k 2c+8..}
-        uint32_t af[kUS][4];
+        uint32_t af[NS][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int col = r & 1, h = r >> 1;
           if (col && !upper) {
 #pragma unroll
-            for (int i = 0; i < kUS; ++i) af[i][r] = 0u;
+            for (int i = 0; i < NS; ++i) af[i][r] = 0u;
             continue;
           }
-          uint32_t d[kUS];
-          digits_pair(av[col][ks][2 * h], av[col][ks][2 * h + 1], col ? e1 : e0, d);
+          uint32_t d[NS];
+          digits_n<NS>(av[col][ks][2 * h], av[col][ks][2 * h + 1], col ? e1 : e0, d);
 #pragma unroll
-          for (int i = 0; i < kUS; ++i) af[i][r] = d[i];
+          for (int i = 0; i < NS; ++i) af[i][r] = d[i];
         }
 #pragma unroll
-        for (int j = 0; j < kUS; ++j)
+        for (int j = 0; j < NS; ++j)
 #pragma unroll
-          for (int i = 0; i < kUS; ++i)
-            if (i + j < kUL) mma_16816(lv[i + j], af[i], bf[j][ks][0], bf[j][ks][1]);
+          for (int i = 0; i < NS; ++i)
+            if (i + j < NL) mma_16816(lv[i + j], af[i], bf[j][ks][0], bf[j][ks][1]);
       }
       // levels -> FP64: value = (hi 2^32 + lo) 2^(E + F - 70) (Horner in base 256, levels
       // 0..3 and 4..7); C fragment t: column 16 mt + gq + 8 (t >> 1) of A, 2c + (t & 1) of B
@@ -183,8 +209,8 @@ __global__ void __launch_bounds__(32 * kGW, 1) k_gram_split(const GramArgs g) {
       for (int t = 0; t < 4; ++t) {
         long long hi = 0, lo = 0;
 #pragma unroll
-        for (int l = 0; l < kUL; ++l) {
-          const long long dl = (long long)__float2int_rn(lv[l][t]);
+        for (int l = 0; l < kUL; ++l) {  // levels NL .. 7 are zero
+          const long long dl = l < NL ? (long long)__float2int_rn(lv[l < NL ? l : 0][t]) : 0;
           if (l < kUL / 2)
             hi = hi * 256 + dl;
           else
@@ -283,7 +309,7 @@ bool gram_split_pays(int p, int q) { return p * q >= 32; }
 
 void launch_gram_split(const double *A, long long lda, int p, const double *B, long long ldb,
                        int q, long long nrows, double *G, int ldg, GramScratch &scr,
-                       cudaStream_t s, const int *need) {
+                       cudaStream_t s, const int *need, bool low) {
   if (p <= 0 || q <= 0) return;
   int trans = 0;
   if (p < q) {  // G^T = B^T A: the narrower operand is B
@@ -318,11 +344,20 @@ void launch_gram_split(const double *A, long long lda, int p, const double *B, l
   grid = grid < kGroup * kMaxGroups ? grid : kGroup * kMaxGroups;
   if (grid < 1) grid = 1;
   count_launch();
+  if (low) {
+    switch (MT) {
+      case 1: launch_pdl(k_gram_split<1, 3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+      case 2: launch_pdl(k_gram_split<2, 3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+      case 3: launch_pdl(k_gram_split<3, 3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+      default: launch_pdl(k_gram_split<4, 3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    }
+    return;
+  }
   switch (MT) {
-    case 1: launch_pdl(k_gram_split<1>, (unsigned)grid, 32 * kGW, 0, s, g); break;
-    case 2: launch_pdl(k_gram_split<2>, (unsigned)grid, 32 * kGW, 0, s, g); break;
-    case 3: launch_pdl(k_gram_split<3>, (unsigned)grid, 32 * kGW, 0, s, g); break;
-    default: launch_pdl(k_gram_split<4>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    case 1: launch_pdl(k_gram_split<1, kUS>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    case 2: launch_pdl(k_gram_split<2, kUS>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    case 3: launch_pdl(k_gram_split<3, kUS>, (unsigned)grid, 32 * kGW, 0, s, g); break;
+    default: launch_pdl(k_gram_split<4, kUS>, (unsigned)grid, 32 * kGW, 0, s, g); break;
   }
 }
 

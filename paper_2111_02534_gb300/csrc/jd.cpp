@@ -161,9 +161,9 @@ void tgram(const double *A, long long lda, long long bsa, int p, const double *B
     cudaEventRecord(a, s);
   }
   // as for the updates, the split pays on tall blocks only
-  if (!low && tl_split_grams && nrows >= 100000 && gram_split_supported(p, q, batch) &&
+  if (tl_split_grams && nrows >= 100000 && gram_split_supported(p, q, batch) &&
       gram_split_pays(p, q))
-    launch_gram_split(A, lda, p, B, ldb, q, nrows, G, ldg, scr, s, need);
+    launch_gram_split(A, lda, p, B, ldb, q, nrows, G, ldg, scr, s, need, low);
   else
     launch_gram(A, lda, bsa, p, B, ldb, bsb, q, nrows, G, ldg, bsg, batch, scr, s, need, low);
   if (rec) {

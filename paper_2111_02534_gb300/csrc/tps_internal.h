@@ -132,9 +132,11 @@ void launch_update_split(const double *A, long long lda, long long bsa, int p, c
 bool gram_split_supported(int p, int q, int batch);
 // the split is faster than the FMA pipe's Gram from p q >= 32 on (measured at 131,584 rows)
 bool gram_split_pays(int p, int q);
+// low: three digits per operand (23-bit truncation, FP32-quality products) for the
+// correction equation, like launch_gram's low.
 void launch_gram_split(const double *A, long long lda, int p, const double *B, long long ldb,
                        int q, long long nrows, double *G, int ldg, GramScratch &scr,
-                       cudaStream_t s, const int *need = nullptr);
+                       cudaStream_t s, const int *need = nullptr, bool low = false);
 // Queries the split update's launch configuration for every slab width up front (before
 // a stream capture).
 void prewarm_update_split();

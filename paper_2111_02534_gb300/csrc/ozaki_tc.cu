@@ -38,6 +38,7 @@
 // is order-independent).  Operand tiles reach shared memory by TMA (128-byte swizzle,
 // K-major), one thread issues tcgen05.mma into tensor memory, and four warps drain it.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -81,6 +82,36 @@ size_t oz_smem_bytes(int SB) {
 // -------------------------------- splitting ----------------------------------
 __device__ __forceinline__ unsigned raw_exponent(double x) {
   return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// The nine balanced base-64 digits of a scaled integer |q| <= 2^54 (most significant first),
+// as BF16 bit patterns: q is cut into three balanced 18-bit chunks by integer arithmetic and
+// each chunk (exact in FP32) into three digits by two FP32 roundings, d0 = rint(c 2^-12),
+// d1 = rint((c - 2^12 d0) 2^-6), d2 = c - 2^12 d0 - 2^6 d1.  Digits 1..8 lie in [-32, 32],
+// the top one in [-64, 64]; every one is exact in BF16 (a hardware conversion).  The digits
+// sum to q with the weights 2^(6 (8 - i)) like the digit-by-digit extraction below, which
+// the mode matrices' ten-digit slices use.
+__device__ __forceinline__ void digits9(long long q, uint16_t (&o)[9]) {
+  long long c[3];
+#pragma unroll
+  for (int k = 2; k > 0; --k) {  // least significant chunks first
+    long long l = q & ((1LL << 18) - 1);
+    if (l >= (1LL << 17)) l -= (1LL << 18);
+    c[k] = l;
+    q = (q - l) >> 18;
+  }
+  c[0] = q;  // |q| <= 2^18
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float f = (float)c[k];
+    const float d0 = rintf(f * (1.f / 4096.f));
+    const float r = fmaf(-d0, 4096.f, f);
+    const float d1 = rintf(r * (1.f / 64.f));
+    const float d2 = fmaf(-d1, 64.f, r);
+    o[3 * k] = __bfloat16_as_ushort(__float2bfloat16_rn(d0));
+    o[3 * k + 1] = __bfloat16_as_ushort(__float2bfloat16_rn(d1));
+    o[3 * k + 2] = __bfloat16_as_ushort(__float2bfloat16_rn(d2));
+  }
 }
 
 // BF16 bit pattern of a small integer (|d| <= 255), exact.
@@ -181,13 +212,20 @@ __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs
     if (outN && r < R && c < C) {
       long long q = scaled_integer(x, rexp[(long long)b * R + r], S);
       uint16_t *dst = outN + (long long)b * S * sN + (long long)r * ldn + c;
-      for (int i = S - 1; i > 0; --i) {
-        long long d = q & 63;
-        if (d >= 32) d -= 64;
-        dst[i * sN] = bf16_of_int((int)d);
-        q = (q - d) >> kBeta;
+      if (S == 9) {
+        uint16_t o[9];
+        digits9(q, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[i * sN] = o[i];
+      } else {
+        for (int i = S - 1; i > 0; --i) {
+          long long d = q & 63;
+          if (d >= 32) d -= 64;
+          dst[i * sN] = bf16_of_int((int)d);
+          q = (q - d) >> kBeta;
+        }
+        dst[0] = bf16_of_int((int)q);
       }
-      dst[0] = bf16_of_int((int)q);
     }
   }
   if (!outT) return;
@@ -199,13 +237,20 @@ __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs
       long long q = scaled_integer(tile[threadIdx.x][threadIdx.y + 8 * j],
                                    cexp[(long long)b * C + c], S);
       uint16_t *dst = outT + (long long)b * S * sT + (long long)c * ldt + r;
-      for (int i = S - 1; i > 0; --i) {
-        long long d = q & 63;
-        if (d >= 32) d -= 64;
-        dst[i * sT] = bf16_of_int((int)d);
-        q = (q - d) >> kBeta;
+      if (S == 9) {
+        uint16_t o[9];
+        digits9(q, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[i * sT] = o[i];
+      } else {
+        for (int i = S - 1; i > 0; --i) {
+          long long d = q & 63;
+          if (d >= 32) d -= 64;
+          dst[i * sT] = bf16_of_int((int)d);
+          q = (q - d) >> kBeta;
+        }
+        dst[0] = bf16_of_int((int)q);
       }
-      dst[0] = bf16_of_int((int)q);
     }
   }
 }
@@ -257,13 +302,20 @@ k_split_fibers(const double *__restrict__ X, long long bs, long long M, int nk, 
     for (int i = tid & 15; i < nk; i += 16) {
       long long q = scaled_integer(tile[f][i], ex[f], S);
       uint16_t *dst = row + i;
-      for (int j = S - 1; j > 0; --j) {
-        long long d = q & 63;
-        if (d >= 32) d -= 64;
-        dst[j * plane] = bf16_of_int((int)d);
-        q = (q - d) >> kBeta;
+      if (S == 9) {
+        uint16_t o[9];
+        digits9(q, o);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) dst[j * plane] = o[j];
+      } else {
+        for (int j = S - 1; j > 0; --j) {
+          long long d = q & 63;
+          if (d >= 32) d -= 64;
+          dst[j * plane] = bf16_of_int((int)d);
+          q = (q - d) >> kBeta;
+        }
+        dst[0] = bf16_of_int((int)q);
       }
-      dst[0] = bf16_of_int((int)q);
     }
   }
 }

@@ -88,7 +88,27 @@ k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
   T acc[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) acc[k] = T(0);
-  for (long long r = r0 + threadIdx.x; r < r1; r += GT) {
+  // two rows per iteration: all of their loads are issued before the first FMA waits
+  long long r = r0 + threadIdx.x;
+  for (; r + GT < r1; r += 2 * GT) {
+    T a[2][BP], b[2][BQ];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int i = 0; i < BP; ++i)
+        a[h][i] = (i0 + i < p) ? (T)As[(long long)(i0 + i) * lda + r + h * GT] : T(0);
+#pragma unroll
+      for (int j = 0; j < BQ; ++j)
+        b[h][j] = (j0 + j < q) ? (T)Bs[(long long)(j0 + j) * ldb + r + h * GT] : T(0);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int i = 0; i < BP; ++i)
+#pragma unroll
+        for (int j = 0; j < BQ; ++j) acc[i * BQ + j] = fma(a[h][i], b[h][j], acc[i * BQ + j]);
+  }
+  if (r < r1) {
     T a[BP], b[BQ];
 #pragma unroll
     for (int i = 0; i < BP; ++i) a[i] = (i0 + i < p) ? (T)As[(long long)(i0 + i) * lda + r] : T(0);
@@ -176,7 +196,18 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
   T acc[BQ];
 #pragma unroll
   for (int j = 0; j < BQ; ++j) acc[j] = T(0);
-  for (int i = 0; i < p; ++i) {
+  // four loads of A in flight before the FMAs that use them
+  int i = 0;
+  for (; i + 4 <= p; i += 4) {
+    T a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = (T)As[(long long)(i + u) * lda + r];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < BQ; ++j) acc[j] = fma(a[u], Ys[i + u][j], acc[j]);
+  }
+  for (; i < p; ++i) {
     const T a = (T)As[(long long)i * lda + r];
 #pragma unroll
     for (int j = 0; j < BQ; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);

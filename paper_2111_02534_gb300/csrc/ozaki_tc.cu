@@ -27,6 +27,11 @@
 //    wave function's leading digit) puts that sum near 1e-16.
 //  * The epilogue converts each level to an integer, combines the levels in two int64
 //    Horner sums (exact) and forms the FP64 result with one conversion pair and one FMA.
+//  * The 2D mode products contract over at most 128 points, short enough for base-256
+//    digits (beta = 8, every digit in [-128, 128], still exact in BF16): seven for the
+//    wave function's fibers (55 bits), eight for the mode matrices (62 bits), and the 35
+//    pairs with i + j <= 8 (1-based) in eight accumulators, every partial sum below
+//    7 * 2^14 * 146 < 2^24 for K <= 146 (54 pairs and ten levels in base 64).
 //
 // The 1D H-apply out = K_x P + P K_y^T + (V - theta) P (P = psi as n_x x n_y) runs as two
 // such products in the transposed orientation (rows of C = the y index, so that one warp
@@ -60,6 +65,11 @@ constexpr int kBeta = 6;
 constexpr int kPsiSlices = 9;  // wave-function digits: 54 bits
 constexpr int kOpSlices = 10;  // mode-matrix digits: 60 bits (see below)
 constexpr int kLevels = 10;    // digit-pair levels kept: i + j <= 9 (0-based)
+// 2D mode products (contraction length <= 128): base-256 digits, |d| <= 128, so a level's
+// partial sums stay below 7 * 2^14 * 146 < 2^24 (exact in FP32) for K <= 146
+constexpr int kPsiSlices2 = 7;  // wave-function digits: 55 bits
+constexpr int kOpSlices2 = 8;   // mode-matrix digits: 62 bits
+constexpr int kLevels2 = 8;     // i + j <= 7
 constexpr int kMaxSlices = 10;
 constexpr int kBM = 128;       // output rows per CTA (TMEM lanes)
 constexpr int kBN = 48;        // output columns per CTA; kLevels * kBN <= 512 TMEM columns
@@ -114,6 +124,46 @@ __device__ __forceinline__ void digits9(long long q, uint16_t (&o)[9]) {
   }
 }
 
+// The S balanced base-256 digits (S = 7: |q| <= 2^55; S = 8: |q| <= 2^62) of a scaled
+// integer, most significant first, as BF16 bit patterns, every digit in [-128, 128]:
+// q = c0 2^48 + c1 2^24 + c2 with c1, c2 balanced 24-bit chunks (integer arithmetic), each
+// chunk (exact in FP32) cut into three digits by two FP32 roundings, d0 = rint(c 2^-16),
+// d1 = rint((c - 2^16 d0) 2^-8), d2 = c - 2^16 d0 - 2^8 d1; c0 is one digit (|c0| <= 128)
+// for S = 7, and two, e0 = rint(c0 / 256) and c0 - 256 e0, for S = 8 (|c0| <= 2^14 + 1).
+// Digit i weighs 2^(8 (S - 1 - i)).
+template <int S>
+__device__ __forceinline__ void digits256(long long q, uint16_t (&o)[S]) {
+  static_assert(S == 7 || S == 8, "seven or eight base-256 digits");
+  long long c[3];
+#pragma unroll
+  for (int k = 2; k > 0; --k) {  // least significant chunks first
+    long long l = q & ((1LL << 24) - 1);
+    if (l >= (1LL << 23)) l -= (1LL << 24);
+    c[k] = l;
+    q = (q - l) >> 24;
+  }
+  c[0] = q;
+  int p = 0;
+  const float f0 = (float)c[0];
+  if (S == 8) {
+    const float e0 = rintf(f0 * (1.f / 256.f));
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(e0));
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(-e0, 256.f, f0)));
+  } else {
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(f0));
+  }
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    const float f = (float)c[k];
+    const float d0 = rintf(f * (1.f / 65536.f));
+    const float r = fmaf(-d0, 65536.f, f);
+    const float d1 = rintf(r * (1.f / 256.f));
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(d0));
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(d1));
+    o[p++] = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(-d1, 256.f, r)));
+  }
+}
+
 // BF16 bit pattern of a small integer (|d| <= 255), exact.
 __device__ __forceinline__ uint16_t bf16_of_int(int d) {
   if (d == 0) return 0;
@@ -124,25 +174,62 @@ __device__ __forceinline__ uint16_t bf16_of_int(int d) {
   return (uint16_t)(s | ((unsigned)(p + 127) << 7) | man);
 }
 
-// round(x * 2^(S*beta - E)) with E = raw_max - 1022 the row exponent, by integer
-// arithmetic on the FP64 fields (subnormals are flushed: they lie 2^-1022 below any row
-// scale that matters here).  |result| <= 2^(S*beta).
-__device__ __forceinline__ long long scaled_integer(double x, unsigned raw_max, int S) {
+// Bits of the scaled integer that S digit slices hold: nine or ten base-64 digits (54 or 60
+// bits, the 1D products), seven or eight base-256 digits (55 or 62 bits, the 2D products).
+__host__ __device__ constexpr int slice_bits(int S) {
+  return S == 7 ? 55 : (S == 8 ? 62 : S * kBeta);
+}
+
+// round(x * 2^(bits - E)) with E = raw_max - 1022 the row exponent, by integer arithmetic
+// on the FP64 fields (subnormals are flushed: they lie 2^-1022 below any row scale that
+// matters here).  |result| <= 2^bits, bits <= 62.
+__device__ __forceinline__ long long scaled_integer(double x, unsigned raw_max, int bits) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((u >> 52) & 0x7FF);
   if (ex == 0 || raw_max == 0) return 0;
   const long long mant = (long long)((u & ((1ULL << 52) - 1)) | (1ULL << 52));
   const int E = (int)raw_max - 1022;
-  const int sh = ex - 1075 + S * kBeta - E;
+  const int sh = ex - 1075 + bits - E;
   long long q;
   if (sh >= 0) {
-    q = mant << sh;                     // |x| < 2^E keeps this below 2^(S beta)
+    q = mant << sh;                     // |x| < 2^E keeps this below 2^bits
   } else if (sh > -63) {
     q = (mant + (1LL << (-sh - 1))) >> (-sh);
   } else {
     q = 0;
   }
   return (u >> 63) ? -q : q;
+}
+
+// The S digit slices of x (row exponent raw_max): dst[i * stride] = digit i, most
+// significant first, in the format that S selects (slice_bits).
+__device__ __forceinline__ void write_digits(double x, unsigned raw_max, int S, uint16_t *dst,
+                                             long long stride) {
+  long long q = scaled_integer(x, raw_max, slice_bits(S));
+  if (S == 9) {
+    uint16_t o[9];
+    digits9(q, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[i * stride] = o[i];
+  } else if (S == 7) {
+    uint16_t o[7];
+    digits256<7>(q, o);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) dst[i * stride] = o[i];
+  } else if (S == 8) {
+    uint16_t o[8];
+    digits256<8>(q, o);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i * stride] = o[i];
+  } else {
+    for (int i = S - 1; i > 0; --i) {
+      long long d = q & 63;
+      if (d >= 32) d -= 64;
+      dst[i * stride] = bf16_of_int((int)d);
+      q = (q - d) >> kBeta;
+    }
+    dst[0] = bf16_of_int((int)q);
+  }
 }
 
 // Row and column exponent maxima of a batch of R x C FP64 matrices (C contiguous):
@@ -209,49 +296,18 @@ __global__ void k_split(const double *__restrict__ X, int R, int C, long long bs
       if (zero_out) zero_out[b * bs + (long long)r * C + c] = 0.0;
     }
     tile[threadIdx.y + 8 * j][threadIdx.x] = x;
-    if (outN && r < R && c < C) {
-      long long q = scaled_integer(x, rexp[(long long)b * R + r], S);
-      uint16_t *dst = outN + (long long)b * S * sN + (long long)r * ldn + c;
-      if (S == 9) {
-        uint16_t o[9];
-        digits9(q, o);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * sN] = o[i];
-      } else {
-        for (int i = S - 1; i > 0; --i) {
-          long long d = q & 63;
-          if (d >= 32) d -= 64;
-          dst[i * sN] = bf16_of_int((int)d);
-          q = (q - d) >> kBeta;
-        }
-        dst[0] = bf16_of_int((int)q);
-      }
-    }
+    if (outN && r < R && c < C)
+      write_digits(x, rexp[(long long)b * R + r], S,
+                   outN + (long long)b * S * sN + (long long)r * ldn + c, sN);
   }
   if (!outT) return;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = c0 + threadIdx.y + 8 * j, r = r0 + threadIdx.x;
-    if (r < R && c < C) {
-      long long q = scaled_integer(tile[threadIdx.x][threadIdx.y + 8 * j],
-                                   cexp[(long long)b * C + c], S);
-      uint16_t *dst = outT + (long long)b * S * sT + (long long)c * ldt + r;
-      if (S == 9) {
-        uint16_t o[9];
-        digits9(q, o);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * sT] = o[i];
-      } else {
-        for (int i = S - 1; i > 0; --i) {
-          long long d = q & 63;
-          if (d >= 32) d -= 64;
-          dst[i * sT] = bf16_of_int((int)d);
-          q = (q - d) >> kBeta;
-        }
-        dst[0] = bf16_of_int((int)q);
-      }
-    }
+    if (r < R && c < C)
+      write_digits(tile[threadIdx.x][threadIdx.y + 8 * j], cexp[(long long)b * C + c], S,
+                   outT + (long long)b * S * sT + (long long)c * ldt + r, sT);
   }
 }
 
@@ -299,24 +355,7 @@ k_split_fibers(const double *__restrict__ X, long long bs, long long M, int nk, 
     const long long m = m0 + f;
     if (m >= M) continue;
     uint16_t *row = out + ((long long)v * S) * plane + m * ld;
-    for (int i = tid & 15; i < nk; i += 16) {
-      long long q = scaled_integer(tile[f][i], ex[f], S);
-      uint16_t *dst = row + i;
-      if (S == 9) {
-        uint16_t o[9];
-        digits9(q, o);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) dst[j * plane] = o[j];
-      } else {
-        for (int j = S - 1; j > 0; --j) {
-          long long d = q & 63;
-          if (d >= 32) d -= 64;
-          dst[j * plane] = bf16_of_int((int)d);
-          q = (q - d) >> kBeta;
-        }
-        dst[0] = bf16_of_int((int)q);
-      }
-    }
+    for (int i = tid & 15; i < nk; i += 16) write_digits(tile[f][i], ex[f], S, row + i, plane);
   }
 }
 
@@ -350,14 +389,15 @@ __device__ __forceinline__ double combine30(long long hi, long long lo, int E) {
 }
 
 // One CTA computes the 128 x kBN tile (m0, n0) of C = A B^T for vector blockIdx.z, with
-// SA digit slices of A and SB of B (kLevels levels kept).
+// SA digit slices of A and SB of B, L levels kept: base-64 digits with L = 10 (the 1D
+// products), base-256 digits with L = 8 (the 2D products).
 // Warp 0 lane 0 loads (TMA), warp 1 lane 0 issues the MMAs, warp 2 owns the tensor
 // memory, all four warps run the epilogue (warp w reads TMEM lanes 32w .. 32w + 31).
 // The MMA issue loop is fully unrolled over the digit pairs with descriptors formed once
 // per tile: a tcgen05.mma costs the issuing thread about 45 cycles at best, and at
 // N = 48 any per-MMA address or loop arithmetic on that thread's critical path (a
 // runtime-bounded pair loop measured about 150 cycles per MMA) idles the tensor pipe.
-template <int SA, int SB>
+template <int SA, int SB, int L>
 __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorMap *tmBp,
                                         const OzArgs &g, int m0, int n0, int v,
                                         uint8_t *smem_raw) {
@@ -365,7 +405,10 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
   const CUtensorMap &tmA = *tmAp, &tmB = *tmBp;
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  constexpr int L = kLevels;
+  static_assert((L == kLevels && SA + SB == kPsiSlices + kOpSlices) ||
+                    (L == kLevels2 && SA == kPsiSlices2 && SB == kOpSlices2),
+                "base-64 (1D) or base-256 (2D) digit products");
+  static_assert(L * kBN <= (int)kTmemCols, "levels must fit in tensor memory");
   const uint32_t bstage = (uint32_t)SB * b_slice_bytes();
   uint8_t *sB = base;
   uint8_t *sA = base + kBStages * bstage;
@@ -513,26 +556,31 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
     for (int c = half * (kBN / 16); c < (half + 1) * (kBN / 16); ++c) {
       long long hi[8], lo[8];
       // all levels of these 8 columns in flight at once, one wait
-      uint32_t r[kLevels][8];
+      uint32_t r[L][8];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r[l]);
+      for (int l = 0; l < L; ++l) tc::tmem_ld_x8(trow + (uint32_t)(l * kBN + c * 8), r[l]);
       tc::tmem_ld_wait();
-      // levels 0..4 and 5..9 in base 64: pairs of levels fit in 32 bits (|D_l| < 2^24)
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        int d[kLevels];
+        int d[L];
 #pragma unroll
-        for (int l = 0; l < kLevels; ++l) d[l] = __float2int_rn(__uint_as_float(r[l][q]));
-        hi[q] = (long long)(d[0] * 64 + d[1]) * (1LL << 18) + (long long)(d[2] * 64 + d[3]) * 64 +
-                d[4];
-        lo[q] = (long long)(d[5] * 64 + d[6]) * (1LL << 18) + (long long)(d[7] * 64 + d[8]) * 64 +
-                d[9];
+        for (int l = 0; l < L; ++l) d[l] = __float2int_rn(__uint_as_float(r[l][q]));
+        if (L == kLevels) {
+          // levels 0..4 and 5..9 in base 64: pairs of levels fit in 32 bits (|D_l| < 2^24)
+          hi[q] = (long long)(d[0] * 64 + d[1]) * (1LL << 18) +
+                  (long long)(d[2] * 64 + d[3]) * 64 + d[4];
+          lo[q] = (long long)(d[5] * 64 + d[6]) * (1LL << 18) +
+                  (long long)(d[7] * 64 + d[8]) * 64 + d[9];
+        } else {
+          // levels 0..3 and 4..7 in base 256, in 64-bit arithmetic
+          hi[q] = (((long long)d[0] * 256 + d[1]) * 256 + d[2]) * 256 + d[3];
+          lo[q] = (((long long)d[4] * 256 + d[5]) * 256 + d[6]) * 256 + d[7];
+        }
       }
       if (!mvalid) continue;
       // the group's 8 outputs: every load (V and psi for the potential term, the previous
       // value for an accumulating store) is issued before any store, so the loads' latency
       // is paid once per group, not once per output
-      static_assert(kLevels == 10 && kBeta == 6, "hi 2^30 + lo needs levels 0..4 / 5..9");
       double val[8], ld1[8], ld2[8];
       long long idx[8];
       int En[8];
@@ -555,10 +603,13 @@ __device__ __forceinline__ void oz_tile(const CUtensorMap *tmAp, const CUtensorM
       for (int q = 0; q < 8; ++q) {
         const int n = n0 + c * 8 + q;
         if (n >= g.N) break;
-        // sum_l D_l 2^(-beta (l + 2)) = (hi 2^30 + lo) 2^(Em + En - 66), hi carrying levels
-        // 0 .. 4 and lo levels 5 .. 9, rounded once to FP64 by integer arithmetic (GB300's
-        // FP64 pipe issues a warp instruction per ~64 cycles of a sub-partition)
-        val[q] = combine30(hi[q], lo[q], Em + En[q]);
+        // base 64: sum_l D_l 2^(-6 (l + 2)) = (hi 2^30 + lo) 2^(Em + En - 66), hi carrying
+        // levels 0 .. 4 and lo levels 5 .. 9; base 256 (A = psi at 55 bits, B = K at 62):
+        // sum_l D_l 2^(104 - 8 l) 2^(Em + En - 117) = (hi 2^32 + lo) 2^(Em + En - 69).
+        // Rounded once to FP64 by integer arithmetic (GB300's FP64 pipe issues a warp
+        // instruction per ~64 cycles of a sub-partition)
+        val[q] = L == kLevels ? combine30(hi[q], lo[q], Em + En[q])
+                              : b256::combine(hi[q], lo[q], Em + En[q] + 1);
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -599,15 +650,15 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUte
   const int v = r / (tm * tn), t = r % (tm * tn);
   const int m0 = (t % tm) * kBM, n0 = (t / tm) * kBN;
   if (!second)
-    oz_tile<kOpSlices, kPsiSlices>(&tmA1, &tmB1, g1, m0, n0, v, smem_raw);
+    oz_tile<kOpSlices, kPsiSlices, kLevels>(&tmA1, &tmB1, g1, m0, n0, v, smem_raw);
   else
-    oz_tile<kPsiSlices, kOpSlices>(&tmA2, &tmB2, g2, m0, n0, v, smem_raw);
+    oz_tile<kPsiSlices, kOpSlices, kLevels>(&tmA2, &tmB2, g2, m0, n0, v, smem_raw);
 }
 
 
-// One product C = A B^T (A = wave-function fiber slices, 9 digits; B = mode-matrix slices,
-// 10 digits) over tiles m fastest, then n, then the vector: a mode product of the 2D
-// H-apply.
+// One product C = A B^T (A = wave-function fiber slices, 7 base-256 digits; B = mode-matrix
+// slices, 8 digits; contraction length <= 128) over tiles m fastest, then n, then the
+// vector: a mode product of the 2D H-apply.
 __global__ void __launch_bounds__(kThreads, 1)
 k_oz_gemm1(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ OzArgs g) {
@@ -616,7 +667,7 @@ k_oz_gemm1(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   const int r = (int)blockIdx.x;
   const int v = r / (tm * tn), t = r % (tm * tn);
   const int m0 = (t % tm) * kBM, n0 = (t / tm) * kBN;
-  oz_tile<kPsiSlices, kOpSlices>(&tmA, &tmB, g, m0, n0, v, smem_raw);
+  oz_tile<kPsiSlices2, kOpSlices2, kLevels2>(&tmA, &tmB, g, m0, n0, v, smem_raw);
 }
 
 // ------------------------------------ host ------------------------------------
@@ -751,6 +802,8 @@ void free_tc_operator(TcOperator *t) {
 cudaError_t ensure_tc_operator_2d(const DevOperator &op, cudaStream_t s) {
   TcOperator *t = new TcOperator();
   t->two_d = true;
+  t->So = kOpSlices2;
+  t->Sp = kPsiSlices2;
   const int So = t->So, Sp = t->Sp;
   long long maxw = 0;
   for (int k = 0; k < 4; ++k) {
@@ -894,7 +947,7 @@ cudaError_t launch_apply_h_tc_2d(const DevOperator &op, const double *psi, doubl
       }
       OzArgs g;
       std::memset(&g, 0, sizeof(g));
-      g.L = kLevels;
+      g.L = kLevels2;
       g.M = (int)M;
       g.N = n;
       g.K = n;

@@ -99,10 +99,14 @@ def test_apply_h_tc_full_size_vs_oracle():
 
 
 @pytest.mark.parametrize("n,nvec,theta", [((8, 8, 6, 6), 2, 0.0), ((6, 6, 10, 10), 3, -0.4),
-                                          ((12, 12, 8, 8), 1, 0.7), ((4, 4, 4, 4), 2, 0.0)])
+                                          ((12, 12, 8, 8), 1, 0.7), ((4, 4, 4, 4), 2, 0.0),
+                                          ((128, 128, 4, 4), 2, 0.3),
+                                          ((4, 4, 128, 128), 1, -0.2)])
 def test_apply_h_tc_2d_vs_oracle(n, nvec, theta):
     """Eq. tensor_op2D with the four mode products on the tensor cores, against the
-    oracle's Kronecker-sum apply, element by element (the same bar as the FP64 path)."""
+    oracle's Kronecker-sum apply, element by element (the same bar as the FP64 path).  The
+    128-point modes are the longest contraction the 2D digit format takes (base-256 digits,
+    level sums exact up to 146 points), as fibers of stride > 1 and as rows."""
     require_gpu()
     tps = _tps()
     from oracle.hamiltonian import problem_2d

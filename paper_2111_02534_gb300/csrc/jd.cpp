@@ -118,26 +118,6 @@ struct SolverWorkspace {
 
 namespace {
 
-// counter-based normal deviates (splitmix64 + Box-Muller) for random start blocks
-uint64_t splitmix64(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ULL;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
-  return x ^ (x >> 31);
-}
-double uniform01(uint64_t seed, uint64_t i) {
-  return ((splitmix64(seed * 0x2545F4914F6CDD1DULL + i) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-}
-void random_normal(std::vector<double> &v, uint64_t seed, uint64_t offset) {
-  const double two_pi = 6.283185307179586;
-  for (size_t e = 0; e < v.size(); e += 2) {
-    const double u1 = uniform01(seed, offset + e), u2 = uniform01(seed, offset + e + 1);
-    const double r = std::sqrt(-2.0 * std::log(u1));
-    v[e] = r * std::cos(two_pi * u2);
-    if (e + 1 < v.size()) v[e + 1] = r * std::sin(two_pi * u2);
-  }
-}
-
 // Timers of the running solve (tps_solver_opts.timing), for the skinny-kernel wrappers.
 thread_local PhaseTiming *tl_timing = nullptr;
 thread_local bool tl_split_updates = false;  // FP64 updates as digit-split tensor-core products
@@ -212,13 +192,12 @@ struct Ctx {
   long long N;
 };
 
+// ncols random start columns, made on the device (counter-based, so reproducible)
 int fill_random(Ctx &c, double *dst, int ncols, uint64_t seed, uint64_t &counter) {
-  std::vector<double> h((size_t)ncols * c.N);
-  random_normal(h, seed, counter);
-  counter += h.size() + 1;
-  TPS_CUDA_TRY(c.ctx, cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double),
-                                      cudaMemcpyHostToDevice, c.s));
-  TPS_CUDA_TRY(c.ctx, cudaStreamSynchronize(c.s));
+  const long long n = (long long)ncols * c.N;
+  launch_fill_normal(dst, n, seed, counter, c.s);
+  counter += (uint64_t)n + 1;
+  TPS_CUDA_TRY(c.ctx, cudaGetLastError());
   return TPS_OK;
 }
 

@@ -239,6 +239,48 @@ __global__ void k_shift_update(const double *theta, const double *nrm2, int k, d
   *shift = lam_min - fmax(fabs(theta[i] - lam_min), 1e-8 * hnorm);
 }
 
+namespace {
+
+// Normal deviates for random start blocks, counter-based (a block depends on the seed and
+// its counter only): the uniform u_i in (0, 1) is the top 24 bits of
+// splitmix64(seed * 0x2545F4914F6CDD1D + i) plus 1/2, times 2^-24 (splitmix64: Steele, Lea &
+// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014), and each pair
+// (u_e, u_e+1) gives two deviates by the Box-Muller transform, in FP32 (a start block needs
+// no more than random directions).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ float uniform01(uint64_t seed, uint64_t i) {
+  return ((float)(splitmix64(seed * 0x2545F4914F6CDD1DULL + i) >> 40) + 0.5f) * (1.f / 16777216.f);
+}
+__global__ void k_fill_normal(double *dst, long long n, uint64_t seed, uint64_t offset) {
+  pdl_entry();
+  for (long long e = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); e < n;
+       e += 2LL * gridDim.x * blockDim.x) {
+    const float u1 = uniform01(seed, offset + (uint64_t)e);
+    const float u2 = uniform01(seed, offset + (uint64_t)e + 1);
+    const float r = sqrtf(-2.f * logf(u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    dst[e] = (double)(r * cs);
+    if (e + 1 < n) dst[e + 1] = (double)(r * sn);
+  }
+}
+
+}  // namespace
+
+void launch_fill_normal(double *dst, long long n, uint64_t seed, uint64_t offset,
+                        cudaStream_t str) {
+  if (n <= 0) return;
+  count_launch();
+  long long blocks = (n / 2 + 256) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  launch_pdl(k_fill_normal, (unsigned)blocks, 256, 0, str, dst, n, seed, offset);
+}
+
 void launch_zero_converged(double *R, long long nrows, const double *nrm2, int k, double thresh2,
                            cudaStream_t str) {
   count_launch();

@@ -38,6 +38,10 @@ void launch_copy_block(const double *src, int lds, int off, double *dst, int ldd
                        cudaStream_t str);
 void launch_copy_small(const double *src, double *dst, int n, cudaStream_t str);
 void launch_sqrt_div(const double *nrm2, double *out, int n, double div, cudaStream_t str);
+// dst[0 .. n) = standard normal deviates i = offset .. offset + n - 1 of the seed's
+// counter-based stream (random start blocks)
+void launch_fill_normal(double *dst, long long n, uint64_t seed, uint64_t offset,
+                        cudaStream_t str);
 void launch_small_gemm(int m, int n, int k, double alpha, const double *A, int lda, const double *B,
                        int ldb, double beta, double *C, int ldc, cudaStream_t str);
 

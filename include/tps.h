@@ -59,12 +59,13 @@ enum { TPS_ANY = 0, TPS_X_EVEN = 1, TPS_X_ODD = 2 }; /* heavy-exchange sector (S
 enum { TPS_F64 = 0, TPS_F32 = 1, TPS_F64_TC = 2, TPS_TF32_TC = 3 };  /* arithmetic of apply calls
                                                                        (data stay FP64) */
 /* TPS_F64_TC: FP64-accurate mode products emulated on the BF16 tensor cores by error-free
- * splitting into six-bit digit slices per operand row (9 for the wave function, 10 for the
- * mode matrices; Ozaki scheme), exact FP32 accumulation per digit level, FP64
- * recombination; H-apply only (1D, and 2D with at most 128 points per mode).
- * TPS_TF32_TC: the preconditioner's four mode products on the tensor cores with TF32 inputs
+ * splitting into digit slices per operand row (1D: 9 six-bit digits for the wave function,
+ * 10 for the mode matrices; 2D, at most 128 points per mode: 7 and 8 eight-bit digits;
+ * Ozaki scheme), exact FP32 accumulation per digit level, FP64 recombination; H-apply only.
+ * TPS_TF32_TC: the preconditioner's mode products on the tensor cores with TF32 inputs
  * (10 explicit mantissa bits) and FP32 accumulation, ~2.5e-3 relative to the exact
- * (T - sigma)^-1 r; 1D preconditioner only. */
+ * (T - sigma)^-1 r; preconditioner only (1D; 2D when every mode has 4 to 128 points, a
+ * multiple of 4). */
 /* Rayleigh-Ritz eigensolver (Sec. 4.1, the projected problem G y = theta y, m <= 64):
  * TPS_RR_MIXED: FP32 eigenvectors (tridiagonalisation, bisection, inverse iteration), then FP64
  *   iterative refinement of the eigenvectors
@@ -183,11 +184,12 @@ int tps_apply_h(tps_ctx *ctx, const void *psi_dev, void *out_dev, int nvec, doub
  * over all 2*dim modes.  Returns TPS_ERR_SINGULAR when
  * min |lambda_sum - theta| < 1e-14 * max |lambda_sum|.  r_dev, out_dev: device
  * [nvec][N] FP64, must not overlap.  dtype TPS_F64: FP64 arithmetic; TPS_F32: FP32
- * arithmetic; TPS_TF32_TC (1D only, TPS_ERR_INVALID_ARG in 2D): the four mode products
- * on the tensor cores with TF32 inputs and FP32 accumulation, ~2.5e-3 relative to the
- * exact solve (the first call on a context builds padded FP32 eigenbases of a few MB).
- * The preconditioner only approximates (H - theta)^-1 whatever the dtype: the solver uses
- * TPS_TF32_TC by default in 1D and TPS_F32 in 2D. */
+ * arithmetic; TPS_TF32_TC: the mode products (four in 1D, eight in 2D) on the tensor
+ * cores with TF32 inputs and FP32 accumulation, ~2.5e-3 relative to the exact solve (the
+ * first call on a context builds padded FP32 eigenbases of a few MB); in 2D every mode
+ * must have 4 to 128 points, a multiple of 4 (else TPS_ERR_INVALID_ARG).  The
+ * preconditioner only approximates (H - theta)^-1 whatever the dtype: the solver uses
+ * TPS_TF32_TC by default (TPS_F32 on 2D grids it does not take). */
 int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, double theta,
                    int dtype, cudaStream_t stream);
 
@@ -213,8 +215,8 @@ typedef struct tps_solver_opts {
   int smooth_start;   /* applications of the kinetic preconditioner (shift -1e-3 ||H||_est) to
                          the random part of the start block, a low-pass filter (default 2) */
   int prec_dtype;     /* arithmetic of the preconditioner inside the solver: TPS_TF32_TC
-                         (default; tensor cores, 1D -- 2D solves use TPS_F32), TPS_F32 or
-                         TPS_F64 */
+                         (default; tensor cores -- TPS_F32 on 2D grids whose modes are not
+                         4 to 128 points, a multiple of 4), TPS_F32 or TPS_F64 */
   int h_dtype;        /* TPS_F64 (default): FP64 H products throughout (on the tensor cores,
                          see h64_dtype); TPS_F32: mixed precision -- a first phase runs the H
                          mode products in FP32 until every pair's residual is below

@@ -866,9 +866,10 @@ int tps_apply_prec(tps_ctx *ctx, const void *r_dev, void *out_dev, int nvec, dou
       (nvec > 0 && (!r_dev || !out_dev)) || !std::isfinite(theta))
     return set_error(ctx, TPS_ERR_INVALID_ARG, "bad apply_prec arguments");
   if (dtype == TPS_TF32_TC) {
-    if (ctx->full.nmodes != 2 || ctx->grid_kind != 0)
+    if (!tf_prec_supported(ctx->full) || ctx->grid_kind != 0)
       return set_error(ctx, TPS_ERR_INVALID_ARG,
-                       "the TF32 tensor-core preconditioner needs a 1D Fourier grid");
+                       "the TF32 tensor-core preconditioner needs a Fourier grid (2D: every "
+                       "mode 4 to 128 points, a multiple of 4)");
     st = ensure_tf_operator(ctx->full);
     if (st) return set_error(ctx, st, "building the TF32 preconditioner operator failed");
   }

@@ -4,6 +4,7 @@
 // elementwise helpers (the small eigensolver is in rr_eigh.cu).  Everything stays on the device; the host only
 // reads a few scalars per outer iteration to steer the loop.
 #include <cstring>
+#include <mutex>
 #include <utility>
 
 #include "pdl.cuh"
@@ -111,9 +112,11 @@ k_gram(const double *__restrict__ A, long long lda, long long bsa, int p,
   if (r < r1) {
     T a[BP], b[BQ];
 #pragma unroll
-    for (int i = 0; i < BP; ++i) a[i] = (i0 + i < p) ? (T)As[(long long)(i0 + i) * lda + r] : T(0);
+    for (int i = 0; i < BP; ++i)
+      a[i] = (i0 + i < p) ? (T)As[(long long)(i0 + i) * lda + r] : T(0);
 #pragma unroll
-    for (int j = 0; j < BQ; ++j) b[j] = (j0 + j < q) ? (T)Bs[(long long)(j0 + j) * ldb + r] : T(0);
+    for (int j = 0; j < BQ; ++j)
+      b[j] = (j0 + j < q) ? (T)Bs[(long long)(j0 + j) * ldb + r] : T(0);
 #pragma unroll
     for (int i = 0; i < BP; ++i)
 #pragma unroll
@@ -172,8 +175,11 @@ int gram_chunks(long long nrows, int batch, int npb) {
 
 // ------------------------------- update --------------------------------------
 // C_s[:, j0:j0+BQ] = beta*C_s + alpha * A_s Y_s[:, j0:j0+BQ]; BQ fits q (1, 2, 4 or 8), so
-// narrow updates do not pay for FMAs on padding columns.  T = float: FP32 products and
-// sums on the FP64 data (the low-precision variant), the beta combination in FP64.
+// narrow updates do not pay for FMAs on padding columns, and a column block reads A once.
+// T = float: FP32 products and sums on the FP64 data (the low-precision variant), the beta
+// combination in FP64.  A grid of at most one wave of CTAs strides over the rows, two
+// rows and four columns of A per thread in flight (a CTA per 256 rows spent most of its
+// life loading Y).
 template <typename T, int BQ>
 __global__ void __launch_bounds__(GT)
 k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
@@ -190,34 +196,47 @@ k_update(const double *__restrict__ A, long long lda, long long bsa, int p,
     Ys[i][j] = (j0 + j < q) ? (T)(alpha * Y[s * bsy + (long long)(j0 + j) * ldy + i]) : T(0);
   }
   __syncthreads();
-  const long long r = blockIdx.x * (long long)GT + threadIdx.x;
-  if (r >= nrows) return;
   const double *As = A + s * bsa;
-  T acc[BQ];
-#pragma unroll
-  for (int j = 0; j < BQ; ++j) acc[j] = T(0);
-  // four loads of A in flight before the FMAs that use them
-  int i = 0;
-  for (; i + 4 <= p; i += 4) {
-    T a[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] = (T)As[(long long)(i + u) * lda + r];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < BQ; ++j) acc[j] = fma(a[u], Ys[i + u][j], acc[j]);
-  }
-  for (; i < p; ++i) {
-    const T a = (T)As[(long long)i * lda + r];
-#pragma unroll
-    for (int j = 0; j < BQ; ++j) acc[j] = fma(a, Ys[i][j], acc[j]);
-  }
   double *Cs = C + s * bsc;
+  const long long stride = (long long)gridDim.x * GT;
+  for (long long r0 = (long long)blockIdx.x * GT + threadIdx.x; r0 < nrows; r0 += 2 * stride) {
+    const long long r1 = r0 + stride;
+    const bool v1 = r1 < nrows;
+    T acc0[BQ], acc1[BQ];
 #pragma unroll
-  for (int j = 0; j < BQ; ++j) {
-    if (j0 + j >= q) break;
-    double *dst = Cs + (long long)(j0 + j) * ldc + r;
-    *dst = (beta == 0.0) ? (double)acc[j] : fma(beta, *dst, (double)acc[j]);
+    for (int j = 0; j < BQ; ++j) acc0[j] = acc1[j] = T(0);
+    int i = 0;
+    for (; i + 4 <= p; i += 4) {
+      T a0[4], a1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a0[u] = (T)As[(long long)(i + u) * lda + r0];
+        a1[u] = v1 ? (T)As[(long long)(i + u) * lda + r1] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < BQ; ++j) {
+          acc0[j] = fma(a0[u], Ys[i + u][j], acc0[j]);
+          acc1[j] = fma(a1[u], Ys[i + u][j], acc1[j]);
+        }
+    }
+    for (; i < p; ++i) {
+      const T a0 = (T)As[(long long)i * lda + r0];
+      const T a1 = v1 ? (T)As[(long long)i * lda + r1] : T(0);
+#pragma unroll
+      for (int j = 0; j < BQ; ++j) {
+        acc0[j] = fma(a0, Ys[i][j], acc0[j]);
+        acc1[j] = fma(a1, Ys[i][j], acc1[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BQ; ++j) {
+      if (j0 + j >= q) break;
+      double *dst = Cs + (long long)(j0 + j) * ldc;
+      dst[r0] = (beta == 0.0) ? (double)acc0[j] : fma(beta, dst[r0], (double)acc0[j]);
+      if (v1) dst[r1] = (beta == 0.0) ? (double)acc1[j] : fma(beta, dst[r1], (double)acc1[j]);
+    }
   }
 }
 
@@ -619,6 +638,26 @@ void launch_gram(const double *A, long long lda, long long bsa, int p, const dou
 #undef TPS_GRAM
 }
 
+// Resident CTAs per SM of k_update<T, BQ> (queried once per instantiation).
+int update_occupancy(bool low, int BQ) {
+  static int occ[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const void *fn[2][4] = {{(const void *)k_update<double, 1>, (const void *)k_update<double, 2>,
+                             (const void *)k_update<double, 4>, (const void *)k_update<double, 8>},
+                            {(const void *)k_update<float, 1>, (const void *)k_update<float, 2>,
+                             (const void *)k_update<float, 4>, (const void *)k_update<float, 8>}};
+    for (int t = 0; t < 2; ++t)
+      for (int b = 0; b < 4; ++b) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[t][b], GT, 0) != cudaSuccess)
+          n = 2;
+        occ[t][b] = n < 1 ? 1 : n;
+      }
+  });
+  return occ[low ? 1 : 0][BQ == 1 ? 0 : (BQ == 2 ? 1 : (BQ == 4 ? 2 : 3))];
+}
+
 void launch_update(const double *A, long long lda, long long bsa, int p, const double *Y, int ldy,
                    long long bsy, int q, double alpha, double beta, double *C, long long ldc,
                    long long bsc, long long nrows, int batch, cudaStream_t s, const int *need,
@@ -633,11 +672,18 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
     }
     return;
   }
-  const int BQ = q >= 8 ? 8 : (q >= 4 ? 4 : (q >= 2 ? 2 : 1));
+  const int BQ = q > 4 ? 8 : (q > 2 ? 4 : q);
+  const int zb = (q + BQ - 1) / BQ;
+  // one wave: as many CTAs as fit on the SMs at once (over all systems and column blocks),
+  // each striding over the rows
+  const int occ = update_occupancy(low, BQ);
+  long long gx = (nrows + GT - 1) / GT;
+  const long long wave = std::max(1LL, 152LL * occ / ((long long)batch * zb));
+  if (gx > 16 * wave) gx = wave;  // short inputs keep a CTA per 256 rows, one row per thread
   // p is processed in slabs of 64 rows of Y; the first slab applies beta
   for (int i0 = 0; i0 < p; i0 += 64) {
     const int pp = p - i0 < 64 ? p - i0 : 64;
-    dim3 grid((unsigned)((nrows + GT - 1) / GT), batch, (q + BQ - 1) / BQ);
+    dim3 grid((unsigned)gx, batch, zb);
     const double bt = i0 == 0 ? beta : 1.0;
     const double *Ai = A + (long long)i0 * lda;
     count_launch();

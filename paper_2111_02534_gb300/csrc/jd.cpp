@@ -587,10 +587,11 @@ int solve_impl(tps_ctx *ctx, int k, int parity, double tol, int block, const dou
       tl_split_grams = false;
     }
   } solve_scope(&w.tm, opts.update_dtype == TPS_F64_TC, opts.gram_dtype == TPS_F64_TC);
-  // the TF32 tensor-core preconditioner exists for the 1D operator; 2D solves use FP32
+  // the TF32 tensor-core preconditioner: 1D, and 2D grids whose modes it takes (else FP32)
   w.prec_dtype = opts.prec_dtype == TPS_F64
                      ? TPS_F64
-                     : ((opts.prec_dtype == TPS_TF32_TC && op.nmodes == 2) ? TPS_TF32_TC : TPS_F32);
+                     : ((opts.prec_dtype == TPS_TF32_TC && tf_prec_supported(op)) ? TPS_TF32_TC
+                                                                                 : TPS_F32);
   w.corr_low = opts.correction_dtype != TPS_F64;
   if (w.prec_dtype == TPS_TF32_TC) {
     const int st_tf = ensure_tf_operator(op);  // allocation errors here, not mid-solve
@@ -1077,7 +1078,8 @@ int solve_graph_impl(tps_ctx *ctx, int k_req, int parity, double tol,
   Ctx c{ctx, op, w, s, N};
   w.tm.reset(false);
   w.prec_dtype = opts.prec_dtype == TPS_F64 ? TPS_F64
-                 : (opts.prec_dtype == TPS_TF32_TC && op.nmodes == 2) ? TPS_TF32_TC : TPS_F32;
+                 : (opts.prec_dtype == TPS_TF32_TC && tf_prec_supported(op)) ? TPS_TF32_TC
+                                                                             : TPS_F32;
   w.corr_low = opts.correction_dtype != TPS_F64;
   w.h64_dtype = (opts.h64_dtype == TPS_F64_TC && op.nmodes == 2) ? TPS_F64_TC : TPS_F64;
   if (w.prec_dtype == TPS_TF32_TC) {
@@ -1551,7 +1553,7 @@ void tps_default_opts(tps_solver_opts *o) {
   o->seed = 12345;
   o->guard = 2;
   o->smooth_start = 2;
-  o->prec_dtype = TPS_TF32_TC;  // 1D; 2D solves use TPS_F32
+  o->prec_dtype = TPS_TF32_TC;  // TPS_F32 on 2D grids the TF32 passes do not take
   o->correction_dtype = TPS_F32;
   o->update_dtype = TPS_F64_TC;
   o->gram_dtype = TPS_F64_TC;

@@ -14,6 +14,7 @@
 // multiples of 16 bytes; padding is never read (the tensor maps stop at the true K).
 #include <mutex>
 
+#include "fp_convert.cuh"
 #include "ozaki_tc.cuh"
 #include "pdl.cuh"
 #include "tps_internal.h"
@@ -26,12 +27,26 @@ namespace {
 // 128 columns keep each MMA useful, while a pass, a short K loop per CTA, is latency-bound
 // and gets faster when its tiles fill one wave on the SMs.
 constexpr int kBM = 128, kBNMax = 128, kBK = 32;  // K block: 32 FP32 = one 128-byte row
-constexpr int kStages = 6;
 constexpr int kThreads = 128;
 constexpr uint32_t kATile = kBM * kBK * 4;        // 16 KB
-constexpr uint32_t kBTileMax = kBNMax * kBK * 4;  // 16 KB
-constexpr int kTmemCols = 256;
-constexpr size_t kSmemBytes = 1024 + kStages * (kATile + kBTileMax) + 256;
+
+// Pipeline depth, widest tile, tensor-memory columns and resident CTAs per SM of a pass.
+// kIntCvt: the FP64 output's conversions on the integer pipes (fp_convert.cuh), which pays
+// in the streaming 2D passes and costs latency in the short 1D ones.
+template <int STAGES, int BNMAX, int TMEMC, int MINB, bool INTCVT>
+struct TfCfg {
+  static constexpr int kStages = STAGES, kBNMax = BNMAX, kTmemCols = TMEMC, kMinBlocks = MINB;
+  static constexpr bool kIntCvt = INTCVT;
+  static constexpr uint32_t kBTile = (uint32_t)BNMAX * kBK * 4;
+  static constexpr size_t kSmem = 1024 + (size_t)STAGES * (kATile + kBTile) + 256;
+  static_assert(BNMAX <= TMEMC && MINB * TMEMC <= 512, "tensor memory of the resident CTAs");
+};
+// 1D passes: K up to the grid size (a deep ring), tiles up to 128 columns, one CTA per SM
+using Cfg1 = TfCfg<6, kBNMax, 256, 1, false>;
+// 2D passes: K <= 128 (at most four K blocks) and tiles up to 64 columns; four CTAs per SM
+// (50 KB of shared memory and 64 tensor-memory columns each) keep four tiles' loads and
+// epilogues in flight, the latency a one-CTA pass of short tiles waits on
+using Cfg2 = TfCfg<2, 64, 64, 4, true>;
 
 struct TfArgs {
   int M, N, K;
@@ -93,9 +108,20 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
 // Launched as a dependent of the previous pass: the set-up and the loads of the B operand
 // (the constant eigenbases) run before pdl_wait, the A operand (the previous pass's
 // output) is loaded and the output written after it.
-__global__ void __launch_bounds__(kThreads, 1)
+template <class Cfg>
+__device__ __forceinline__ double out_f64(float v) {
+  if constexpr (Cfg::kIntCvt)
+    return f64_of_f32(v);
+  else
+    return (double)v;
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks)
 k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const TfArgs g) {
+  constexpr int kStages = Cfg::kStages;
+  constexpr uint32_t kBTileMax = Cfg::kBTile;
   extern __shared__ uint8_t smem_raw[];
   __shared__ int abort_flag;
   uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -124,7 +150,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     tc::prefetch_tmap(&tmA);
     tc::prefetch_tmap(&tmB);
   }
-  if (warp == 2) tc::tmem_alloc(holder, kTmemCols);
+  if (warp == 2) tc::tmem_alloc(holder, Cfg::kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -203,7 +229,11 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const float lr = (g.epi == 1 && mvalid) ? g.lamR[r] - sig : 0.f;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
     // contiguous rows (os_n = 1) are written 16 bytes at a time when aligned
-    const bool vec = g.os_n == 1 && ((g.epi == 2) ? (rowoff & 1) == 0 : (rowoff & 3) == 0);
+    const bool vec =
+        g.os_n == 1 && ((g.epi == 2) ? ((rowoff & 1) == 0 &&
+                                        (reinterpret_cast<uintptr_t>(g.out64) & 15) == 0)
+                                     : ((rowoff & 3) == 0 &&
+                                        (reinterpret_cast<uintptr_t>(g.out32) & 15) == 0));
     for (int c = 0; c < BN; c += 32) {
       uint32_t d[32];
       tmem_ld_x32(trow + (uint32_t)c, d);
@@ -221,7 +251,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (g.epi == 2) {
           double2 *o = reinterpret_cast<double2 *>(g.out64 + rowoff + nb);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) o[q] = make_double2((double)val[2 * q], (double)val[2 * q + 1]);
+          for (int q = 0; q < 16; ++q) o[q] = make_double2(out_f64<Cfg>(val[2 * q]), out_f64<Cfg>(val[2 * q + 1]));
         } else {
           float4 *o = reinterpret_cast<float4 *>(g.out32 + rowoff + nb);
 #pragma unroll
@@ -235,7 +265,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           if (q >= lim || n >= g.N) break;
           const long long idx = rowoff + (long long)n * g.os_n;
           if (g.epi == 2)
-            g.out64[idx] = (double)val[q];
+            g.out64[idx] = out_f64<Cfg>(val[q]);
           else
             g.out32[idx] = val[q];
         }
@@ -244,7 +274,7 @@ k_tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 2) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 2) tc::tmem_dealloc(tmem, Cfg::kTmemCols);
 }
 
 // FP64 [rows][cols] -> FP32 [rows][ld] (ld >= cols; padding left as is): block b takes rows
@@ -266,12 +296,48 @@ __global__ void k_to_f32_rows(const double *__restrict__ x, float *__restrict__ 
   }
 }
 
+// y[i] = x[i], FP64 -> FP32, i < n (contiguous rows, ld = cols), grid-strided: two values
+// per thread and step when x and y are 16- and 8-byte aligned (VEC), else one
+template <bool VEC>
+__global__ void k_to_f32_flat(const double *__restrict__ x, float *__restrict__ y, long long n) {
+  if (threadIdx.x == 0) pdl_trigger();  // pass 1 may be scheduled (it waits for this grid)
+  if (!VEC) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      y[i] = f32_of_f64(x[i]);
+    return;
+  }
+  const long long n2 = n >> 1;
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  float2 *y2 = reinterpret_cast<float2 *>(y);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x2[i];
+    y2[i] = make_float2(f32_of_f64(v.x), f32_of_f64(v.y));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) y[n - 1] = f32_of_f64(x[n - 1]);
+}
+
 // dst[r][c] = src[r][c] (or src[c][r] when transposed), rows x cols, ld padded, FP32
 __global__ void k_pad_copy(const float *__restrict__ src, int rows, int cols, int transpose,
                            float *__restrict__ dst, int ld) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * ld; e += gridDim.x * blockDim.x) {
     const int r = e / ld, c = e - (e / ld) * ld;
     dst[e] = c < cols ? (transpose ? src[(long long)c * rows + r] : src[(long long)r * cols + c]) : 0.f;
+  }
+}
+
+// out[(i1 n2 + i2) n3 + i3] = l1[i1] + l2[i2] + l3[i3]: the eigenvalue sums of three modes
+// over the rows of the 2D preconditioner's dividing pass
+__global__ void k_lam_sum3(const float *__restrict__ l1, const float *__restrict__ l2,
+                           const float *__restrict__ l3, int n1, int n2, int n3,
+                           float *__restrict__ out) {
+  const long long total = (long long)n1 * n2 * n3;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i3 = (int)(e % n3);
+    const long long r = e / n3;
+    out[e] = l1[r / n2] + l2[r % n2] + l3[i3];
   }
 }
 
@@ -326,17 +392,18 @@ int tile_n(int N, int mtiles) {
   return (bn + 15) & ~15;
 }
 
-std::once_flag g_attr_once;
-
+template <class Cfg>
 void launch_tf32_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const TfArgs &g,
                       cudaStream_t s) {
-  std::call_once(g_attr_once, [] {
-    cudaFuncSetAttribute(k_tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_tf32_gemm<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Cfg::kSmem);
   });
   count_launch();
-  launch_pdl(k_tf32_gemm,
+  launch_pdl(k_tf32_gemm<Cfg>,
              dim3((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + g.BN - 1) / g.BN)),
-             dim3(kThreads), kSmemBytes, s, ta, tb, g);
+             dim3(kThreads), Cfg::kSmem, s, ta, tb, g);
 }
 
 }  // namespace
@@ -352,17 +419,69 @@ struct TfOperator {
   const void *ws0 = nullptr, *ws1 = nullptr;
   long long wscap = -1;
   CUtensorMap mA[4];                 // A operands of passes 1 .. 4
+  // 2D: per mode k the tile width and the B operands S_k^T (forward) and S_k (backward)
+  // over the FP32 eigenbases themselves (n_k is a multiple of 4, so rows need no padding);
+  // mA4[k] the input of the passes that contract mode k; lamR the sums of the eigenvalues
+  // of modes 1, 2, 3 over the rows of the dividing pass
+  bool two_d = false;
+  int n4[4] = {0, 0, 0, 0}, BN4[4] = {0, 0, 0, 0};
+  float *lamR = nullptr;
+  CUtensorMap mST4[4], mS4[4], mA4[4];
 };
 
 void free_tf_operator(TfOperator *t) {
   if (!t) return;
   cudaFree(t->Sx);
+  cudaFree(t->lamR);
   cudaFree(t->err);
   delete t;
 }
 
+bool tf_prec_supported(const DevOperator &op) {
+  if (op.nmodes == 2) return true;
+  if (op.nmodes != 4) return false;
+  for (int k = 0; k < 4; ++k)
+    if (op.n[k] < 4 || op.n[k] > 128 || op.n[k] % 4 != 0) return false;
+  return true;
+}
+
+// 2D: every mode 4 .. 128 points, a multiple of 4 (TMA rows of 16 bytes)
+int ensure_tf_operator_2d(const DevOperator &op) {
+  TfOperator *t = new TfOperator();
+  t->two_d = true;
+  bool ok = true;
+  for (int k = 0; k < 4; ++k) {
+    const int n = op.n[k];
+    if (n < 4 || n > 128 || n % 4 != 0) {
+      delete t;
+      return TPS_ERR_INVALID_ARG;
+    }
+    t->n4[k] = n;
+    const int tiles = (n + Cfg2::kBNMax - 1) / Cfg2::kBNMax;
+    t->BN4[k] = (((n + tiles - 1) / tiles) + 15) & ~15;
+    ok = ok && make_f32_map(&t->mST4[k], op.STf[k], n, n, n, t->BN4[k]) &&
+         make_f32_map(&t->mS4[k], op.Sf[k], n, n, n, t->BN4[k]);
+  }
+  const long long nr = (long long)op.n[1] * op.n[2] * op.n[3];
+  if (!ok || cudaMalloc((void **)&t->lamR, nr * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void **)&t->err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) {
+    free_tf_operator(t);
+    return ok ? TPS_ERR_NOMEM : TPS_ERR_INVALID_ARG;
+  }
+  k_lam_sum3<<<256, 256>>>(op.lamf[1], op.lamf[2], op.lamf[3], op.n[1], op.n[2], op.n[3],
+                           t->lamR);
+  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    free_tf_operator(t);
+    return TPS_ERR_CUDA;
+  }
+  op.tf = t;
+  return TPS_OK;
+}
+
 int ensure_tf_operator(const DevOperator &op) {
   if (op.tf) return TPS_OK;
+  if (op.nmodes == 4) return ensure_tf_operator_2d(op);
   if (op.nmodes != 2) return TPS_ERR_INVALID_ARG;
   TfOperator *t = new TfOperator();
   t->nx = op.n[0];
@@ -401,9 +520,73 @@ int ensure_tf_operator(const DevOperator &op) {
 }
 
 long long tf_prec_workspace_floats(const DevOperator &op, int nvec) {
+  if (op.nmodes == 4) return (long long)nvec * op.N;
   const long long a = (long long)nvec * op.n[0] * pad4(op.n[1]);
   const long long b = (long long)nvec * op.n[1] * pad4(op.n[0]);
   return a > b ? a : b;
+}
+
+// 2D (four modes a, b, c, d = x1, x2, y1, y2; C order, d fastest): eight passes, each
+// contracting the last index of its input and storing its output index first, so the
+// indices rotate by one per pass and every pass reads its contraction index contiguously:
+//   X[a][b][c][d] -> T1[j_d][a][b][c] -> T2[j_c][j_d][a][b] -> T3[j_b][j_c][j_d][a]
+//   -> T4[j_a][j_b][j_c][j_d] divided by lambda_a + lambda_b + lambda_c + lambda_d - sigma
+// (B = S_k^T: t_j = sum_i x_i S_k[i][j]), then the same four contractions with B = S_k
+// (u_i = sum_j t_j S_k[i][j]), the last one storing FP64 in the original order.  A pass over
+// mode k is C = A B^T with A = nvec N / n_k rows of n_k values; its output element (v, row r,
+// column n) lies at v N + n (N / n_k) + r.
+int launch_apply_prec_tf32_2d(const DevOperator &op, const double *r, double *out, int nvec,
+                              double sigma, ApplyWorkspace &ws, cudaStream_t s,
+                              const double *sigma_dev) {
+  TfOperator *t = op.tf;
+  if (tf_prec_workspace_floats(op, nvec) > 2 * ws.capacity) return TPS_ERR_INVALID_ARG;
+  const long long N = op.N;
+  float *bufA = reinterpret_cast<float *>(ws.t0), *bufB = reinterpret_cast<float *>(ws.t1);
+  // the passes over modes 3 and 1 read bufA, those over modes 2 and 0 read bufB
+  auto inbuf = [&](int k) { return (k & 1) ? bufA : bufB; };
+  if (t->ws0 != ws.t0 || t->ws1 != ws.t1 || t->wscap != ws.capacity) {
+    const long long fl = 2 * ws.capacity;  // floats per buffer
+    for (int k = 0; k < 4; ++k)
+      if (!make_f32_map(&t->mA4[k], inbuf(k), t->n4[k], fl / t->n4[k], t->n4[k], kBM))
+        return TPS_ERR_INVALID_ARG;
+    t->ws0 = ws.t0;
+    t->ws1 = ws.t1;
+    t->wscap = ws.capacity;
+  }
+  {
+    // the rows (n_3 values, a multiple of 4) need no padding: one flat conversion
+    const long long n = (long long)nvec * N;
+    long long blocks = (n / 2 + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    count_launch();
+    if ((reinterpret_cast<uintptr_t>(r) & 15) == 0 && (reinterpret_cast<uintptr_t>(bufA) & 7) == 0)
+      k_to_f32_flat<true><<<(unsigned)blocks, 256, 0, s>>>(r, bufA, n);
+    else
+      k_to_f32_flat<false><<<(unsigned)blocks, 256, 0, s>>>(r, bufA, n);
+  }
+  TfArgs g{};
+  g.err = t->err;
+  g.sigma = (float)sigma;
+  g.sigma_dev = sigma_dev;
+  g.os_v = N;
+  g.os_r = 1;
+  for (int pass = 0; pass < 8; ++pass) {
+    const int k = 3 - (pass & 3);
+    const int n = t->n4[k];
+    g.M = (int)((long long)nvec * (N / n));
+    g.N = n;
+    g.K = n;
+    g.R = (int)(N / n);
+    g.BN = t->BN4[k];
+    g.os_n = N / n;
+    g.epi = pass == 3 ? 1 : (pass == 7 ? 2 : 0);
+    g.out32 = (k & 1) ? bufB : bufA;  // the next pass's input
+    g.out64 = out;
+    g.lamR = t->lamR;
+    g.lamN = op.lamf[0];
+    launch_tf32_gemm<Cfg2>(t->mA4[k], pass < 4 ? t->mST4[k] : t->mS4[k], g, s);
+  }
+  return TPS_OK;
 }
 
 int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, int nvec,
@@ -411,6 +594,8 @@ int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, 
                            const double *sigma_dev) {
   if (nvec <= 0) return TPS_OK;
   TfOperator *t = op.tf;
+  if (t && t->two_d && op.nmodes == 4)
+    return launch_apply_prec_tf32_2d(op, r, out, nvec, sigma, ws, s, sigma_dev);
   if (!t || op.nmodes != 2) return TPS_ERR_INVALID_ARG;
   if (tf_prec_workspace_floats(op, nvec) > 2 * ws.capacity) return TPS_ERR_INVALID_ARG;
   const int nx = t->nx, ny = t->ny, XP = t->XP, YP = t->YP;
@@ -440,22 +625,22 @@ int launch_apply_prec_tf32(const DevOperator &op, const double *r, double *out, 
   g.M = nvec * nx; g.N = ny; g.K = ny; g.R = nx; g.BN = t->BNy;
   g.os_v = (long long)ny * XP; g.os_r = 1; g.os_n = XP;
   g.out32 = bufB; g.epi = 0;
-  launch_tf32_gemm(t->mA[0], t->mSTy, g, s);
+  launch_tf32_gemm<Cfg1>(t->mA[0], t->mSTy, g, s);
   // pass 2: t1T[v][j][i] = sum_x t0T[v][j][x] S_x[x][i] / (lambda_x[i] + lambda_y[j] - sigma)
   g.M = nvec * ny; g.N = nx; g.K = nx; g.R = ny; g.BN = t->BNx;
   g.os_v = (long long)ny * XP; g.os_r = XP; g.os_n = 1;
   g.out32 = bufA; g.epi = 1; g.lamR = op.lamf[1]; g.lamN = op.lamf[0];
-  launch_tf32_gemm(t->mA[1], t->mSTx, g, s);
+  launch_tf32_gemm<Cfg1>(t->mA[1], t->mSTx, g, s);
   // pass 3: t2[v][x][j] = sum_i S_x[x][i] t1T[v][j][i]
   g.M = nvec * ny; g.N = nx; g.K = nx; g.R = ny; g.BN = t->BNx;
   g.os_v = (long long)nx * YP; g.os_r = 1; g.os_n = YP;
   g.out32 = bufB; g.epi = 0;
-  launch_tf32_gemm(t->mA[2], t->mSx, g, s);
+  launch_tf32_gemm<Cfg1>(t->mA[2], t->mSx, g, s);
   // pass 4: out[v][x][y] = sum_j t2[v][x][j] S_y[y][j]
   g.M = nvec * nx; g.N = ny; g.K = ny; g.R = nx; g.BN = t->BNy;
   g.os_v = (long long)nx * ny; g.os_r = ny; g.os_n = 1;
   g.out64 = out; g.epi = 2;
-  launch_tf32_gemm(t->mA[3], t->mSy, g, s);
+  launch_tf32_gemm<Cfg1>(t->mA[3], t->mSy, g, s);
   return TPS_OK;
 }
 

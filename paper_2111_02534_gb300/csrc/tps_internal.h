@@ -84,10 +84,12 @@ cudaError_t launch_apply_h_tc(const DevOperator &op, const double *psi, double *
                               const double *theta_dev, double theta, cudaStream_t s);
 cudaError_t ensure_tc_operator(const DevOperator &op, cudaStream_t s);
 void free_tc_operator(struct TcOperator *t);
-// TF32 tensor-core preconditioner (1D): out[v] = (T - sigma)^-1 r[v] with the four mode
-// products in TF32 (FP64 r and out; the FP32 intermediates use the workspace, which must
-// hold tf_prec_workspace_floats / 2 doubles).  ensure_tf_operator builds op.tf (padded
-// eigenbases, synchronous); the launcher returns TPS_ERR_INVALID_ARG without it.
+// TF32 tensor-core preconditioner: out[v] = (T - sigma)^-1 r[v] with the mode products
+// in TF32 (four in 1D, eight in 2D; FP64 r and out; the FP32 intermediates use the
+// workspace, which must hold tf_prec_workspace_floats / 2 doubles).  ensure_tf_operator
+// builds op.tf (padded eigenbases, synchronous); the launcher returns TPS_ERR_INVALID_ARG
+// without it.  tf_prec_supported: 1D, or 2D with every mode 4 .. 128 points, a multiple of 4.
+bool tf_prec_supported(const DevOperator &op);
 void free_tf_operator(struct TfOperator *t);
 int ensure_tf_operator(const DevOperator &op);
 long long tf_prec_workspace_floats(const DevOperator &op, int nvec);

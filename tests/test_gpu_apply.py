@@ -300,10 +300,74 @@ def test_apply_prec_1d_tf32_full_size():
     ctx.close()
 
 
-def test_apply_prec_tf32_rejects_2d():
+# 2D: eight TF32 mode products, each off by at most ~2 * 2^-10 relative in norm for the
+# orthogonal eigenbases: 1.6e-2 together, bar 2e-2.
+TF32_TOL_2D = 2e-2
+
+
+@pytest.mark.parametrize("n,nvec,theta", [((8, 8, 4, 4), 3, -0.4), ((4, 4, 12, 12), 2, -0.1),
+                                          ((12, 12, 4, 4), 5, -1.0), ((8, 8, 8, 8), 1, -0.3),
+                                          ((16, 16, 4, 4), 2, -0.6)])
+def test_apply_prec_2d_tf32(n, nvec, theta):
+    # Eq. sylvester_equation over four modes on the tensor cores, against the oracle's dense
+    # solve of (T - theta) w = r: K below one 32-wide block (4, 8, 12) and above it (16), rows
+    # of a pass ragged against the 128-row tiles, tiles spanning several vectors
     require_gpu()
     tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
-    ctx = make_ctx_2d(20.0, 1.0, (8, 8, 8, 8), (5.0,) * 4, 1.0, 1.0)
+    L = (4.0, 4.0, 3.0, 3.0)
+    P = problem_2d(20.0, 1.0, 1.0, n, L, 2.0, 1.0)
+    ctx = make_ctx_2d(20.0, 1.0, n, L, 2.0, 1.0)
+    r = random_block(nvec, P.N, seed=nvec + 21)
+    out = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(dev(r), out, theta, dtype=tps.TF32_TC)
+    ctx.device_status()
+    got = host(out)
+    ref = apply_dense(P, r, theta)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= TF32_TOL_2D, err.max()
+    assert err.max() > 1e-7           # it really ran in TF32
+    out2 = torch.empty_like(out)
+    ctx.apply_prec(dev(r), out2, theta, dtype=tps.TF32_TC)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["long_modes", "full_size"])
+def test_apply_prec_2d_tf32_large(which):
+    # 128-point modes (four K blocks, two 64-wide tiles per pass) and the 48^4 workload:
+    # the FP64 preconditioner's result, pinned here by the oracle's kinetic residual, is the
+    # reference for the TF32 one
+    require_gpu()
+    tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
+    if which == "long_modes":
+        n, L, M, v0, sg, theta, nvec = (128, 128, 4, 4), (8.0, 8.0, 3.0, 3.0), 20.0, 2.0, 1.0, -0.2, 3
+        P = problem_2d(M, 1.0, 1.0, n, L, v0, sg)
+        ctx = make_ctx_2d(M, 1.0, n, L, v0, sg)
+    else:
+        w = WORKLOADS["2d_n48"]
+        theta, nvec = -0.3, 8
+        P = problem_2d(w.M, w.m, w.hbar, w.n, w.L, w.v0, w.sigma)
+        ctx = make_ctx_2d(w.M, w.m, w.n, w.L, w.v0, w.sigma)
+    r = random_block(nvec, P.N, seed=17)
+    a = torch.empty(nvec, P.N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    ctx.apply_prec(dev(r), a, theta, dtype=tps.F64)
+    ctx.apply_prec(dev(r), b, theta, dtype=tps.TF32_TC)
+    ctx.device_status()
+    ha = host(a)
+    assert kinetic_residual(P, ha[:2], r[:2], theta) <= 1e-10
+    err = np.linalg.norm(host(b) - ha, axis=1) / np.linalg.norm(ha, axis=1)
+    assert err.max() <= TF32_TOL_2D, err.max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [(6, 6, 8, 8), (8, 8, 6, 6), (132, 132, 4, 4)])
+def test_apply_prec_tf32_rejects_2d_modes(n):
+    # the 2D TF32 passes need every mode 4 .. 128 points, a multiple of 4
+    require_gpu()
+    tps = __import__("paper_2111_02534_gb300.tps", fromlist=["tps"])
+    ctx = make_ctx_2d(20.0, 1.0, n, (5.0,) * 4, 1.0, 1.0)
     N = ctx.info()[0]
     x = torch.ones(1, N, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)

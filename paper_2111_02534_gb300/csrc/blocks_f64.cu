@@ -677,9 +677,9 @@ void launch_update(const double *A, long long lda, long long bsa, int p, const d
   // one wave: as many CTAs as fit on the SMs at once (over all systems and column blocks),
   // each striding over the rows
   const int occ = update_occupancy(low, BQ);
-  long long gx = (nrows + GT - 1) / GT;
+  long long gx = (nrows + 2 * GT - 1) / (2 * GT);
   const long long wave = std::max(1LL, 152LL * occ / ((long long)batch * zb));
-  if (gx > 16 * wave) gx = wave;  // short inputs keep a CTA per 256 rows, one row per thread
+  if (gx > 8 * wave) gx = wave;  // short inputs keep a CTA per 512 rows
   // p is processed in slabs of 64 rows of Y; the first slab applies beta
   for (int i0 = 0; i0 < p; i0 += 64) {
     const int pp = p - i0 < 64 ? p - i0 : 64;

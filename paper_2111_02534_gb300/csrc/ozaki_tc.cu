@@ -378,6 +378,7 @@ struct OzArgs {
   const double *theta_dev;       // theta_v (null: theta0)
   double theta0;
   int *err;                      // nonzero after a timed-out wait
+  int nvec;                      // vectors (the persistent product's tile count)
 };
 
 // (hi 2^30 + lo) 2^(E - 66) rounded to the nearest FP64 value, |hi|, |lo| < 2^49: as
@@ -658,16 +659,280 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUte
 
 // One product C = A B^T (A = wave-function fiber slices, 7 base-256 digits; B = mode-matrix
 // slices, 8 digits; contraction length <= 128) over tiles m fastest, then n, then the
-// vector: a mode product of the 2D H-apply.
-__global__ void __launch_bounds__(kThreads, 1)
-k_oz_gemm1(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           const __grid_constant__ OzArgs g) {
+// vector: a mode product of the 2D H-apply.  Persistent: one CTA per SM takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... with the three stages of a tile overlapped across tiles.
+// Warp 0 lane 0 streams the slices of tile after tile through the shared-memory rings;
+// warp 1 lane 0 issues a tile's MMAs once the epilogue has released the tensor memory of
+// the previous one; warps 2 .. 9 (two per TMEM lane quarter, each half of the columns)
+// fetch the tile's old output values and exponents while its MMAs run, then drain the
+// accumulators, release the tensor memory (mbarrier tmem_empty, 8 arrivals) and only then
+// store, so that the next tile's MMAs run during the stores.  (A CTA per tile, which ran the
+// loads, the MMAs and the epilogue one after the other, took 9 % longer at 48^4.)
+constexpr int kPEpiWarps = 16;  // four per TMEM lane quarter, a quarter of the columns each
+constexpr int kPThreads = 64 + 32 * kPEpiWarps;
+
+// The persistent kernel's epilogue (warps 2 .. 17): warp w reads TMEM lanes 32 (w % 4) ..
+// + 31 (rows) and the columns of part (w - 2) / 4 of four, base-256 levels (kLevels2).
+// Its per-output work is a chain of dependent integer operations, so it takes four warps
+// per quarter to keep the issue slots busy (with two, a tile took 17.7 us at 21 % issue).  Per tile:
+// the exponents and, for an accumulating store, the old output values are loaded before the
+// accumulators are ready; after the drain the tensor memory is released, then the outputs
+// are stored.
+__device__ __forceinline__ void oz_epilogue_persistent(const OzArgs &g, uint32_t tmem,
+                                                       uint64_t *accum, uint64_t *tmem_empty,
+                                                       const int *abort_flag, long long T,
+                                                       int tm, int tn) {
+  constexpr int L = kLevels2;
+  constexpr int NH = kBN / (kPEpiWarps / 4);  // columns per thread
+  static_assert(NH % 4 == 0, "whole 4-column groups per part");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = (warp - 2) >> 2;  // half: the column part
+  const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+  const long long nstride = g.inner ? g.inner : g.ldo;
+  long long tcount = 0;
+  for (long long t = blockIdx.x; t < T; t += gridDim.x, ++tcount) {
+    __syncwarp();  // the warp-collective loads below start converged
+    const int v = (int)(t / ((long long)tm * tn)), r = (int)(t % ((long long)tm * tn));
+    const int m0 = (r % tm) * kBM, n0 = (r / tm) * kBN;
+    const int m = m0 + 32 * quarter + lane;
+    const bool mvalid = m < g.M;
+    const long long mbase = g.inner ? (long long)(m / g.inner) * g.outer + m % g.inner : m;
+    const int nb = n0 + half * NH;
+    // while the tile's MMAs run: the row exponent, and the values an accumulating store
+    // adds to
+    const int Em = mvalid ? (int)g.expA[v * g.expA_bs + m] - 1022 : 0;
+    double acc[NH];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) {
+      const int n = nb + q;
+      acc[q] = (g.epi == 1 && mvalid && n < g.N)
+                   ? g.out[v * g.out_bs + mbase + (long long)n * nstride]
+                   : 0.0;
+    }
+    bool ok = tc::mbar_wait(accum, (uint32_t)(tcount & 1), g.err, 5);
+    ok = __all_sync(0xffffffffu, ok);
+    const int aborted = __shfl_sync(0xffffffffu, *((const volatile int *)abort_flag), 0);
+    if (!ok || aborted) break;
+    tc::tc_fence_after();
+    // the products, apart from the old values (whose loads may still be in flight), so
+    // that the drain and the release do not wait for them
+    double val[NH];
+    // four columns at a time (eight levels each): wider groups exceed the register budget
+#pragma unroll
+    for (int cc = 0; cc < NH / 4; ++cc) {
+      // the columns' exponents (a few cached values) load under the TMEM reads
+      int En[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int n = nb + cc * 4 + q;
+        En[q] = n < g.N ? (int)g.expB[v * g.expB_bs + n] - 1022 : 0;
+      }
+      uint32_t rr[L][4];
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+        tc::tmem_ld_x4(trow + (uint32_t)(l * kBN + half * NH + cc * 4), rr[l]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int d[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) d[l] = __float2int_rn(__uint_as_float(rr[l][q]));
+        // (hi 2^32 + lo) 2^(Em + En - 69): levels 0..3 and 4..7 in base 256
+        const long long hi = (((long long)d[0] * 256 + d[1]) * 256 + d[2]) * 256 + d[3];
+        const long long lo = (((long long)d[4] * 256 + d[5]) * 256 + d[6]) * 256 + d[7];
+        val[cc * 4 + q] = b256::combine(hi, lo, Em + En[q] + 1);
+      }
+    }
+    // the accumulators are read: the next tile's MMAs may overwrite them
+    tc::tc_fence_before();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(tmem_empty);
+    if (!mvalid) continue;
+    if (g.epi == 2) {
+      // y2: (V - theta) psi + the product, every load before any store
+      const double th = g.theta_dev ? g.theta_dev[v] : g.theta0;
+#pragma unroll
+      for (int cc = 0; cc < NH / 4; ++cc) {
+        double vv[4], pp[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int n = nb + cc * 4 + q;
+          const long long idx = mbase + (long long)(n < g.N ? n : n0) * nstride;
+          vv[q] = n < g.N ? g.V[idx] : 0.0;
+          pp[q] = n < g.N ? g.psi[v * g.out_bs + idx] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int n = nb + cc * 4 + q;
+          if (n < g.N)
+            g.out[v * g.out_bs + mbase + (long long)n * nstride] =
+                fma(vv[q] - th, pp[q], val[cc * 4 + q]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        const int n = nb + q;
+        if (n < g.N) g.out[v * g.out_bs + mbase + (long long)n * nstride] = acc[q] + val[q];
+      }
+    }
+  }
+}
+
+// registers are reserved per group of four warps: 18 warps take 20 warps' worth
+__global__ void __launch_bounds__(kPThreads, 1)
+k_oz_gemm1p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ OzArgs g) {
+  constexpr int SA = kPsiSlices2, SB = kOpSlices2, L = kLevels2;
   extern __shared__ uint8_t smem_raw[];
+  __shared__ int abort_flag;
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t bstage = (uint32_t)SB * b_slice_bytes();
+  uint8_t *sB = base;
+  uint8_t *sA = base + kBStages * bstage;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sA + kAStages * kATileBytes);
+  uint64_t *fullA = bars, *emptyA = bars + kAStages;
+  uint64_t *fullB = bars + 2 * kAStages, *emptyB = fullB + kBStages;
+  uint64_t *accum = emptyB + kBStages, *tmem_empty = accum + 1;
+  uint32_t *holder = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tm = (g.M + kBM - 1) / kBM, tn = (g.N + kBN - 1) / kBN;
-  const int r = (int)blockIdx.x;
-  const int v = r / (tm * tn), t = r % (tm * tn);
-  const int m0 = (t % tm) * kBM, n0 = (t / tm) * kBN;
-  oz_tile<kPsiSlices2, kOpSlices2, kLevels2>(&tmA, &tmB, g, m0, n0, v, smem_raw);
+  const long long T = (long long)tm * tn * g.nvec;
+  const int KB = (g.K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kAStages; ++i) {
+      tc::mbar_init(&fullA[i], 1);
+      tc::mbar_init(&emptyA[i], 1);
+    }
+    for (int i = 0; i < kBStages; ++i) {
+      tc::mbar_init(&fullB[i], 1);
+      tc::mbar_init(&emptyB[i], 1);
+    }
+    tc::mbar_init(accum, 1);
+    tc::mbar_init(tmem_empty, kPEpiWarps);
+    abort_flag = 0;
+    tc::fence_barrier_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) tc::tmem_alloc(holder, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: per tile and K block, the B slices (one stage), then the A slices
+      int lastA[kAStages], lastB[kBStages];
+      for (int i = 0; i < kAStages; ++i) lastA[i] = -1;
+      for (int i = 0; i < kBStages; ++i) lastB[i] = -1;
+      bool ok = true;
+      long long acount = 0, bcount = 0;
+      for (long long t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        const int v = (int)(t / ((long long)tm * tn)), r = (int)(t % ((long long)tm * tn));
+        const int m0 = (r % tm) * kBM, n0 = (r / tm) * kBN;
+        for (int kb = 0; kb < KB && ok; ++kb, ++bcount) {
+          const int sb = (int)(bcount % kBStages);
+          const uint32_t rb = (uint32_t)(bcount / kBStages);
+          if (!tc::mbar_wait(&emptyB[sb], (rb & 1u) ^ 1u, g.err, 1)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&fullB[sb], bstage);
+          for (int j = 0; j < SB; ++j)
+            tc::tma_load_3d(sB + sb * bstage + j * b_slice_bytes(), &tmB, &fullB[sb], kb * kBK,
+                            n0, v * g.zB + j);
+          lastB[sb] = (int)(rb & 1u);
+          for (int i = 0; i < SA; ++i, ++acount) {
+            const int sa = (int)(acount % kAStages);
+            const uint32_t ra = (uint32_t)(acount / kAStages);
+            if (!tc::mbar_wait(&emptyA[sa], (ra & 1u) ^ 1u, g.err, 2)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&fullA[sa], kATileBytes);
+            tc::tma_load_3d(sA + sa * kATileBytes, &tmA, &fullA[sa], kb * kBK, m0,
+                            v * g.zA + i);
+            lastA[sa] = (int)(ra & 1u);
+          }
+        }
+      }
+      if (!ok) {
+        // wind down: let every copy this thread started land before the CTA exits
+        atomicExch(&abort_flag, 1);
+        for (int i = 0; i < kAStages; ++i)
+          if (lastA[i] >= 0) tc::mbar_wait(&fullA[i], (uint32_t)lastA[i], nullptr, 0);
+        for (int i = 0; i < kBStages; ++i)
+          if (lastB[i] >= 0) tc::mbar_wait(&fullB[i], (uint32_t)lastB[i], nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: a tile's level l = i + j accumulates at column l * kBN; its first
+      // MMA (K block 0, k-step 0, the level's smallest i) overwrites the previous tile's
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
+      constexpr uint64_t kSliceStep = b_slice_bytes() >> 4;
+      bool ok = true;
+      long long acount = 0, bcount = 0, tcount = 0;
+      for (long long t = blockIdx.x; t < T && ok; t += gridDim.x, ++tcount) {
+        if (tcount > 0 &&
+            !tc::mbar_wait(tmem_empty, (uint32_t)((tcount - 1) & 1), g.err, 6)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        for (int kb = 0; kb < KB && ok; ++kb, ++bcount) {
+          const int sb = (int)(bcount % kBStages);
+          const uint32_t rb = (uint32_t)(bcount / kBStages);
+          if (!tc::mbar_wait(&fullB[sb], rb & 1u, g.err, 3)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint64_t bdesc = tc::smem_desc_sw128(tc::smem_addr(sB + sb * bstage));
+          const bool later = kb > 0;
+#pragma unroll
+          for (int i = 0; i < SA; ++i, ++acount) {
+            const int sa = (int)(acount % kAStages);
+            const uint32_t ra = (uint32_t)(acount / kAStages);
+            if (!tc::mbar_wait(&fullA[sa], ra & 1u, g.err, 4)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const uint64_t adesc = tc::smem_desc_sw128(tc::smem_addr(sA + sa * kATileBytes));
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+              if (i + j < L) {
+                const bool first = i == (i + j >= SB ? i + j - SB + 1 : 0);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                  tc::mma_bf16(tmem + (uint32_t)((i + j) * kBN), adesc + (uint64_t)(2 * kk),
+                               bdesc + (uint64_t)j * kSliceStep + (uint64_t)(2 * kk), idesc,
+                               (later || kk > 0 || !first) ? 1u : 0u);
+              }
+            }
+            tc::mma_commit(&emptyA[sa]);  // the A stage is free once these MMAs are done
+          }
+          if (ok) tc::mma_commit(&emptyB[sb]);
+        }
+        // the tile's accumulators are complete once its MMAs are (after a failure: only so
+        // that nothing is in flight at exit)
+        tc::mma_commit(accum);
+      }
+      if (!ok) atomicExch(&abort_flag, 1);
+    }
+  } else {
+    oz_epilogue_persistent(g, tmem, accum, tmem_empty, &abort_flag, T, tm, tn);
+  }
+  __syncwarp();  // lanes 1 .. 31 of warps 0 and 1 wait for their lane 0
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------ host ------------------------------------
@@ -705,6 +970,9 @@ bool make_slice_map(CUtensorMap *map, const void *base, int cols, int rows, long
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// the persistent 2D product: B stages of kOpSlices2 slices and one more barrier
+size_t ozp_smem_bytes() { return oz_smem_bytes(kOpSlices2) + 8; }
 
 int round8(int n) { return (n + 7) & ~7; }
 
@@ -924,8 +1192,8 @@ cudaError_t launch_apply_h_tc_2d(const DevOperator &op, const double *psi, doubl
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_oz_gemm1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)oz_smem_bytes(kMaxSlices));
+    attr = cudaFuncSetAttribute(k_oz_gemm1p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ozp_smem_bytes());
   });
   if (attr != cudaSuccess) return attr;
   for (int v0 = 0; v0 < nvec; v0 += t.chunk) {
@@ -969,11 +1237,13 @@ cudaError_t launch_apply_h_tc_2d(const DevOperator &op, const double *psi, doubl
       g.theta_dev = theta_dev ? theta_dev + v0 : nullptr;
       g.theta0 = theta;
       g.err = t.err;
+      g.nvec = nv;
       const long long tiles = ((M + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * nv;
       if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
       count_launch();
-      k_oz_gemm1<<<(unsigned)tiles, kThreads, oz_smem_bytes(kMaxSlices), s>>>(t.mF4[k],
-                                                                            t.mK4[k], g);
+      // persistent: one CTA per SM (no more CTAs than tiles)
+      const unsigned grid = (unsigned)(tiles < 152 ? tiles : 152);
+      k_oz_gemm1p<<<grid, kPThreads, ozp_smem_bytes(), s>>>(t.mF4[k], t.mK4[k], g);
       const cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) return le;
     }

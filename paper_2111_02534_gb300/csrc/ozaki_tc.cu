@@ -359,6 +359,42 @@ k_split_fibers(const double *__restrict__ X, long long bs, long long M, int nk, 
   }
 }
 
+// Exponent and digit slices of the rows of a batch of [M][n] matrices (the fibers of the
+// fastest mode of the 2D layout), n <= kMaxFiber, in one pass: a warp per row reads its n
+// values (up to four per lane), takes the raw exponent maximum by a warp reduction, writes
+// it to fexp[v M + m] and the S digit slices to out[((v S + plane) M + m) ld + i].  (The
+// 1D splitter, built for the transposed pair of a 1D vector, needed a separate exponent
+// pass and ran 32-wide tiles half empty on 48-value rows.)
+__global__ void __launch_bounds__(256)
+k_split_rows(const double *__restrict__ X, long long bs, long long M, int n, int nv, int S,
+             unsigned *__restrict__ fexp, uint16_t *__restrict__ out, int ld) {
+  const int lane = threadIdx.x & 31;
+  const long long rows = M * nv;
+  const long long plane = M * ld;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long v = row / M, m = row - v * M;
+    const double *x = X + v * bs + m * n;
+    double val[kMaxFiber / 32];
+    unsigned e = 0;
+#pragma unroll
+    for (int h = 0; h < kMaxFiber / 32; ++h) {
+      const int i = lane + 32 * h;
+      val[h] = i < n ? x[i] : 0.0;
+      const unsigned r = raw_exponent(val[h]);
+      e = r > e ? r : e;
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0) fexp[row] = e;
+    uint16_t *dst = out + (v * S) * plane + m * ld;
+#pragma unroll
+    for (int h = 0; h < kMaxFiber / 32; ++h) {
+      const int i = lane + 32 * h;
+      if (i < n) write_digits(val[h], e, S, dst + i, plane);
+    }
+  }
+}
+
 // ------------------------------ the product kernel ------------------------------
 struct OzArgs {
   int M, N, K;
@@ -1204,10 +1240,11 @@ cudaError_t launch_apply_h_tc_2d(const DevOperator &op, const double *psi, doubl
       const long long M = t.M4[k];
       const int n = t.n4[k];
       if (t.sig4[k] == 1) {  // the fibers are the rows of the [M][n] view
-        const cudaError_t me = cudaMemsetAsync(t.eF, 0, sizeof(unsigned) * nv * M, s);
-        if (me != cudaSuccess) return me;
-        launch_exponents(P, (int)M, n, op.N, nv, t.eF, nullptr, s);
-        launch_split(P, (int)M, n, op.N, nv, t.Sp, t.eF, t.F, t.ld4[k], nullptr, nullptr, 0, s);
+        long long blocks = (M * nv + 7) / 8;  // 8 rows (warps) per block
+        if (blocks > 152LL * 16) blocks = 152LL * 16;
+        count_launch();
+        k_split_rows<<<(unsigned)blocks, 256, 0, s>>>(P, op.N, M, n, nv, t.Sp, t.eF, t.F,
+                                                      t.ld4[k]);
       } else {
         count_launch();
         k_split_fibers<<<dim3((unsigned)((M + 31) / 32), nv), 256, 0, s>>>(

@@ -41,7 +41,13 @@
 // with the potential term fused into the first epilogue; both products run in one launch
 // and add their tiles to the zeroed output (two terms per element, so the FP64 atomic sum
 // is order-independent).  Operand tiles reach shared memory by TMA (128-byte swizzle,
-// K-major), one thread issues tcgen05.mma into tensor memory, and four warps drain it.
+// K-major), one thread issues tcgen05.mma into tensor memory, and eight warps drain it.
+//
+// The 2D H-apply (Eq. tensor_op2D) runs its four mode products one after the other, each
+// over the fibers of its mode (A = fiber slices, B = K_k slices), with a persistent kernel:
+// one CTA per SM takes tile after tile, its producer, MMA and epilogue warps working on
+// successive tiles at once (the 48-point contraction gives short MMA loops, so a CTA per
+// tile spent most of its time in the epilogue with the tensor pipe idle).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

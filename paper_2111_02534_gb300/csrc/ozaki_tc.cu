@@ -701,15 +701,16 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUte
 
 // One product C = A B^T (A = wave-function fiber slices, 7 base-256 digits; B = mode-matrix
 // slices, 8 digits; contraction length <= 128) over tiles m fastest, then n, then the
-// vector: a mode product of the 2D H-apply.  Persistent: one CTA per SM takes tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... with the three stages of a tile overlapped across tiles.
-// Warp 0 lane 0 streams the slices of tile after tile through the shared-memory rings;
-// warp 1 lane 0 issues a tile's MMAs once the epilogue has released the tensor memory of
-// the previous one; warps 2 .. 9 (two per TMEM lane quarter, each half of the columns)
-// fetch the tile's old output values and exponents while its MMAs run, then drain the
-// accumulators, release the tensor memory (mbarrier tmem_empty, 8 arrivals) and only then
-// store, so that the next tile's MMAs run during the stores.  (A CTA per tile, which ran the
-// loads, the MMAs and the epilogue one after the other, took 9 % longer at 48^4.)
+// vector: a mode product of the 2D H-apply.  Persistent: one CTA per SM takes tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... with the three stages of a tile overlapped across
+// tiles.  Warp 0 lane 0 streams the slices of tile after tile through the shared-memory
+// rings; warp 1 lane 0 issues a tile's MMAs once the epilogue has released the tensor
+// memory of the previous one; warps 2 .. 17 (four per TMEM lane quarter, a quarter of the
+// columns each) fetch the tile's old output values while its MMAs run, then drain the
+// accumulators, release the tensor memory (mbarrier tmem_empty, one arrival per epilogue
+// warp) and only then store, so that the next tile's MMAs run during the stores.  (A CTA per tile, which ran the
+// loads, the MMAs and the epilogue one after the other, took 5.2 ms per 8-vector apply at
+// 48^4 against 3.7 ms.)
 constexpr int kPEpiWarps = 16;  // four per TMEM lane quarter, a quarter of the columns each
 constexpr int kPThreads = 64 + 32 * kPEpiWarps;
 

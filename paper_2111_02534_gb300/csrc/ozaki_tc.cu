@@ -844,6 +844,9 @@ k_oz_gemm1p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int tm = (g.M + kBM - 1) / kBM, tn = (g.N + kBN - 1) / kBN;
   const long long T = (long long)tm * tn * g.nvec;
   const int KB = (g.K + kBK - 1) / kBK;
+  // one K block and one column tile (modes of at most 48 points): every tile multiplies by
+  // the same B slices, loaded once into stage 0 and kept
+  const bool b_fixed = KB == 1 && tn == 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kAStages; ++i) {
@@ -879,17 +882,19 @@ k_oz_gemm1p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int v = (int)(t / ((long long)tm * tn)), r = (int)(t % ((long long)tm * tn));
         const int m0 = (r % tm) * kBM, n0 = (r / tm) * kBN;
         for (int kb = 0; kb < KB && ok; ++kb, ++bcount) {
-          const int sb = (int)(bcount % kBStages);
-          const uint32_t rb = (uint32_t)(bcount / kBStages);
-          if (!tc::mbar_wait(&emptyB[sb], (rb & 1u) ^ 1u, g.err, 1)) {
-            ok = false;
-            break;
+          const int sb = b_fixed ? 0 : (int)(bcount % kBStages);
+          const uint32_t rb = b_fixed ? 0u : (uint32_t)(bcount / kBStages);
+          if (!b_fixed || t == blockIdx.x) {
+            if (!tc::mbar_wait(&emptyB[sb], (rb & 1u) ^ 1u, g.err, 1)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&fullB[sb], bstage);
+            for (int j = 0; j < SB; ++j)
+              tc::tma_load_3d(sB + sb * bstage + j * b_slice_bytes(), &tmB, &fullB[sb],
+                              kb * kBK, n0, v * g.zB + j);
+            lastB[sb] = (int)(rb & 1u);
           }
-          tc::mbar_arrive_expect_tx(&fullB[sb], bstage);
-          for (int j = 0; j < SB; ++j)
-            tc::tma_load_3d(sB + sb * bstage + j * b_slice_bytes(), &tmB, &fullB[sb], kb * kBK,
-                            n0, v * g.zB + j);
-          lastB[sb] = (int)(rb & 1u);
           for (int i = 0; i < SA; ++i, ++acount) {
             const int sa = (int)(acount % kAStages);
             const uint32_t ra = (uint32_t)(acount / kAStages);
@@ -929,8 +934,8 @@ k_oz_gemm1p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         tc::tc_fence_after();
         for (int kb = 0; kb < KB && ok; ++kb, ++bcount) {
-          const int sb = (int)(bcount % kBStages);
-          const uint32_t rb = (uint32_t)(bcount / kBStages);
+          const int sb = b_fixed ? 0 : (int)(bcount % kBStages);
+          const uint32_t rb = b_fixed ? 0u : (uint32_t)(bcount / kBStages);
           if (!tc::mbar_wait(&fullB[sb], rb & 1u, g.err, 3)) {
             ok = false;
             break;
@@ -961,7 +966,7 @@ k_oz_gemm1p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             tc::mma_commit(&emptyA[sa]);  // the A stage is free once these MMAs are done
           }
-          if (ok) tc::mma_commit(&emptyB[sb]);
+          if (ok && !b_fixed) tc::mma_commit(&emptyB[sb]);
         }
         // the tile's accumulators are complete once its MMAs are (after a failure: only so
         // that nothing is in flight at exit)
